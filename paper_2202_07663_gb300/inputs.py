@@ -1,0 +1,189 @@
+"""Seeded synthetic inputs for the lens-likelihood hot path.
+
+This module holds input generation only: parameter draws, PSF images, noise
+realisations and the serving request stream. It contains none of the lens
+model's arithmetic (no deflection, no light profile, no convolution, no
+likelihood), so both the CUDA path and the FP64 oracle may use it.
+
+Parameter vectors have 22 entries in the order of Table 2 of arXiv:2202.07663:
+  0 thetaE   1 gamma_epl  2 e_epl1  3 e_epl2  4 x_epl  5 y_epl
+  6 gamma_ext1  7 gamma_ext2
+  8 R_l  9 n_l  10 e_l1  11 e_l2  12 x_l  13 y_l  14 I_l
+  15 R_s  16 n_s  17 e_s1  18 e_s2  19 x_s  20 y_s  21 I_s
+Units: arcsec for positions and radii, counts/s for amplitudes.
+
+The paper's 100 lenstronomy systems and its TinyTim PSF are not available;
+these synthetic systems stand in for them with the paper's pixel scale
+(0.065 arcsec, Sec. 3) and the distributions below.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Tuple
+
+import numpy as np
+
+NPARAM = 22
+PARAM_NAMES = (
+    "theta_E", "gamma_epl", "e_epl1", "e_epl2", "x_epl", "y_epl",
+    "gamma_ext1", "gamma_ext2",
+    "R_l", "n_l", "e_l1", "e_l2", "x_l", "y_l", "I_l",
+    "R_s", "n_s", "e_s1", "e_s2", "x_s", "y_s", "I_s",
+)
+
+PIXEL_SCALE = 0.065  # arcsec per detector pixel (Sec. 3)
+
+# Box used for multi-start draws and for clipping perturbed vectors: the truth
+# ranges of the uniform parameters and +-2 sigma of the normal ones.
+PRIOR_BOX = np.array([
+    [1.0, 2.0],      # theta_E
+    [1.8, 2.2],      # gamma_epl
+    [-0.2, 0.2],     # e_epl1
+    [-0.2, 0.2],     # e_epl2
+    [-0.1, 0.1],     # x_epl
+    [-0.1, 0.1],     # y_epl
+    [-0.1, 0.1],     # gamma_ext1
+    [-0.1, 0.1],     # gamma_ext2
+    [0.5, 1.5],      # R_l
+    [2.0, 5.0],      # n_l
+    [-0.2, 0.2],     # e_l1
+    [-0.2, 0.2],     # e_l2
+    [-0.1, 0.1],     # x_l
+    [-0.1, 0.1],     # y_l
+    [100.0, 1000.0],  # I_l
+    [0.05, 0.3],     # R_s
+    [0.5, 4.0],      # n_s
+    [-0.3, 0.3],     # e_s1
+    [-0.3, 0.3],     # e_s2
+    [-0.6, 0.6],     # x_s
+    [-0.6, 0.6],     # y_s
+    [50.0, 500.0],   # I_s
+], dtype=np.float64)
+
+
+@dataclasses.dataclass(frozen=True)
+class SystemSpec:
+    """Shape and noise model of one synthetic lens system."""
+    H: int
+    W: int
+    k: int                      # supersampling factor
+    K: int                      # PSF side (odd)
+    psf: str = "gaussian"       # "gaussian" (FWHM 0.1") or "moffat" (beta 3, FWHM 0.12")
+    pixel_scale: float = PIXEL_SCALE
+    sigma_bkg: float = 0.01
+    gain_exposure: float = 1000.0   # G * t_exp, seconds (G = 1)
+
+
+# The five workloads: shapes, PSFs and batch sizes.
+CONFIGS = {
+    1: dict(spec=SystemSpec(60, 60, 2, 11, "gaussian"), B=64, draw="perturbed"),
+    2: dict(spec=SystemSpec(60, 60, 2, 11, "gaussian"), B=4096, draw="box"),
+    3: dict(spec=SystemSpec(100, 100, 4, 21, "moffat"), B=512, draw="perturbed"),
+    5: dict(spec=SystemSpec(200, 200, 4, 21, "gaussian"), B=16384, draw="box"),
+}
+
+
+def rng_for(config: int, system: int = 0) -> np.random.Generator:
+    """PCG64 stream for (config, system): seed = config * 1000 + system."""
+    return np.random.default_rng(config * 1000 + system)
+
+
+def draw_truth(rng: np.random.Generator) -> np.ndarray:
+    """One truth vector from the synthetic simulation distribution."""
+    p = np.empty(NPARAM)
+    p[0] = rng.uniform(1.0, 2.0)
+    p[1] = rng.uniform(1.8, 2.2)
+    p[2:4] = rng.normal(0.0, 0.1, 2)
+    p[4:6] = rng.normal(0.0, 0.05, 2)
+    p[6:8] = rng.normal(0.0, 0.05, 2)
+    p[8] = rng.uniform(0.5, 1.5)
+    p[9] = rng.uniform(2.0, 5.0)
+    p[10:12] = rng.normal(0.0, 0.1, 2)
+    p[12:14] = rng.normal(0.0, 0.05, 2)
+    p[14] = math.exp(rng.uniform(math.log(100.0), math.log(1000.0)))
+    p[15] = rng.uniform(0.05, 0.3)
+    p[16] = rng.uniform(0.5, 4.0)
+    p[17:19] = rng.normal(0.0, 0.15, 2)
+    p[19:21] = p[4:6] + rng.normal(0.0, 0.3, 2)
+    p[21] = math.exp(rng.uniform(math.log(50.0), math.log(500.0)))
+    return p
+
+
+def draw_perturbed(rng: np.random.Generator, truth: np.ndarray, B: int, frac: float = 0.02) -> np.ndarray:
+    """B vectors: truth + N(0, frac * box width), clipped to the box."""
+    width = PRIOR_BOX[:, 1] - PRIOR_BOX[:, 0]
+    out = truth[None, :] + rng.normal(0.0, 1.0, (B, NPARAM)) * (frac * width)[None, :]
+    lo = np.minimum(PRIOR_BOX[:, 0], truth)
+    hi = np.maximum(PRIOR_BOX[:, 1], truth)
+    return np.clip(out, lo, hi)
+
+
+def draw_box(rng: np.random.Generator, B: int) -> np.ndarray:
+    """B multi-start vectors, uniform over the box (amplitudes log-uniform)."""
+    u = rng.uniform(0.0, 1.0, (B, NPARAM))
+    out = PRIOR_BOX[:, 0] + u * (PRIOR_BOX[:, 1] - PRIOR_BOX[:, 0])
+    for j in (14, 21):
+        lo, hi = np.log(PRIOR_BOX[j])
+        out[:, j] = np.exp(lo + u[:, j] * (hi - lo))
+    return out
+
+
+def gaussian_psf(K: int, fwhm: float = 0.1, pixel_scale: float = PIXEL_SCALE) -> np.ndarray:
+    """Gaussian PSF sampled at pixel centres, normalised to unit sum."""
+    sig = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0))) / pixel_scale
+    c = (K - 1) / 2.0
+    r = np.arange(K) - c
+    g = np.exp(-0.5 * (r[:, None] ** 2 + r[None, :] ** 2) / sig ** 2)
+    return g / g.sum()
+
+
+def moffat_psf(K: int, beta: float = 3.0, fwhm: float = 0.12, pixel_scale: float = PIXEL_SCALE) -> np.ndarray:
+    """Moffat PSF sampled at pixel centres, normalised to unit sum."""
+    alpha = fwhm / (2.0 * math.sqrt(2.0 ** (1.0 / beta) - 1.0)) / pixel_scale
+    c = (K - 1) / 2.0
+    r = np.arange(K) - c
+    m = (1.0 + (r[:, None] ** 2 + r[None, :] ** 2) / alpha ** 2) ** (-beta)
+    return m / m.sum()
+
+
+def make_psf(spec: SystemSpec) -> np.ndarray:
+    if spec.psf == "gaussian":
+        return gaussian_psf(spec.K, pixel_scale=spec.pixel_scale)
+    if spec.psf == "moffat":
+        return moffat_psf(spec.K, pixel_scale=spec.pixel_scale)
+    raise ValueError("unknown psf kind %r" % spec.psf)
+
+
+def add_noise(rng: np.random.Generator, model: np.ndarray, sigma_bkg: float, gain_exposure: float) -> np.ndarray:
+    """Observed image from a noiseless model image (counts/s):
+    Poisson(G t_exp M) / (G t_exp) + N(0, sigma_bkg^2)."""
+    model = np.asarray(model, dtype=np.float64)
+    out = model.copy()
+    if gain_exposure > 0:
+        out = rng.poisson(np.clip(model, 0.0, None) * gain_exposure) / gain_exposure
+    return out + rng.normal(0.0, sigma_bkg, model.shape)
+
+
+@dataclasses.dataclass
+class LensRequest:
+    """One request of the serving stream."""
+    index: int
+    arrival_s: float
+    spec: SystemSpec
+    B: int
+    seed: int
+
+
+def serving_stream(n: int = 1000, rate_hz: float = 20.0, seed: int = 4000,
+                   sizes: Tuple[int, ...] = (40, 60, 80, 120), ks: Tuple[int, ...] = (2, 4),
+                   Ks: Tuple[int, ...] = (11, 21), bmin: int = 256, bmax: int = 2048) -> List[LensRequest]:
+    """Seeded Poisson arrivals of heterogeneous lens systems."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
+    out = []
+    for i in range(n):
+        s = int(rng.choice(sizes))
+        spec = SystemSpec(s, s, int(rng.choice(ks)), int(rng.choice(Ks)), "gaussian")
+        out.append(LensRequest(i, float(t[i]), spec, int(rng.integers(bmin, bmax + 1)), seed * 1000 + i))
+    return out

@@ -1,0 +1,68 @@
+"""Mutation check of the oracle pins.
+
+Each case plants one plausible mistake in a copy of the oracle source (a
+dropped term, a wrong sign, a swapped index, a transposed operand), builds it
+on the CPU, and runs the pin suite against it: the pins must fail for every
+mutant. The real oracle is never modified.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "gl_oracle.cpp")
+
+MUTANTS = {
+    "rotation_sign": ("yp = -s * dx + c * dy;", "yp = s * dx + c * dy;"),
+    "rotate_back_sign": ("ax = c * alx - s * aly;", "ax = c * alx + s * aly;"),
+    "series_coefficient": ("(2.0 * n - (2.0 - t)) / (2.0 * n + (2.0 - t))", "(2.0 * n - (2.0 - t)) / (2.0 * n + (2.0 + t))"),
+    "series_sign": ("const T cn = -f *", "const T cn = f *"),
+    "epl_b_scale": ("const T b = thetaE * sqrt(q);", "const T b = thetaE;"),
+    "epl_power": ("pow(b / R, t - 1.0)", "pow(b / R, t)"),
+    "phi_half_angle": ("phi = 0.5 * atan2(e2, e1);", "phi = atan2(e2, e1);"),
+    "q_of_e": ("q = (1.0 - e) / (1.0 + e);", "q = 1.0 - e;"),
+    "shear_sign": ("ay = g2 * x - g1 * y;", "ay = g2 * x + g1 * y;"),
+    "shear_swap": ("ax = g1 * x + g2 * y;", "ax = g1 * y + g2 * x;"),
+    "sersic_bn": ("1.9992 * l[1] - 0.3271", "1.9992 * l[1] + 0.3271"),
+    "sersic_axis_ratio": ("sqrt(q * xl * xl + yl * yl / q)", "sqrt(xl * xl / q + q * yl * yl)"),
+    "sersic_index": ("pow(rho / l[0], 1.0 / l[1])", "pow(rho / l[0], l[1])"),
+    "lens_light_at_beta": ("return sersic(bx, by, p + 15) + sersic(T(x), T(y), p + 8);",
+                           "return sersic(bx, by, p + 15) + sersic(bx, by, p + 8);"),
+    "grid_transpose": ("const double x = (j * k + b - cx) * sub;", "const double x = (i * k + a - cx) * sub;"),
+    "grid_offset": ("const double cx = (k * W - 1) * 0.5", "const double cx = (k * W) * 0.5"),
+    "binning_norm": ("out[i * W + j] = acc / double(k * k);", "out[i * W + j] = acc / double(k);"),
+    "conv_no_flip": ("const int ii = i + c - a;", "const int ii = i - c + a;"),
+    "conv_transpose": ("acc += psf[a * K + b] * img[ii * W + jj];", "acc += psf[b * K + a] * img[ii * W + jj];"),
+    "poisson_term": ("var = var + model[i] / s.gain_exposure;", "var = var + model[i] * s.gain_exposure;"),
+    "loglik_norm": ("ll += -0.5 * (c2 + log(2.0 * PI * var));", "ll += -0.5 * (c2 + log(var));"),
+    "dual_product_rule": ("r.d[i] = a.d[i] * b.v + a.v * b.d[i];", "r.d[i] = a.d[i] * b.v;"),
+    "dual_quotient": ("r.d[i] = (a.d[i] - r.v * b.d[i]) * inv;", "r.d[i] = (a.d[i] + r.v * b.d[i]) * inv;"),
+}
+
+
+def _run_mutant(name, old, new, tmp):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor for %s not unique/present" % name
+    path = os.path.join(tmp, name + ".cpp")
+    lib = os.path.join(tmp, name + ".so")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    subprocess.run(["g++", "-std=c++17", "-O1", "-fopenmp", "-fPIC", "-shared", path, "-o", lib], check=True)
+    env = dict(os.environ, GL_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode
+
+
+def test_every_planted_mistake_fails_a_pin():
+    with tempfile.TemporaryDirectory() as tmp:
+        with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+            futs = [ex.submit(_run_mutant, n, o, w, tmp) for n, (o, w) in MUTANTS.items()]
+            results = dict(f.result() for f in futs)
+    survivors = [n for n, rc in results.items() if rc == 0]
+    assert not survivors, "mutants not caught by any pin: %s" % survivors
