@@ -393,6 +393,25 @@ void orc_likelihood_image(const double* model, const double* image, const double
   likelihood(s, model, *loglik, *chi2);
 }
 
+// Model image M [H, W] and its Jacobian J [H, W, 22] = dM / d params of one
+// vector (forward-mode duals through binning and convolution).
+void orc_model_jacobian(const double* params, int H, int W, const double* psf, int K, double dpix, int k,
+                        double* model_out, double* jac_out) {
+  const System s{nullptr, nullptr, H, W, psf, K, dpix, k, 0.0};
+  using D = Dual<NPARAM>;
+  D p[NPARAM];
+  for (int i = 0; i < NPARAM; ++i) {
+    p[i] = D(params[i]);
+    p[i].d[i] = 1.0;
+  }
+  std::vector<D> pre, model;
+  model_image(s, p, pre, model);
+  for (int i = 0; i < H * W; ++i) {
+    model_out[i] = model[i].v;
+    for (int j = 0; j < NPARAM; ++j) jac_out[size_t(i) * NPARAM + j] = model[i].d[j];
+  }
+}
+
 // Noiseless model images (PSF-convolved) for B parameter vectors: out [B, H, W].
 void orc_simulate(const double* params, int B, int H, int W, const double* psf, int K,
                   double dpix, int k, double* out, int nthreads) {

@@ -64,6 +64,7 @@ def _load():
             "orc_binned_image": ([_d, i, i, i, dbl, _d], None),
             "orc_convolve": ([_d, i, i, _d, i, _d], None),
             "orc_simulate": ([_d, i, i, i, _d, i, dbl, i, _d, i], None),
+            "orc_model_jacobian": ([_d, i, i, _d, i, dbl, i, _d, _d], None),
             "orc_likelihood_image": ([_d, _d, _d, i, i, dbl, _d, _d], None),
             "orc_loglik": ([_d, i, _d, _d, i, i, _d, i, dbl, i, dbl, _d, _d, _d, i], None),
         }
@@ -192,3 +193,13 @@ def likelihood_image(model, image, sigma, gain_exposure: float):
     _load().orc_likelihood_image(_p(model), _p(image), _p(sigma), H, W, float(gain_exposure),
                                  ctypes.byref(ll), ctypes.byref(c2))
     return ll.value, c2.value
+
+
+def model_jacobian(params, H: int, W: int, psf, pixel_scale: float, k: int):
+    """(M [H, W], J [H, W, 22]): model image of one vector and dM/dparams."""
+    p = _f64(params).reshape(NPARAM)
+    psf = _f64(psf)
+    M = np.empty((H, W))
+    J = np.empty((H, W, NPARAM))
+    _load().orc_model_jacobian(_p(p), H, W, _p(psf), psf.shape[0], float(pixel_scale), int(k), _p(M), _p(J))
+    return M, J

@@ -509,3 +509,28 @@ def test_loglik_value_path_equals_gradient_path():
         ll, c2 = oracle.likelihood_image(model[i], D, 0.01, 1000.0)
         assert a[0][i] == pytest.approx(ll, rel=1e-13)
         assert a[1][i] == pytest.approx(c2, rel=1e-13)
+
+
+def test_model_jacobian_matches_differences_and_gradient():
+    """dM/dparams from the oracle's duals: central differences of the model, and
+    the chain rule J^T dlogL/dM reproduces the log L gradient."""
+    truth, D, psf = _small_system(8, H=10, W=12, k=2, K=3)
+    p = inputs.draw_perturbed(np.random.default_rng(8), truth, 1)[0]
+    M, J = oracle.model_jacobian(p, 10, 12, psf, 0.065, 2)
+    np.testing.assert_allclose(M, oracle.simulate(p, 10, 12, psf, 0.065, 2)[0], rtol=1e-14)
+    def cd(i, h):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        return (oracle.simulate(pp, 10, 12, psf, 0.065, 2)[0] - oracle.simulate(pm, 10, 12, psf, 0.065, 2)[0]) / (2 * h)
+
+    for i in (0, 1, 3, 9, 16, 19):
+        h = 1e-4 * max(1.0, abs(p[i]))
+        fd = (4 * cd(i, h / 2) - cd(i, h)) / 3
+        np.testing.assert_allclose(J[:, :, i], fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+    G, sig = 1000.0, 0.01
+    v = sig ** 2 + M / G
+    r = D - M
+    gpix = r / v + (r * r / (v * v) - 1 / v) / (2 * G)
+    _, _, g = oracle.loglik(p, D, sig, psf, 0.065, 2, G, grad=True)
+    np.testing.assert_allclose(np.einsum("hw,hwj->j", gpix, J), g[0], rtol=1e-9, atol=1e-9 * np.abs(g).max())
