@@ -1,0 +1,376 @@
+"""Benchmark of the batched lens log-likelihood + gradient on GB300.
+
+One step = one gl_loglik_grad call over B = 4096 parameter vectors of one
+synthetic 60x60 lens (k = 2 supersampling, 11x11 Gaussian PSF, 0.065"/pix):
+the multi-start batched workload. Every step runs the whole hot path:
+per-vector setup, ray shooting + lights + binning, PSF convolution +
+likelihood + pixel adjoint, recomputed-ray adjoint, gradient reduction.
+
+Prints ONE JSON line (rank 0). Keys beyond the metric:
+  e2e          same metric through the host-buffer C-ABI entry point
+               (pinned params in, log L + gradient out, copies timed)
+  roofline     dominant kernel (k_ray_adj) against the FP32 ALU peak
+  cpu_baseline the FP64 oracle on the host cores, bounded sample
+  clocks       nvidia-smi SM clocks and throttle reasons during the timed region
+  gpu_launches kernels this library launched in the timed region
+
+--impl reference times the FP64 CPU oracle on the same workload instead
+(the paper publishes no per-evaluation reference implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2202_07663_gb300 import inputs  # noqa: E402
+
+CONFIG = 2
+METRIC = "log-lik+grad evals/s"
+UNIT = "evals/s"
+WORKLOAD = "multistart-60x60-k2-psf11-B4096"
+
+# FP32 flop counts per ray of the two ray kernels (FMA = 2), N = EPL series
+# terms of the vector; per pixel of the convolution kernel.
+def flops_ray_fwd(N):
+    return 83 + 9 * N
+
+
+def flops_ray_adj(N):
+    return 306 + 31 * N
+
+
+def flops_conv_pixel(K, grad):
+    return (4 if grad else 2) * K * K + 25
+
+
+SERIES_TOL = 2e-8
+NMAX = 64
+
+
+def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
+    """Per-vector EPL series length, the rules the setup kernel applies:
+    forward  smallest N >= 0 with f^(N+1)/(1-f) <= tol,
+    adjoint  smallest N >= 1 with (N+1) f^N/(1-f)^2 <= tol."""
+    f = np.hypot(params[:, 2].astype(np.float64), params[:, 3].astype(np.float64))
+    N = np.arange(0, NMAX + 1)[None, :]
+    with np.errstate(divide="ignore"):
+        lf = np.where(f > 0, np.log(np.maximum(f, 1e-300)), -1e300)[:, None]
+    l1f = np.log1p(-np.minimum(f, 0.999999))[:, None]
+    if adjoint:
+        good = (np.log(N + 1.0) + N * lf - 2 * l1f <= np.log(SERIES_TOL)) & (N >= 1)
+    else:
+        good = (N + 1) * lf - l1f <= np.log(SERIES_TOL)
+    first = np.where(good.any(axis=1), good.argmax(axis=1), NMAX)
+    return first.astype(np.int64)
+
+
+# DRAM bytes per launch of k_ray_adj from one ncu capture, valid only for the
+# kernel source it was taken on (sha256 prefix of gl_kernels.cu + gl_device.cuh).
+TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("gl_kernels.cu", "gl_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2202_07663_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(device, rank: int):
+    """Synthetic lens system (observed image from the GPU model + seeded noise) and B vectors."""
+    import torch
+    from paper_2202_07663_gb300 import abi
+    c = inputs.CONFIGS[CONFIG]
+    spec, B = c["spec"], c["B"]
+    rng = inputs.rng_for(CONFIG, 0)
+    truth = inputs.draw_truth(rng)
+    psf = inputs.make_psf(spec).astype(np.float32)
+    blank = np.zeros((spec.H, spec.W), np.float32)
+    s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
+    s0.close()
+    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
+    params = inputs.draw_box(np.random.default_rng(CONFIG * 1000 + 17 + rank), B).astype(np.float32)
+    return spec, B, truth, psf, image, params
+
+
+def cpu_baseline(spec, psf, image, params, budget_s: float = 12.0):
+    """The FP64 oracle (log L + gradient) on a bounded sample of the same workload."""
+    import oracle
+    oracle.build()
+    nt = oracle.max_threads()
+    args = (image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k, spec.gain_exposure)
+    n0 = min(len(params), max(nt, 8))
+    t = time.perf_counter()
+    oracle.loglik(params[:n0].astype(np.float64), *args, grad=True, nthreads=nt)
+    dt = time.perf_counter() - t
+    n = int(min(len(params), max(n0, math.floor(n0 * budget_s / max(dt, 1e-3)))))
+    t = time.perf_counter()
+    oracle.loglik(params[:n].astype(np.float64), *args, grad=True, nthreads=nt)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": "%d of the %d vectors (log L + forward-mode gradient, FP64), %.1f s" % (n, len(params), dt)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    c = inputs.CONFIGS[CONFIG]
+    spec, B = c["spec"], c["B"]
+    rng = inputs.rng_for(CONFIG, 0)
+    truth = inputs.draw_truth(rng)
+    psf = inputs.make_psf(spec).astype(np.float32)
+    model = oracle.simulate(truth, spec.H, spec.W, psf, spec.pixel_scale, spec.k)[0]
+    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
+    params = inputs.draw_box(np.random.default_rng(CONFIG * 1000 + 17), B).astype(np.float32)
+    nt = oracle.max_threads()
+    a = (image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k, spec.gain_exposure)
+    per_step = max(nt * 2, 32)
+    for w in range(args.warmup):
+        oracle.loglik(params[:nt].astype(np.float64), *a, grad=True, nthreads=nt)
+    times = []
+    for s in range(args.steps):
+        sl = params[(s * per_step) % B:(s * per_step) % B + per_step].astype(np.float64)
+        t = time.perf_counter()
+        oracle.loglik(sl, *a, grad=True, nthreads=nt)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = per_step * args.steps / total
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": spec.H, "W": spec.W, "supersample": spec.k, "psf": spec.K, "B": B,
+                   "step_sample": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                         "sample": "%d vectors per step of the %d-vector workload" % (per_step, B)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2202_07663_gb300 import abi, build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+
+    spec, B, truth, psf, image, params = make_workload(device, rank)
+    sysm = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    sysm.reserve(B)
+    p_dev = torch.from_numpy(params).to(device)
+    ll = torch.empty(B, dtype=torch.float64, device=device)
+    g = torch.empty(B, 22, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)   # > L2 (129 MB)
+
+    def step():
+        sysm.loglik_grad(p_dev, out=(ll, g, None))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident in HBM; L2 flushed between steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    abi.gl_profile_reset()
+    abi.gl_profile_enable(True)
+    n0 = abi.gl_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
+        t0 = time.perf_counter()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    launches = abi.gl_launch_count() - n0
+    prof = abi.gl_profile_read()
+    abi.gl_profile_enable(False)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    t_rank = torch.tensor([step_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+    step_ms = float(t_rank.item())
+    value = world * B / (step_ms * 1e-3)
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    hp = torch.from_numpy(params).pin_memory()
+    hl = torch.empty(B, dtype=torch.float64).pin_memory()
+    hg = torch.empty(B, 22, dtype=torch.float64).pin_memory()
+    hp_np, hl_np, hg_np = hp.numpy(), hl.numpy(), hg.numpy()
+    for _ in range(3):
+        sysm.loglik_grad_host(hp_np, hl_np, hg_np)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sysm.loglik_grad_host(hp_np, hl_np, hg_np)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * B / float(te.item())
+
+    # ---- roofline of the dominant kernel, from the live event timings
+    n_adj, ms_adj = prof["k_ray_adj"]
+    N = series_terms(params, adjoint=True)
+    rays = spec.H * spec.W * spec.k * spec.k
+    flop_adj = float(rays * flops_ray_adj(N).sum())
+    adj_s = (ms_adj / max(n_adj, 1)) * 1e-3
+    peaks, peak_src = read_peaks()
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flop_adj / adj_s / 1e12
+    th = kernel_source_hash()
+    traffic = TRAFFIC.get(th)
+    kern = {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items() if v[0] > 0}
+    tot = sum(v[1] for v in prof.values())
+    for k in kern:
+        kern[k]["share"] = round(prof[k][1] / tot, 4) if tot > 0 else None
+    clocks = clk.summary()
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, psf, image, params)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f64 per-vector sums)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": spec.H, "W": spec.W, "supersample": spec.k, "psf": spec.K,
+                   "pixel_scale": spec.pixel_scale, "B_per_gpu": B, "params": "uniform over the prior box",
+                   "l2": "flushed (256 MB write) between timed steps, flush outside the step events",
+                   "parallelism": "replicas (B per GPU)" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 22 * 4,
+                "d2h_bytes_per_step": B * 8 + B * 22 * 8},
+        "roofline": {"bound": "alu", "kernel": "k_ray_adj", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                     "flops_per_launch": flop_adj, "launch_ms": adj_s * 1e3,
+                     "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 x %.0f MHz (max SM clock, %s peaks file)" % (
+                         sms, sm_mhz, peak_src),
+                     "mean_series_terms": float(N.mean())},
+        "kernels": kern,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * gigalens.h - C ABI of the GB300 (sm_103a) batched lens-model likelihood.
+ *
+ * The library evaluates, for B parameter vectors of one lens system at a time
+ * (or of several systems in one grouped launch), the forward model of
+ * GIGA-Lens (arXiv:2202.07663, Sec. 2.1.1), its Gaussian log-likelihood with
+ * model-dependent variance (Sec. 2.1.2, Eq. model-def) and the gradient of
+ * that log-likelihood with respect to the 22 physical parameters (Sec. 2.2).
+ *
+ * Conventions shared by every entry point:
+ *  - Parameter vectors are rows of GL_NPARAM = 22 float32 values in the order
+ *    of Table 2: thetaE, gamma_epl, e_epl1, e_epl2, x_epl, y_epl, gamma_ext1,
+ *    gamma_ext2, R_l, n_l, e_l1, e_l2, x_l, y_l, I_l, R_s, n_s, e_s1, e_s2,
+ *    x_s, y_s, I_s. Positions and radii in arcsec, amplitudes in counts/s.
+ *  - Images are row-major float32 [H, W]; row i has y = (i - (H-1)/2) * pixel
+ *    scale and column j has x = (j - (W-1)/2) * pixel scale (pixel centres
+ *    symmetric about the origin). The k-times supersampled grid follows the
+ *    same rule at pixel scale / k (Sec. 2.1.1, last paragraph).
+ *  - Unless a name ends in _host, every pointer argument other than the
+ *    gl_system handle is DEVICE memory owned by the caller, and every call is
+ *    asynchronous on the given CUDA stream (cudaStream_t passed as void*;
+ *    NULL means the legacy default stream). Results are valid once the
+ *    stream has reached the call.
+ *  - Every call returns GL_OK (0) or a negative GL_ERR_* code; no exception
+ *    or abort crosses the ABI. gl_error_string() names a code and
+ *    gl_last_error_message() gives detail for the calling thread.
+ *  - A vector with a non-finite entry, or |e| >= 1 for any of the three
+ *    ellipticities, or R <= 0 or n <= 0 for a light profile, is not an error:
+ *    its log-likelihood, chi^2 and gradient come back as NaN.
+ *  - Calls on one gl_system share its scratch memory: issue them on one
+ *    stream (or serialise them). Different systems are independent.
+ */
+#ifndef GIGALENS_H_
+#define GIGALENS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GL_NPARAM 22
+
+enum gl_status {
+  GL_OK = 0,
+  GL_ERR_INVALID_ARG = -1, /* bad pointer, size or value; nothing was launched */
+  GL_ERR_OOM = -2,         /* device or pinned allocation failed */
+  GL_ERR_CUDA = -3,        /* a CUDA runtime call failed; see gl_last_error_message */
+  GL_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+  GL_ERR_BUDGET = -5,      /* request exceeds the caller's memory budget */
+  GL_ERR_UNSUPPORTED = -6  /* shape outside what the kernels support (e.g. image too large) */
+};
+
+typedef struct gl_system gl_system;
+
+/*
+ * gl_system_create - upload one lens system and keep it resident.
+ *
+ * Defines the data of the likelihood of Sec. 2.1.2 (Eq. model-def): the
+ * observed image I_obs (counts/s), the background noise sigma_bkg, the PSF
+ * and the exposure term G * t_exp; and the pixel grid of Sec. 2.1.1
+ * (detector pixel scale, supersampling factor k_super).
+ *
+ *  out           receives the handle (host pointer to a gl_system*).
+ *  image         HOST float32 [H, W], observed image I_obs.
+ *  noise_map     HOST float32 [H, W], per-pixel background standard
+ *                deviation sigma_bkg (> 0), or NULL with sigma_bkg_scalar.
+ *  sigma_bkg     used for every pixel when noise_map is NULL (> 0).
+ *  H, W          image size, 1 <= H, W <= 4096.
+ *  psf           HOST float32 [K, K], used as given (not renormalised).
+ *  K             PSF side, odd, 1 <= K <= 63.
+ *  pixel_scale   arcsec per detector pixel (> 0).
+ *  supersample   k_super >= 1 (<= 16).
+ *  gain_exposure G * t_exp in seconds; <= 0 drops the Poisson term of the
+ *                variance (sigma_tot^2 = sigma_bkg^2).
+ *  stream        stream for the uploads; the call returns after they finish.
+ *
+ * The library copies every input; the caller keeps its buffers. Errors:
+ * GL_ERR_INVALID_ARG for bad sizes, pointers or values; GL_ERR_UNSUPPORTED
+ * when the zero-padded image does not fit the shared-memory convolution
+ * stage ((ceil(H/16)*16 + K - 1) * (W + K - 1) * 4 bytes + K*K*4 must stay
+ * below 220 KiB); GL_ERR_OOM / GL_ERR_CUDA on device failures.
+ */
+int gl_system_create(gl_system** out, const float* image, const float* noise_map, float sigma_bkg,
+                     int H, int W, const float* psf, int K, double pixel_scale, int supersample,
+                     double gain_exposure, void* stream);
+
+/* Free the system, its resident data and its scratch. Synchronises the
+ * device first. NULL is accepted. */
+int gl_system_destroy(gl_system* sys);
+
+/* Pre-size the system's scratch for batches of up to B vectors so that later
+ * calls with B' <= B allocate nothing. */
+int gl_system_reserve(gl_system* sys, int B);
+
+/* Device bytes the system's scratch needs for a batch of B vectors. */
+size_t gl_system_scratch_bytes(const gl_system* sys, int B);
+
+/* Device bytes held by the resident data (image, variance, PSF). */
+size_t gl_system_resident_bytes(const gl_system* sys);
+
+/*
+ * gl_loglik - log-likelihood of B parameter vectors (Sec. 2.1.2, Eq.
+ * model-def):
+ *   log L = -1/2 sum_pixels [ (I_obs - I_model)^2 / s2 + ln(2 pi s2) ],
+ *   s2 = sigma_bkg^2 + I_model / (G t_exp),
+ * with I_model the PSF-convolved, k x k averaged, supersampled image of
+ * Sec. 2.1.1. Arithmetic is float32 per ray and per pixel; each vector's sum
+ * is accumulated in float64.
+ *
+ *  params      device float32 [B, 22].
+ *  B           number of vectors, 0 <= B <= 2^24 (B = 0 does nothing).
+ *  loglik_out  device float64 [B].
+ *  chi2_out    device float64 [B] (first term of the sum, Sec. 2.1.2
+ *              Eq. chi^2), or NULL.
+ */
+int gl_loglik(gl_system* sys, const float* params, int B, double* loglik_out, double* chi2_out, void* stream);
+
+/*
+ * gl_loglik_grad - gl_loglik plus d log L / d params (Sec. 2.2), computed
+ * by a hand-written adjoint: the pixel adjoint is correlated with the PSF
+ * and spread over the k x k subpixels, then every ray is recomputed and its
+ * forward-mode derivatives are contracted with that adjoint. No ray position
+ * is stored.
+ *
+ *  grad_out    device float64 [B, 22], same order as params.
+ */
+int gl_loglik_grad(gl_system* sys, const float* params, int B, double* loglik_out, double* chi2_out,
+                   double* grad_out, void* stream);
+
+/*
+ * gl_loglik_grad_host - gl_loglik_grad with HOST buffers: copies params in,
+ * computes, copies the results out and synchronises the stream before
+ * returning. params/loglik_out/grad_out are host memory (pinned is fastest);
+ * chi2_out may be NULL.
+ */
+int gl_loglik_grad_host(gl_system* sys, const float* params, int B, double* loglik_out, double* chi2_out,
+                        double* grad_out, void* stream);
+
+/*
+ * gl_simulate - noiseless model images I_model (Sec. 2.1.1): ray-shoot the
+ * supersampled grid, add lens light, average k x k, convolve with the PSF.
+ *
+ *  images_out  device float32 [B, H, W].
+ */
+int gl_simulate(gl_system* sys, const float* params, int B, float* images_out, void* stream);
+
+/*
+ * Grouped launch over several systems (continuous batching): one set of
+ * kernel launches covers n (system, batch) segments. For segment s,
+ * params[s] is device float32 [B[s], 22], loglik_out[s] device float64
+ * [B[s]] and grad_out[s] device float64 [B[s], 22] or NULL (log L only).
+ * chi2_out may be NULL or hold NULL entries. The host arrays are read before
+ * the call returns. A system may appear in at most one segment of a call.
+ * 1 <= n <= GL_MAX_SEGMENTS.
+ */
+#define GL_MAX_SEGMENTS 256
+int gl_loglik_grad_grouped(gl_system* const* systems, const float* const* params, const int* B,
+                           double* const* loglik_out, double* const* chi2_out, double* const* grad_out, int n,
+                           void* stream);
+
+/* Name of a status code (static string). */
+const char* gl_error_string(int code);
+
+/* Detail of the calling thread's last error (static per-thread buffer). */
+const char* gl_last_error_message(void);
+
+/*
+ * Instrumentation. When enabled, every kernel the library launches is
+ * bracketed by CUDA events recorded on the launching stream. gl_profile_read
+ * synchronises on those events and fills, per kernel kind (indices below),
+ * the number of launches and the summed device time in milliseconds;
+ * arrays hold GL_KERNEL_KINDS entries. gl_launch_count counts every kernel
+ * launch since load (profiling on or off).
+ */
+#define GL_KERNEL_KINDS 6
+enum gl_kernel_kind {
+  GL_K_SETUP = 0,    /* per-vector constants */
+  GL_K_RAY_FWD = 1,  /* ray shooting + lights + k x k binning */
+  GL_K_CONV = 2,     /* PSF convolution + likelihood (+ pixel adjoint) */
+  GL_K_RAY_ADJ = 3,  /* recomputed rays + forward-mode derivatives */
+  GL_K_FINAL = 4,    /* per-vector gradient reduction */
+  GL_K_OTHER = 5
+};
+int gl_profile_enable(int on);
+int gl_profile_reset(void);
+int gl_profile_read(long long* launches, double* total_ms);
+const char* gl_kernel_name(int kind);
+long long gl_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GIGALENS_H_ */

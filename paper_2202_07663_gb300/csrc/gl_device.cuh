@@ -1,0 +1,180 @@
+// gl_device.cuh - device data layout and per-ray arithmetic of the lens model.
+//
+// Model (arXiv:2202.07663, Sec. 2.1.1): an elliptical power-law (EPL) mass
+// plus external shear deflects each ray of a k-times supersampled pixel grid;
+// the source Sersic is evaluated at the ray's source-plane position, the lens
+// Sersic at its image-plane position; k x k rays are averaged to a detector
+// pixel; the result is convolved with the PSF.
+//
+// The EPL is evaluated in a form derived for this code rather than in the
+// paper's (q, phi, rotate, series, rotate back) sequence. With the complex
+// ellipticity eps = e1 + i e2 = f e^{2 i phi}, f = (1-q)/(1+q), and the
+// offset z = (x - x_c) + i (y - y_c) of a ray from the lens centre:
+//
+//   w   = z - eps conj(z)                 (= 2/(1+q) e^{i phi} (q x_l + i y_l))
+//   rho^2 = |w|^2 / (1 - |eps|^2)         (= q x_l^2 + y_l^2 / q, the paper's
+//                                          elliptical radius of Eq. kappa)
+//   u   = -conj(eps) w / conj(w)          (= -f e^{2 i phi_ell}, Tessore & Metcalf)
+//   F(u) = sum_n a_n u^n,  a_0 = 1,  a_n = a_{n-1} c_n,
+//          c_n = (2n - 2 + t) / (2n + 2 - t),  t = gamma - 1
+//   alpha = (thetaE / rho)^t  w  F(u)     (image frame, complex)
+//
+// This is the Tessore & Metcalf (2015) deflection that the paper cites,
+// rotated back to the image frame, after the identities
+//   2b/(1+q) (b/R)^(t-1) e^{i phi} e^{i phi_ell} = (thetaE/rho)^t w
+// (b = thetaE sqrt(q), R = sqrt(q) rho) have been applied. It is smooth in
+// (e1, e2) through e = 0, needs no atan2 and no rotation, and gives the
+// gradient with respect to e1, e2 in closed form. F is evaluated by Horner's
+// rule with a per-vector term count N, so all rays of a vector run the same
+// loop.
+//
+// The Sersic profile (Eq. Sersic) uses the same quadratic form for its
+// elliptical radius: q x_l^2 + y_l^2 / q = A dx^2 + 2 B dx dy + C dy^2 with
+// A = (1 + e^2 - 2 e1)/(1 - e^2), B = -2 e2/(1 - e^2), C = (1 + e^2 + 2 e1)/(1 - e^2),
+// and is evaluated as I = I0 exp2(k1 (1 - s)), s = exp2(c1 log2(rho^2) + c0),
+// with c1 = 1/(2n), c0 = -log2(R_eff)/n, k1 = b_n / ln 2, b_n = 1.9992 n - 0.3271.
+#pragma once
+
+#include <cstdint>
+
+namespace gl {
+
+constexpr int NPARAM = 22;
+constexpr int NMAX = 64;             // cap on EPL series terms per vector
+constexpr int NACC = 24;             // adjoint accumulators per vector
+constexpr float RHO2_MIN = 1e-12f;   // (1e-6 arcsec)^2: EPL deflection zero / Sersic radius floor
+constexpr int RAY_THREADS = 256;     // block size of the ray kernels
+
+// Accumulator slots of the adjoint (per vector, before the chain rule).
+enum Acc {
+  A_THETAE = 0, A_T, A_E1, A_E2, A_XC, A_YC, A_G1, A_G2,            // mass (x b_s/n_s)
+  A_L_R, A_L_N1, A_L_N2, A_L_E1, A_L_E2, A_L_X, A_L_Y, A_L_I,        // lens light
+  A_S_R, A_S_N1, A_S_N2, A_S_E1, A_S_E2, A_S_X, A_S_Y, A_S_I         // source
+};
+
+struct LightC {
+  float A, B2, C;          // rho^2 = A dx^2 + B2 dx dy + C dy^2 (B2 = 2B)
+  float x, y;              // centre
+  float c1, c0;            // log2 s = c1 log2(rho^2) + c0
+  float k1;                // b_n / ln 2
+  float I0;                // amplitude
+  float A1, B21, C1;       // d(A, B2, C)/d e1
+  float A2, B22, C2;       // d(A, B2, C)/d e2
+};
+
+struct __align__(16) VecConst {
+  float xc, yc;            // EPL centre
+  float e1, e2;            // EPL complex ellipticity
+  float om1, op1;          // 1 - e1, 1 + e1
+  float t;                 // gamma - 1
+  float log2_thetaE;
+  float inv_1me2;          // 1 / (1 - |eps|^2)
+  float g1, g2;            // external shear
+  int nterms;              // series terms of F (0 <= N <= NMAX); < 0 marks an invalid vector
+  int nterms_adj;          // series terms of F, dF/du and dF/dt in the adjoint (1 <= N <= NMAX)
+  int pad_[3];
+  LightC light[2];         // [0] lens light at theta, [1] source at beta
+  float cn[NMAX];          // c_n, n = 1..N at index n-1
+  float cnt[NMAX];         // d c_n / d t
+};
+static_assert(sizeof(VecConst) % 16 == 0, "VecConst must be a whole number of 16-byte words");
+
+// One (system, batch) segment of a launch.
+struct Seg {
+  // resident system
+  const float* image;      // I_obs [H, W]
+  const float* sigma2;     // sigma_bkg^2 [H, W]
+  const float* psf;        // [K, K]
+  int H, W, K, k;
+  float sub;               // pixel_scale / k
+  float x0, y0;            // coordinates of supersampled pixel (0, 0)
+  float inv_gain;          // 1 / (G t_exp), 0 drops the Poisson term
+  // this call
+  const float* params;     // [B, 22]
+  int B;
+  int ntiles;              // ray tiles per vector
+  int tile_pix;            // detector pixels per ray tile
+  double* loglik;          // [B] or null
+  double* chi2;            // [B] or null
+  double* grad;            // [B, 22] or null
+  float* sim;              // [B, H, W] or null
+  // scratch
+  VecConst* vc;            // [B]
+  float* work;             // [B, H, W]: binned pre-PSF image, then the subpixel adjoint
+  double* partial;         // [B, ntiles, NACC]
+  // first item of this segment in the launch's item spaces
+  int vec_begin;           // per-vector kernels
+  int ray_begin;           // ray kernels (B * ntiles items)
+  int conv_begin;          // convolution kernel of this segment's PSF class
+};
+
+// ---------------------------------------------------------------- MUFU ----
+// Single hardware instructions of the special-function unit.
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ------------------------------------------------------------ forward -----
+
+// Elliptical Sersic at (px, py).
+__device__ __forceinline__ float sersic_fwd(const LightC& L, float px, float py) {
+  const float dx = px - L.x, dy = py - L.y;
+  float r2 = fmaf(L.A * dx, dx, fmaf(L.B2 * dx, dy, L.C * dy * dy));
+  r2 = fmaxf(r2, RHO2_MIN);
+  const float s = ex2(fmaf(L.c1, lg2(r2), L.c0));
+  return L.I0 * ex2(fmaf(-L.k1, s, L.k1));
+}
+
+// EPL deflection (complex, image frame) at (x, y); cn in shared memory.
+__device__ __forceinline__ void epl_fwd(const VecConst& V, const float* cn, float x, float y,
+                                        float& ax, float& ay) {
+  const float dx = x - V.xc, dy = y - V.yc;
+  const float wr = fmaf(V.om1, dx, -V.e2 * dy);
+  const float wi = fmaf(V.op1, dy, -V.e2 * dx);
+  const float w2 = fmaf(wr, wr, wi * wi);
+  const float r2 = w2 * V.inv_1me2;
+  if (r2 < RHO2_MIN) {
+    ax = 0.f;
+    ay = 0.f;
+    return;
+  }
+  const float S = ex2(V.t * fmaf(-0.5f, lg2(r2), V.log2_thetaE));
+  const float iw2 = rcp(w2);
+  const float vr = (wr * wr - wi * wi) * iw2;
+  const float vi = 2.f * wr * wi * iw2;
+  const float ur = -fmaf(V.e1, vr, V.e2 * vi);
+  const float ui = fmaf(V.e2, vr, -V.e1 * vi);
+  float hr = 1.f, hi = 0.f;
+  for (int n = V.nterms; n >= 1; --n) {
+    const float c = cn[n - 1];
+    const float tr = fmaf(ur, hr, -ui * hi);
+    const float ti = fmaf(ur, hi, ui * hr);
+    hr = fmaf(c, tr, 1.f);
+    hi = c * ti;
+  }
+  ax = S * fmaf(wr, hr, -wi * hi);
+  ay = S * fmaf(wr, hi, wi * hr);
+}
+
+// Surface brightness of one ray (lensed source + lens light).
+__device__ __forceinline__ float ray_intensity(const VecConst& V, const float* cn, float x, float y) {
+  float ax, ay;
+  epl_fwd(V, cn, x, y, ax, ay);
+  const float bx = x - ax - fmaf(V.g1, x, V.g2 * y);
+  const float by = y - ay - fmaf(V.g2, x, -V.g1 * y);
+  return sersic_fwd(V.light[1], bx, by) + sersic_fwd(V.light[0], x, y);
+}
+
+}  // namespace gl

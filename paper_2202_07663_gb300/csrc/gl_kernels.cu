@@ -1,0 +1,733 @@
+// gl_kernels.cu - sm_103a kernels of the batched lens likelihood and gradient.
+//
+// Launch sequence of one call (arXiv:2202.07663, Sec. 2.1.1 -> 2.1.2 -> 2.2):
+//   k_setup    per vector: FP64 derived constants (ellipticity forms, series
+//              coefficients, Sersic exponents) -> VecConst
+//   k_ray_fwd  per (vector, pixel tile): k x k rays per detector pixel, EPL +
+//              shear deflection, source and lens Sersic, k x k mean -> work
+//   k_conv     per vector: shared-memory PSF convolution of work, per-pixel
+//              Gaussian log-likelihood term, FP64 block reduction -> log L;
+//              for the gradient also the pixel adjoint d log L / d I_model,
+//              correlated with the PSF and divided by k^2 -> work
+//   k_ray_adj  per (vector, pixel tile): rays recomputed, forward-mode
+//              derivatives contracted with the subpixel adjoint -> partial
+//   k_final    per vector: fixed-order FP64 sum of the tile partials and the
+//              per-vector chain rule -> grad
+// Every kernel loops over its items with a grid stride, so the same code
+// serves one-system launches (one segment passed by value) and grouped
+// launches over many systems (segment table in device memory).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "gl_device.cuh"
+#include "gl_launch.h"
+
+namespace gl {
+
+// ------------------------------------------------------ segment sources ---
+
+struct OneSeg {
+  Seg s;
+  __device__ __forceinline__ int nvec() const { return s.B; }
+  __device__ __forceinline__ int nray() const { return s.B * s.ntiles; }
+  __device__ __forceinline__ int nconv() const { return s.B; }
+  __device__ __forceinline__ const Seg* vec_seg(int item, int& local) const { local = item; return &s; }
+  __device__ __forceinline__ const Seg* ray_seg(int item, int& local) const { local = item; return &s; }
+  __device__ __forceinline__ const Seg* conv_seg(int item, int& local) const { local = item; return &s; }
+};
+
+// Segments in device memory. The convolution kernel of one PSF class sees
+// the contiguous run [conv_first, conv_first + conv_nseg) of the table.
+struct SegTable {
+  const Seg* segs;   // device, sorted by PSF class, then vec_begin / ray_begin ascending
+  int nseg, vec_total, ray_total;
+  int conv_first, conv_nseg, conv_total;
+  __device__ __forceinline__ int nvec() const { return vec_total; }
+  __device__ __forceinline__ int nray() const { return ray_total; }
+  __device__ __forceinline__ int nconv() const { return conv_total; }
+  __device__ __forceinline__ const Seg* conv_seg(int item, int& local) const {
+    const Seg* c = segs + conv_first;
+    int lo = 0;
+    for (int i = 1; i < conv_nseg; ++i) lo = (c[i].conv_begin <= item) ? i : lo;
+    local = item - c[lo].conv_begin;
+    return c + lo;
+  }
+  __device__ __forceinline__ const Seg* vec_seg(int item, int& local) const {
+    int lo = 0;
+    for (int i = 1; i < nseg; ++i) lo = (segs[i].vec_begin <= item) ? i : lo;
+    local = item - segs[lo].vec_begin;
+    return segs + lo;
+  }
+  __device__ __forceinline__ const Seg* ray_seg(int item, int& local) const {
+    int lo = 0;
+    for (int i = 1; i < nseg; ++i) lo = (segs[i].ray_begin <= item) ? i : lo;
+    local = item - segs[lo].ray_begin;
+    return segs + lo;
+  }
+};
+
+// Copy a struct of 4-byte words into shared memory with the whole block.
+template <class T>
+__device__ __forceinline__ void block_copy(T* dst, const T* src) {
+  static_assert(sizeof(T) % 4 == 0, "word copy");
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < int(sizeof(T) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------- k_setup ----
+
+__device__ void setup_light(const double* p, LightC& L, bool& ok) {
+  const double R = p[0], n = p[1], e1 = p[2], e2 = p[3];
+  const double e2s = e1 * e1 + e2 * e2;
+  ok = ok && R > 0.0 && n > 0.0 && e2s < 1.0;
+  const double D = 1.0 - e2s, iD = 1.0 / D, iD2 = iD * iD;
+  L.A = float((1.0 + e2s - 2.0 * e1) * iD);
+  L.B2 = float(-4.0 * e2 * iD);
+  L.C = float((1.0 + e2s + 2.0 * e1) * iD);
+  L.x = float(p[4]);
+  L.y = float(p[5]);
+  L.c1 = float(0.5 / n);
+  L.c0 = float(-log2(R) / n);
+  const double bn = 1.9992 * n - 0.3271;
+  L.k1 = float(bn / 0.69314718055994530942);
+  L.I0 = float(p[6]);
+  // derivatives of (A, 2B, C) with respect to e1 and e2
+  L.A1 = float(2.0 * (e2 * e2 - (1.0 - e1) * (1.0 - e1)) * iD2);
+  L.B21 = float(-8.0 * e1 * e2 * iD2);
+  L.C1 = float(2.0 * ((1.0 + e1) * (1.0 + e1) - e2 * e2) * iD2);
+  L.A2 = float(4.0 * e2 * (1.0 - e1) * iD2);
+  L.B22 = float(-4.0 * (1.0 - e1 * e1 + e2 * e2) * iD2);
+  L.C2 = float(4.0 * e2 * (1.0 + e1) * iD2);
+}
+
+// Truncation target of the EPL series. The forward pass keeps the smallest N
+// with |F - F_N| <= f^(N+1)/(1-f) <= SERIES_TOL; the adjoint also needs
+// dF/du = sum n a_n u^(n-1), whose tail is <= (N+1) f^N/(1-f)^2, so it keeps
+// the smallest N >= 1 with that bound <= SERIES_TOL.
+constexpr double SERIES_TOL = 2e-8;
+
+// One warp per vector. GB300's FP64 rate is a small fraction of its FP32
+// rate, so the FP64 work is spread over lanes instead of repeated on each:
+// lanes 0..21 check one parameter each, lane 0 derives the EPL constants,
+// lanes 1 and 2 the two light profiles (FP64); all lanes compute series
+// coefficients and, by ballot, the two term counts (FP32 suffices for both).
+template <class Src>
+__global__ void k_setup(const __grid_constant__ Src src) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < src.nvec(); item += gridDim.x * wpb) {
+    int b;
+    const Seg* s = src.vec_seg(item, b);
+    VecConst* V = s->vc + b;
+    const float* pp = s->params + size_t(b) * NPARAM;
+    bool ok = lane >= NPARAM || isfinite(pp[lane]);
+    const float e1f = pp[2], e2f = pp[3], tf = pp[1] - 1.0f;
+    if (lane == 0) {
+      const double thetaE = pp[0], t = double(pp[1]) - 1.0, e1 = pp[2], e2 = pp[3];
+      const double e2s = e1 * e1 + e2 * e2;
+      ok = ok && thetaE > 0.0 && e2s < 1.0 && t > -1.0 && t < 3.0;
+      V->xc = pp[4];
+      V->yc = pp[5];
+      V->e1 = float(e1);
+      V->e2 = float(e2);
+      V->om1 = float(1.0 - e1);
+      V->op1 = float(1.0 + e1);
+      V->t = float(t);
+      V->log2_thetaE = float(log2(thetaE));
+      V->inv_1me2 = float(1.0 / (1.0 - e2s));
+      V->g1 = pp[6];
+      V->g2 = pp[7];
+    } else if (lane == 1 || lane == 2) {
+      double q[7];
+      for (int i = 0; i < 7; ++i) q[i] = pp[(lane == 1 ? 8 : 15) + i];
+      LightC L;
+      setup_light(q, L, ok);
+      V->light[lane - 1] = L;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    // term counts: lane tests N = lane + 1 and lane + 33 (adjoint), N = lane and lane + 32 (forward)
+    const float f = sqrtf(e1f * e1f + e2f * e2f);
+    const float lf = f > 0.f ? logf(f) : -1e30f;
+    const float l1f = log1pf(-fminf(f, 0.999999f));
+    const float ltol = logf(float(SERIES_TOL));
+    auto adj_ok = [&](int N) { return logf(float(N + 1)) + N * lf - 2.f * l1f <= ltol; };
+    auto fwd_ok = [&](int N) { return (N + 1) * lf - l1f <= ltol; };
+    const unsigned a_lo = __ballot_sync(0xffffffffu, adj_ok(lane + 1));
+    const unsigned a_hi = __ballot_sync(0xffffffffu, adj_ok(lane + 33));
+    const unsigned f_lo = __ballot_sync(0xffffffffu, fwd_ok(lane));
+    const unsigned f_hi = __ballot_sync(0xffffffffu, fwd_ok(lane + 32));
+    const int n_adj = a_lo ? __ffs(a_lo) : (a_hi ? 32 + __ffs(a_hi) : NMAX);
+    const int n_fwd = f_lo ? __ffs(f_lo) - 1 : (f_hi ? 32 + __ffs(f_hi) - 1 : NMAX);
+    for (int n = lane + 1; n <= NMAX; n += 32) {
+      const float den = 2.f * n + 2.f - tf;
+      const float iden = 1.0f / den;
+      V->cn[n - 1] = (2.f * n - 2.f + tf) * iden;
+      V->cnt[n - 1] = 4.f * n * iden * iden;
+    }
+    if (lane == 0) {
+      V->nterms = ok ? min(n_fwd, NMAX) : -1;
+      V->nterms_adj = min(max(n_adj, 1), NMAX);
+    }
+  }
+}
+
+// ----------------------------------------------------------- k_ray_fwd ----
+
+template <class Src>
+__global__ void __launch_bounds__(RAY_THREADS) k_ray_fwd(const __grid_constant__ Src src) {
+  __shared__ VecConst sv;
+  __shared__ Seg ss;
+  for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
+    int local;
+    const Seg* sp = src.ray_seg(item, local);
+    block_copy(&ss, sp);
+    __syncthreads();
+    const int b = local / ss.ntiles, tile = local - b * ss.ntiles;
+    block_copy(&sv, ss.vc + b);
+    __syncthreads();
+    const int HW = ss.H * ss.W, W = ss.W, k = ss.k;
+    const int p0 = tile * ss.tile_pix;
+    const int p1 = min(HW, p0 + ss.tile_pix);
+    const float inv_k2 = 1.0f / float(k * k);
+    const bool valid = sv.nterms >= 0;
+    float* out = ss.work + size_t(b) * HW;
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      const int i = p / W, j = p - i * W;
+      float acc = 0.f;
+      if (valid) {
+        for (int a = 0; a < k; ++a) {
+          const float y = fmaf(float(i * k + a), ss.sub, ss.y0);
+          for (int c = 0; c < k; ++c) {
+            const float x = fmaf(float(j * k + c), ss.sub, ss.x0);
+            acc += ray_intensity(sv, sv.cn, x, y);
+          }
+        }
+        acc *= inv_k2;
+      } else {
+        acc = __int_as_float(0x7fc00000);
+      }
+      out[p] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------- k_ray_adj -----
+
+// Lens or source light: accumulates R, n (two terms), e1, e2, x, y, I0 slots
+// and returns (Gx, Gy) = s I / rho^2 (A dx + B dy, B dx + C dy), so that
+// dI/d(centre) = (b_n/n) (Gx, Gy) and dI/d(position) = -(b_n/n) (Gx, Gy).
+__device__ __forceinline__ void light_adj(const LightC& L, float px, float py, float g, float* acc,
+                                          float& Gx, float& Gy) {
+  const float dx = px - L.x, dy = py - L.y;
+  const float dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
+  float r2 = fmaf(L.A, dxx, fmaf(L.B2, dxy, L.C * dyy));
+  const bool floored = r2 < RHO2_MIN;
+  r2 = fmaxf(r2, RHO2_MIN);
+  const float ls = fmaf(L.c1, lg2(r2), L.c0);
+  const float s = ex2(ls);
+  const float e = ex2(fmaf(-L.k1, s, L.k1));
+  const float I = L.I0 * e;
+  const float hI = g * I;
+  const float hs = hI * s;
+  acc[0] += hs;
+  acc[1] = fmaf(hI, s - 1.f, acc[1]);
+  acc[2] = fmaf(hs, ls, acc[2]);
+  const float q = floored ? 0.f : s * I * rcp(r2);
+  const float Bh = 0.5f * L.B2;
+  Gx = q * fmaf(L.A, dx, Bh * dy);
+  Gy = q * fmaf(Bh, dx, L.C * dy);
+  const float gq = g * q;
+  acc[3] = fmaf(gq, fmaf(L.A1, dxx, fmaf(L.B21, dxy, L.C1 * dyy)), acc[3]);
+  acc[4] = fmaf(gq, fmaf(L.A2, dxx, fmaf(L.B22, dxy, L.C2 * dyy)), acc[4]);
+  acc[5] = fmaf(g, Gx, acc[5]);
+  acc[6] = fmaf(g, Gy, acc[6]);
+  acc[7] = fmaf(g, e, acc[7]);
+}
+
+// One ray: adds g x (derivatives of its intensity) to the 24 accumulators.
+__device__ __forceinline__ void ray_adj(const VecConst& V, const float* cn, const float* cnt, float x, float y,
+                                        float g, float* acc) {
+  float Gx, Gy;
+  light_adj(V.light[0], x, y, g, acc + A_L_R, Gx, Gy);
+
+  // EPL deflection with the pieces of its parameter derivatives
+  const float dx = x - V.xc, dy = y - V.yc;
+  const float wr = fmaf(V.om1, dx, -V.e2 * dy);
+  const float wi = fmaf(V.op1, dy, -V.e2 * dx);
+  const float w2 = fmaf(wr, wr, wi * wi);
+  const float r2 = w2 * V.inv_1me2;
+  const bool inside = r2 < RHO2_MIN;
+  float ar = 0.f, ai = 0.f;
+  // d alpha / d (t, e1, e2, xc, yc), complex; d/d thetaE = (t/thetaE) alpha
+  float dtr = 0.f, dti = 0.f, d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
+  float dxr = 0.f, dxi = 0.f, dyr = 0.f, dyi = 0.f;
+  if (!inside) {
+    const float lrho = fmaf(-0.5f, lg2(r2), V.log2_thetaE);  // log2(thetaE / rho)
+    const float S = ex2(V.t * lrho);
+    const float iw2 = rcp(w2);
+    const float vr = (wr * wr - wi * wi) * iw2;
+    const float vi = 2.f * wr * wi * iw2;
+    const float ur = -fmaf(V.e1, vr, V.e2 * vi);
+    const float ui = fmaf(V.e2, vr, -V.e1 * vi);
+    // Horner for F, dF/du and dF/dt
+    float hr = 1.f, hi = 0.f, pr = 0.f, pi = 0.f, tr = 0.f, ti = 0.f;
+    for (int n = V.nterms_adj; n >= 1; --n) {
+      const float c = cn[n - 1], ct = cnt[n - 1];
+      const float uhr = fmaf(ur, hr, -ui * hi), uhi = fmaf(ur, hi, ui * hr);
+      const float upr = fmaf(ur, pr, -ui * pi), upi = fmaf(ur, pi, ui * pr);
+      const float utr = fmaf(ur, tr, -ui * ti), uti = fmaf(ur, ti, ui * tr);
+      pr = c * (hr + upr);
+      pi = c * (hi + upi);
+      tr = fmaf(ct, uhr, c * utr);
+      ti = fmaf(ct, uhi, c * uti);
+      hr = fmaf(c, uhr, 1.f);
+      hi = c * uhi;
+    }
+    const float swr = S * wr, swi = S * wi;     // S w
+    ar = fmaf(swr, hr, -swi * hi);
+    ai = fmaf(swr, hi, swi * hr);
+    // t: alpha ln(thetaE/rho) + S w dF/dt
+    const float lnr = 0.69314718f * lrho;
+    dtr = fmaf(ar, lnr, fmaf(swr, tr, -swi * ti));
+    dti = fmaf(ai, lnr, fmaf(swr, ti, swi * tr));
+    // e1, e2
+    const float Pr = fmaf(wr, dx, -wi * dy), Pi = fmaf(wr, dy, wi * dx);   // w z
+    const float a1 = V.t * fmaf(Pr, iw2, -V.e1 * V.inv_1me2);             // d ln S / d e1
+    const float a2 = V.t * fmaf(Pi, iw2, -V.e2 * V.inv_1me2);             // d ln S / d e2
+    const float sfr = S * hr, sfi = S * hi;                                // S F
+    const float swpr = fmaf(swr, pr, -swi * pi), swpi = fmaf(swr, pi, swi * pr);  // S w F'
+    const float k1 = 2.f * Pi * iw2, k2 = 2.f * Pr * iw2;
+    const float du1r = fmaf(-k1, ui, -vr), du1i = fmaf(k1, ur, -vi);      // du/de1 = -V + i k1 u
+    const float du2r = fmaf(k2, ui, -vi), du2i = fmaf(-k2, ur, vr);       // du/de2 = iV - i k2 u
+    // dw/de1 = (-dx, dy), dw/de2 = (-dy, -dx)
+    d1r = fmaf(ar, a1, fmaf(sfr, -dx, -sfi * dy)) + fmaf(swpr, du1r, -swpi * du1i);
+    d1i = fmaf(ai, a1, fmaf(sfr, dy, sfi * -dx)) + fmaf(swpr, du1i, swpi * du1r);
+    d2r = fmaf(ar, a2, fmaf(sfr, -dy, sfi * dx)) + fmaf(swpr, du2r, -swpi * du2i);
+    d2i = fmaf(ai, a2, fmaf(sfr, -dx, sfi * -dy)) + fmaf(swpr, du2i, swpi * du2r);
+    // centre: kappa and shear of the EPL from homogeneity, z kappa + conj(z) gamma = (1-t) alpha
+    const float kap = 0.5f * (2.f - V.t) * S;
+    const float iz2 = rcp(fmaf(dx, dx, dy * dy));
+    const float Qr = fmaf(1.f - V.t, ar, -kap * dx), Qi = fmaf(1.f - V.t, ai, -kap * dy);
+    const float gr = fmaf(Qr, dx, -Qi * dy) * iz2, gi = fmaf(Qr, dy, Qi * dx) * iz2;   // Q z / |z|^2
+    dxr = -(kap + gr);
+    dxi = -gi;
+    dyr = -gi;
+    dyi = -(kap - gr);
+  }
+  // lens equation with external shear, source at beta
+  const float bx = x - ar - fmaf(V.g1, x, V.g2 * y);
+  const float by = y - ai - fmaf(V.g2, x, -V.g1 * y);
+  light_adj(V.light[1], bx, by, g, acc + A_S_R, Gx, Gy);
+  // mass: g Ghat . d alpha / d p  (times b_s/n_s in the chain rule)
+  const float gx = g * Gx, gy = g * Gy;
+  acc[A_THETAE] = fmaf(gx, ar, fmaf(gy, ai, acc[A_THETAE]));
+  acc[A_T] = fmaf(gx, dtr, fmaf(gy, dti, acc[A_T]));
+  acc[A_E1] = fmaf(gx, d1r, fmaf(gy, d1i, acc[A_E1]));
+  acc[A_E2] = fmaf(gx, d2r, fmaf(gy, d2i, acc[A_E2]));
+  acc[A_XC] = fmaf(gx, dxr, fmaf(gy, dxi, acc[A_XC]));
+  acc[A_YC] = fmaf(gx, dyr, fmaf(gy, dyi, acc[A_YC]));
+  acc[A_G1] = fmaf(gx, x, fmaf(-gy, y, acc[A_G1]));
+  acc[A_G2] = fmaf(gx, y, fmaf(gy, x, acc[A_G2]));
+}
+
+template <class Src>
+__global__ void __launch_bounds__(RAY_THREADS) k_ray_adj(const __grid_constant__ Src src) {
+  __shared__ VecConst sv;
+  __shared__ Seg ss;
+  __shared__ double red[RAY_THREADS / 32][NACC];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
+    int local;
+    const Seg* sp = src.ray_seg(item, local);
+    block_copy(&ss, sp);
+    __syncthreads();
+    const int b = local / ss.ntiles, tile = local - b * ss.ntiles;
+    block_copy(&sv, ss.vc + b);
+    __syncthreads();
+    float acc[NACC];
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
+    const int HW = ss.H * ss.W, W = ss.W, k = ss.k;
+    const int p0 = tile * ss.tile_pix;
+    const int p1 = min(HW, p0 + ss.tile_pix);
+    const float* gpre = ss.work + size_t(b) * HW;
+    if (sv.nterms >= 0) {
+      for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const int i = p / W, j = p - i * W;
+        const float g = gpre[p];
+        for (int a = 0; a < k; ++a) {
+          const float y = fmaf(float(i * k + a), ss.sub, ss.y0);
+          for (int c = 0; c < k; ++c) {
+            const float x = fmaf(float(j * k + c), ss.sub, ss.x0);
+            ray_adj(sv, sv.cn, sv.cnt, x, y, g, acc);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) {
+      const double v = warp_sum(double(acc[a]));
+      if (lane == 0) red[warp][a] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NACC) {
+      double v = 0.0;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+      ss.partial[(size_t(b) * ss.ntiles + tile) * NACC + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// -------------------------------------------------------------- k_conv ----
+
+// out(i, j) = sum_{a,b} ker[a K + b] in[(i + a) Wp + j + b] for the R rows
+// i = i0 .. i0 + R - 1 of column j. The kernel column sits in registers and
+// every input value is read once per kernel column.
+template <int K, int R>
+__device__ __forceinline__ void corr_strip(const float* in, int Wp, const float* ker, int i0, int j, float* acc) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.f;
+  const float* base = in + i0 * Wp + j;
+#pragma unroll 1
+  for (int b = 0; b < K; ++b) {
+    float kc[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) kc[a] = ker[a * K + b];
+    const float* col = base + b;
+#pragma unroll
+    for (int ii = 0; ii < R + K - 1; ++ii) {
+      const float v = col[ii * Wp];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int a = ii - r;
+        if (a >= 0 && a < K) acc[r] = fmaf(kc[a], v, acc[r]);
+      }
+    }
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void corr_strip_any(const float* in, int Wp, const float* ker, int K, int i0, int j,
+                                               float* acc) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.f;
+  const float* base = in + i0 * Wp + j;
+  for (int b = 0; b < K; ++b) {
+    const float* col = base + b;
+    for (int ii = 0; ii < R + K - 1; ++ii) {
+      const float v = col[ii * Wp];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int a = ii - r;
+        if (a >= 0 && a < K) acc[r] = fmaf(ker[a * K + b], v, acc[r]);
+      }
+    }
+  }
+}
+
+// One vector: image in shared memory (zero halo), PSF flipped for the
+// convolution, then (gradient) the adjoint correlated with the unflipped PSF.
+// K > 0: compile-time PSF side; K == 0: any odd side (s.K).
+template <int K, int R>
+__device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* red2) {
+  const int Kk = K > 0 ? K : s.K;
+  const int H = s.H, W = s.W, HW = H * W;
+  const int nstrip = (H + R - 1) / R;
+  const int Hp = nstrip * R + Kk - 1, Wp = W + Kk - 1;
+  const int c = (Kk - 1) / 2;
+  float* ker = smem;
+  float* img = smem + ((Kk * Kk + 3) & ~3);
+  float* work = s.work + size_t(b) * HW;
+  const bool want_sim = (mode == MODE_SIM);
+  const bool want_grad = (mode == MODE_GRAD);
+
+  for (int i = threadIdx.x; i < Kk * Kk; i += blockDim.x) ker[i] = s.psf[Kk * Kk - 1 - i];  // flipped
+  for (int i = threadIdx.x; i < Hp * Wp; i += blockDim.x) img[i] = 0.f;
+  __syncthreads();
+  for (int p = threadIdx.x; p < HW; p += blockDim.x) {
+    const int i = p / W, j = p - i * W;
+    img[(i + c) * Wp + j + c] = work[p];
+  }
+  __syncthreads();
+
+  double ll = 0.0, c2 = 0.0;
+  const int units = nstrip * W;
+  float acc[R];
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int strip = u / W, j = u - strip * W;
+    const int i0 = strip * R;
+    if (K > 0) corr_strip<(K > 0 ? K : 1), R>(img, Wp, ker, i0, j, acc);
+    else corr_strip_any<R>(img, Wp, ker, Kk, i0, j, acc);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = i0 + r;
+      if (i < H) {
+        const int p = i * W + j;
+        const float M = acc[r];
+        if (want_sim) {
+          s.sim[size_t(b) * HW + p] = M;
+        } else {
+          const float v = fmaf(M, s.inv_gain, s.sigma2[p]);
+          const float res = s.image[p] - M;
+          const float iv = 1.0f / v;
+          const float t2 = res * res * iv;
+          c2 += double(t2);
+          ll += double(t2) + double(logf(6.28318530717958648f * v));
+          if (want_grad) {
+            // d log L / d M = res/v + (res^2/v^2 - 1/v) / (2 G t_exp)
+            const float gm = fmaf(0.5f * s.inv_gain, fmaf(t2, iv, -iv), res * iv);
+            work[p] = gm;
+          }
+        }
+      }
+    }
+  }
+  if (!want_sim) {
+    ll = warp_sum(ll);
+    c2 = warp_sum(c2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      red2[2 * warp] = ll;
+      red2[2 * warp + 1] = c2;
+    }
+  }
+  __syncthreads();
+  if (!want_sim && threadIdx.x == 0) {
+    double L = 0.0, C = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      L += red2[2 * w];
+      C += red2[2 * w + 1];
+    }
+    if (s.loglik) s.loglik[b] = -0.5 * L;
+    if (s.chi2) s.chi2[b] = C;
+  }
+  if (!want_grad) return;
+
+  // adjoint: gpre = (PSF correlated with dlogL/dM) / k^2
+  for (int i = threadIdx.x; i < Kk * Kk; i += blockDim.x) ker[i] = s.psf[i];
+  for (int p = threadIdx.x; p < HW; p += blockDim.x) {
+    const int i = p / W, j = p - i * W;
+    img[(i + c) * Wp + j + c] = work[p];
+  }
+  __syncthreads();
+  const float inv_k2 = 1.0f / float(s.k * s.k);
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int strip = u / W, j = u - strip * W;
+    const int i0 = strip * R;
+    if (K > 0) corr_strip<(K > 0 ? K : 1), R>(img, Wp, ker, i0, j, acc);
+    else corr_strip_any<R>(img, Wp, ker, Kk, i0, j, acc);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = i0 + r;
+      if (i < H) work[i * W + j] = acc[r] * inv_k2;
+    }
+  }
+}
+
+template <int K, int R, int NT, class Src>
+__global__ void __launch_bounds__(NT) k_conv(const __grid_constant__ Src src, int mode) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  __shared__ double red2[2 * (NT / 32)];
+  __shared__ Seg ss;
+  for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x) {
+    int b;
+    const Seg* sp = src.conv_seg(item, b);
+    block_copy(&ss, sp);
+    __syncthreads();
+    conv_vector<K, R>(ss, b, mode, smem, red2);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- k_final ----
+
+template <class Src>
+__global__ void k_final(const __grid_constant__ Src src) {
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < src.nvec(); item += gridDim.x * blockDim.x) {
+    int b;
+    const Seg* s = src.vec_seg(item, b);
+    double* g = s->grad + size_t(b) * NPARAM;
+    if (s->vc[b].nterms < 0) {
+      for (int i = 0; i < NPARAM; ++i) g[i] = nan("");
+      continue;
+    }
+    double a[NACC];
+    for (int i = 0; i < NACC; ++i) a[i] = 0.0;
+    const double* part = s->partial + size_t(b) * s->ntiles * NACC;
+    for (int t = 0; t < s->ntiles; ++t)
+      for (int i = 0; i < NACC; ++i) a[i] += part[t * NACC + i];
+    double p[NPARAM];
+    for (int i = 0; i < NPARAM; ++i) p[i] = double(s->params[size_t(b) * NPARAM + i]);
+    const double ln2 = 0.69314718055994530942;
+    const double bs = 1.9992 * p[16] - 0.3271, ms = bs / p[16];   // b_n / n of the source
+    g[0] = ms * (p[1] - 1.0) / p[0] * a[A_THETAE];
+    g[1] = ms * a[A_T];
+    g[2] = ms * a[A_E1];
+    g[3] = ms * a[A_E2];
+    g[4] = ms * a[A_XC];
+    g[5] = ms * a[A_YC];
+    g[6] = ms * a[A_G1];
+    g[7] = ms * a[A_G2];
+    for (int l = 0; l < 2; ++l) {
+      const double* q = p + (l == 0 ? 8 : 15);
+      const double* c = a + (l == 0 ? A_L_R : A_S_R);
+      double* o = g + (l == 0 ? 8 : 15);
+      const double bn = 1.9992 * q[1] - 0.3271, m = bn / q[1];
+      o[0] = m / q[0] * c[0];
+      o[1] = -1.9992 * c[1] + m * ln2 * c[2];
+      o[2] = -0.5 * m * c[3];
+      o[3] = -0.5 * m * c[4];
+      o[4] = m * c[5];
+      o[5] = m * c[6];
+      o[6] = c[7];
+    }
+  }
+}
+
+// ------------------------------------------------------------- launch -----
+
+static int g_num_sms = 0;
+
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+// Convolution classes: (PSF side, strip rows, threads). Class 2 takes any odd side.
+struct ConvClass {
+  int K, R, NT;
+};
+static constexpr ConvClass kConvClasses[3] = {{11, 16, 128}, {21, 16, 256}, {0, 8, 128}};
+
+int conv_class(int K) { return K == 11 ? 0 : (K == 21 ? 1 : 2); }
+
+size_t conv_smem_bytes(int H, int W, int K) {
+  const int R = kConvClasses[conv_class(K)].R;
+  const int nstrip = (H + R - 1) / R;
+  const size_t Hp = size_t(nstrip) * R + K - 1, Wp = size_t(W) + K - 1;
+  return (size_t((K * K + 3) & ~3) + Hp * Wp) * sizeof(float);
+}
+
+void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix) {
+  const int HW = H * W;
+  const long long rays = (long long)HW * k * k;
+  const int target = num_sms() * 8;
+  long long nt = B > 0 ? (target + B - 1) / B : 1;
+  const long long by_work = (rays + RAY_THREADS * 8 - 1) / (RAY_THREADS * 8);  // >= 8 rays per thread
+  if (nt > by_work) nt = by_work;
+  if (nt < 1) nt = 1;
+  if (nt > HW) nt = HW;
+  int tp = int((HW + nt - 1) / nt);
+  *tile_pix = tp;
+  *ntiles = (HW + tp - 1) / tp;
+}
+
+template <int K, int R, int NT, class Src>
+static cudaError_t launch_conv(const Src& src, int nitems, size_t smem, int mode, cudaStream_t st, bool persistent) {
+  static size_t attr = 48 * 1024;
+  if (smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv<K, R, NT, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  int grid = nitems;
+  if (persistent) grid = grid < num_sms() * 4 ? grid : num_sms() * 4;
+  k_conv<K, R, NT, Src><<<grid, NT, smem, st>>>(src, mode);
+  return cudaSuccess;
+}
+
+template <class Src>
+static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t smem, int mode, cudaStream_t st,
+                                     bool persistent) {
+  switch (cls) {
+    case 0: return launch_conv<11, 16, 128>(src, nitems, smem, mode, st, persistent);
+    case 1: return launch_conv<21, 16, 256>(src, nitems, smem, mode, st, persistent);
+    default: return launch_conv<0, 8, 128>(src, nitems, smem, mode, st, persistent);
+  }
+}
+
+template <class Src>
+static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj_final, cudaStream_t st,
+                            Hooks* hooks, bool persistent) {
+  const int sms = num_sms();
+  cudaError_t e;
+  const int vthreads = 128, wpb = vthreads / 32;
+  int sgrid = (nvec + wpb - 1) / wpb;
+  int fgrid = (nvec + vthreads - 1) / vthreads;
+  int rgrid = nray;
+  if (persistent) {
+    sgrid = sgrid < sms * 4 ? sgrid : sms * 4;
+    fgrid = fgrid < sms ? fgrid : sms;
+    rgrid = rgrid < sms * 4 ? rgrid : sms * 4;
+  }
+  if (fwd) {
+    hooks->before(GL_K_SETUP, st);
+    k_setup<Src><<<sgrid, vthreads, 0, st>>>(src);
+    if ((e = hooks->after(GL_K_SETUP, st)) != cudaSuccess) return e;
+    hooks->before(GL_K_RAY_FWD, st);
+    k_ray_fwd<Src><<<rgrid, RAY_THREADS, 0, st>>>(src);
+    return hooks->after(GL_K_RAY_FWD, st);
+  }
+  if (adj_final) {
+    hooks->before(GL_K_RAY_ADJ, st);
+    k_ray_adj<Src><<<rgrid, RAY_THREADS, 0, st>>>(src);
+    if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
+    hooks->before(GL_K_FINAL, st);
+    k_final<Src><<<fgrid, vthreads, 0, st>>>(src);
+    return hooks->after(GL_K_FINAL, st);
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
+  if (s.B <= 0) return cudaSuccess;
+  OneSeg src{s};
+  cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false);
+  if (e != cudaSuccess) return e;
+  hooks->before(GL_K_CONV, st);
+  e = launch_conv_class(conv_class(s.K), src, s.B, conv_smem_bytes(s.H, s.W, s.K), mode, st, false);
+  if (e != cudaSuccess) return e;
+  if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
+  if (mode != MODE_GRAD) return cudaSuccess;
+  return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false);
+}
+
+cudaError_t launch_table(const Seg* d_segs, int nseg, int vec_total, int ray_total, const ConvRun* conv, int nconv,
+                         int mode, cudaStream_t st, Hooks* hooks) {
+  if (vec_total <= 0) return cudaSuccess;
+  SegTable src{d_segs, nseg, vec_total, ray_total, 0, nseg, vec_total};
+  cudaError_t e = run_rays(src, vec_total, ray_total, true, false, st, hooks, true);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < nconv; ++i) {
+    SegTable cs = src;
+    cs.conv_first = conv[i].first;
+    cs.conv_nseg = conv[i].nseg;
+    cs.conv_total = conv[i].nitems;
+    hooks->before(GL_K_CONV, st);
+    e = launch_conv_class(conv[i].cls, cs, conv[i].nitems, conv[i].smem, mode, st, true);
+    if (e != cudaSuccess) return e;
+    if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
+  }
+  if (mode != MODE_GRAD) return cudaSuccess;
+  return run_rays(src, vec_total, ray_total, false, true, st, hooks, true);
+}
+
+}  // namespace gl

@@ -1,0 +1,48 @@
+// gl_launch.h - host-side launch interface between the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "../../include/gigalens.h"
+
+namespace gl {
+
+struct Seg;
+
+enum Mode { MODE_SIM = 0, MODE_LOGLIK = 1, MODE_GRAD = 2 };
+
+// Called around every kernel launch: instrumentation and error checks.
+struct Hooks {
+  virtual void before(int kind, cudaStream_t st) = 0;
+  virtual cudaError_t after(int kind, cudaStream_t st) = 0;
+  virtual ~Hooks() = default;
+};
+
+// Dynamic shared memory of the convolution stage for an H x W image, K x K PSF.
+size_t conv_smem_bytes(int H, int W, int K);
+
+// Convolution kernel class of a PSF side (0: K = 11, 1: K = 21, 2: any other odd K).
+int conv_class(int K);
+constexpr int CONV_CLASSES = 3;
+
+// One convolution launch of a grouped call: segments [first, first + nseg) of
+// the (class-sorted) table, nitems vectors, dynamic shared memory smem.
+struct ConvRun {
+  int cls, first, nseg, nitems;
+  size_t smem;
+};
+
+// Split each vector's detector pixels into ray tiles for a batch of B.
+void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix);
+
+// One segment, passed by value.
+cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks);
+
+// Segments in device memory, sorted by convolution class (grouped launch;
+// persistent grids); one convolution launch per ConvRun.
+cudaError_t launch_table(const Seg* d_segs, int nseg, int vec_total, int ray_total, const ConvRun* conv, int nconv,
+                         int mode, cudaStream_t st, Hooks* hooks);
+
+}  // namespace gl

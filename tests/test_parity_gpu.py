@@ -1,0 +1,228 @@
+"""GPU (CUDA, FP32 + FP64 reductions) vs FP64 oracle, element by element.
+
+Every case builds its observed image with the oracle, evaluates the same
+float32 inputs on both sides and compares with the tolerances of
+``gpu_common``. Cases span several ray tiles with ragged tails, the
+benchmark's launch configuration (60x60, k=2, 11x11 PSF, B=4096) on sampled
+vectors, the larger workloads on sampled vectors, and the degenerate inputs.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2202_07663_gb300 import inputs  # noqa: E402
+from gpu_common import assert_parity, conditioned_bound, make_system, oracle_eval  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def abi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_07663_gb300 import build, abi as _abi
+    build.build()
+    oracle.build()
+    return _abi
+
+
+def _gpu(abi, spec, image, psf, params, grad=True):
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    p = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+    if grad:
+        ll, g = s.loglik_grad(p)
+        out = ll.cpu().numpy(), g.cpu().numpy()
+    else:
+        out = s.loglik(p).cpu().numpy(), None
+    s.close()
+    return out
+
+
+def test_config1_plain_b64(abi):
+    """60x60, k=2, 11x11 Gaussian PSF; 64 perturbed vectors; all compared."""
+    spec = inputs.CONFIGS[1]["spec"]
+    truth, image, psf = make_system(spec, 1000)
+    params = inputs.draw_perturbed(np.random.default_rng(1), truth, 64).astype(np.float32)
+    ll, g = _gpu(abi, spec, image, psf, params)
+    rl, _, rg = oracle_eval(spec, image, psf, params)
+    assert_parity(ll, g, rl, rg, "config 1")
+
+
+def test_near_truth_gradient(abi):
+    """Vectors 0.1% of the box from the truth: residuals are noise and the
+    gradient is a near-cancelling pixel sum, so the FP32 model error bound
+    eps * C_i is added to the gradient tolerance."""
+    spec = inputs.CONFIGS[1]["spec"]
+    truth, image, psf = make_system(spec, 1001)
+    params = inputs.draw_perturbed(np.random.default_rng(2), truth, 8, frac=0.001).astype(np.float32)
+    params[0] = truth.astype(np.float32)
+    ll, g = _gpu(abi, spec, image, psf, params)
+    rl, _, rg = oracle_eval(spec, image, psf, params)
+    assert_parity(ll, g, rl, rg, "near truth", extra=conditioned_bound(spec, image, psf, params))
+
+
+def test_simulate_matches_oracle(abi):
+    spec = inputs.SystemSpec(37, 29, 3, 7, "moffat")
+    truth, image, psf = make_system(spec, 7)
+    params = inputs.draw_perturbed(np.random.default_rng(3), truth, 5).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    m = s.simulate(torch.from_numpy(params).cuda()).cpu().numpy()
+    s.close()
+    ref = oracle.simulate(params.astype(np.float64), spec.H, spec.W, psf, spec.pixel_scale, spec.k)
+    tol = 1e-4 * np.abs(ref) + 1e-5 * np.abs(ref).max()
+    assert np.all(np.abs(m - ref) <= tol), np.max(np.abs(m - ref) / tol)
+
+
+@pytest.mark.parametrize("H,W,k,K,B", [
+    (1, 1, 1, 1, 1), (2, 3, 1, 3, 2), (3, 3, 2, 3, 3), (5, 7, 3, 5, 1), (17, 13, 2, 3, 5),
+    (33, 31, 1, 11, 3), (45, 64, 3, 21, 2), (16, 16, 4, 9, 4), (61, 59, 2, 11, 7)])
+def test_shapes_and_ragged_tiles(abi, H, W, k, K, B):
+    spec = inputs.SystemSpec(H, W, k, K, "gaussian")
+    truth, image, psf = make_system(spec, 100 + H * W + k + K)
+    params = inputs.draw_perturbed(np.random.default_rng(H + W), truth, B).astype(np.float32)
+    ll, g = _gpu(abi, spec, image, psf, params)
+    rl, _, rg = oracle_eval(spec, image, psf, params)
+    assert_parity(ll, g, rl, rg, "%dx%d k=%d K=%d" % (H, W, k, K))
+
+
+def test_no_poisson_term_and_pixel_noise_map(abi):
+    spec = inputs.SystemSpec(30, 26, 2, 5, "gaussian", gain_exposure=0.0)
+    truth, image, psf = make_system(spec, 11)
+    sigma = np.random.default_rng(5).uniform(0.005, 0.05, image.shape).astype(np.float32)
+    params = inputs.draw_perturbed(np.random.default_rng(6), truth, 6).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, 0.0, noise_map=sigma)
+    ll, g = s.loglik_grad(torch.from_numpy(params).cuda())
+    s.close()
+    rl, _, rg = oracle.loglik(params.astype(np.float64), image, sigma, psf, spec.pixel_scale, spec.k, 0.0, grad=True)
+    assert_parity(ll.cpu().numpy(), g.cpu().numpy(), rl, rg, "no Poisson, noise map")
+
+
+def test_zero_ellipticity(abi):
+    """e = 0 exactly for all three profiles: log L against the oracle at e = 0,
+    gradient against the oracle at |e| = 1e-9 (the model is smooth in e)."""
+    spec = inputs.SystemSpec(32, 32, 2, 5, "gaussian")
+    truth, image, psf = make_system(spec, 12)
+    params = inputs.draw_perturbed(np.random.default_rng(8), truth, 4).astype(np.float32)
+    for j in (2, 3, 10, 11, 17, 18):
+        params[:, j] = 0.0
+    ll, g = _gpu(abi, spec, image, psf, params)
+    rl, _, _ = oracle_eval(spec, image, psf, params, grad=False)
+    near = params.astype(np.float64)
+    for j in (2, 10, 17):
+        near[:, j] = 1e-9
+    _, _, rg = oracle.loglik(near, image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k,
+                             spec.gain_exposure, grad=True)
+    assert_parity(ll, g, rl, rg, "e = 0")
+
+
+def test_lens_centre_on_a_ray(abi):
+    """The EPL centre exactly on a subpixel centre (rho = 0): deflection zero there."""
+    spec = inputs.SystemSpec(9, 9, 1, 3, "gaussian")
+    truth, image, psf = make_system(spec, 13)
+    p = truth.astype(np.float32)[None, :].repeat(2, 0)
+    p[:, 4] = 0.0
+    p[:, 5] = 0.0
+    p[1, 4] = np.float32(spec.pixel_scale)
+    ll, g = _gpu(abi, spec, image, psf, p)
+    rl, _, rg = oracle_eval(spec, image, psf, p)
+    # a 9 x 9 cut-out around the lens-light cusp: add the FP32 model error bound
+    assert_parity(ll, g, rl, rg, "centre on a ray", extra=conditioned_bound(spec, image, psf, p))
+
+
+def test_invalid_vectors_give_nan_and_leave_others(abi):
+    spec = inputs.SystemSpec(20, 20, 2, 5, "gaussian")
+    truth, image, psf = make_system(spec, 14)
+    p = inputs.draw_perturbed(np.random.default_rng(9), truth, 6).astype(np.float32)
+    p[1, 3] = np.nan        # non-finite
+    p[2, 2] = 1.2           # |e_epl| >= 1
+    p[3, 8] = -0.5          # R_l <= 0
+    p[4, 16] = 0.0          # n_s <= 0
+    ll, g = _gpu(abi, spec, image, psf, p)
+    assert np.all(np.isnan(ll[1:5])) and np.all(np.isnan(g[1:5]))
+    good = [0, 5]
+    rl, _, rg = oracle_eval(spec, image, psf, p[good])
+    assert_parity(ll[good], g[good], rl, rg, "valid neighbours")
+
+
+def test_batch_zero_and_argument_errors(abi):
+    spec = inputs.SystemSpec(10, 10, 1, 3, "gaussian")
+    _, image, psf = make_system(spec, 15)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    ll, g = s.loglik_grad(torch.empty(0, 22, device="cuda"))
+    assert ll.shape == (0,) and g.shape == (0, 22)
+    lib = abi.lib_handle()
+    assert lib.gl_loglik(s.handle, None, 3, None, None, None) == -1
+    assert lib.gl_loglik(s.handle, 8, -1, 8, None, None) == -1
+    assert lib.gl_loglik_grad(None, 8, 1, 8, None, 8, None) == -1
+    s.close()
+    with pytest.raises(abi.GLError):
+        abi.GLSystem(image, np.ones((4, 4), np.float32), spec.pixel_scale, 1, 1000.0, sigma_bkg=0.01)
+    with pytest.raises(abi.GLError):
+        abi.GLSystem(image, psf, spec.pixel_scale, 0, 1000.0, sigma_bkg=0.01)
+    with pytest.raises(abi.GLError):
+        abi.GLSystem(image, psf, spec.pixel_scale, 1, 1000.0, sigma_bkg=0.0)
+    with pytest.raises(abi.GLError):  # too large for the shared-memory convolution stage
+        abi.GLSystem(np.zeros((400, 400), np.float32), psf, spec.pixel_scale, 1, 1000.0, sigma_bkg=0.01)
+
+
+def test_deterministic_and_host_path(abi):
+    spec = inputs.CONFIGS[1]["spec"]
+    truth, image, psf = make_system(spec, 16)
+    params = inputs.draw_perturbed(np.random.default_rng(10), truth, 40).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    p = torch.from_numpy(params).cuda()
+    a = [t.cpu().numpy() for t in s.loglik_grad(p)]
+    b = [t.cpu().numpy() for t in s.loglik_grad(p)]
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    hl = np.empty(40)
+    hg = np.empty((40, 22))
+    s.loglik_grad_host(params, hl, hg)
+    np.testing.assert_array_equal(hl, a[0])
+    np.testing.assert_array_equal(hg, a[1])
+    ll_only = s.loglik(p).cpu().numpy()
+    np.testing.assert_array_equal(ll_only, a[0])
+    s.close()
+
+
+def test_grouped_launch_equals_single_calls(abi):
+    specs = [inputs.SystemSpec(40, 40, 2, 11), inputs.SystemSpec(25, 31, 4, 21), inputs.SystemSpec(18, 18, 1, 5)]
+    systems, params, singles = [], [], []
+    for i, spec in enumerate(specs):
+        truth, image, psf = make_system(spec, 200 + i)
+        s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+        p = torch.from_numpy(inputs.draw_perturbed(np.random.default_rng(i), truth, 10 + 7 * i).astype(np.float32)).cuda()
+        systems.append(s)
+        params.append(p)
+        singles.append([t.cpu().numpy() for t in s.loglik_grad(p)])
+    lls, grads, _ = abi.loglik_grad_grouped(systems, params)
+    for (sl, sg), ll, g in zip(singles, lls, grads):
+        np.testing.assert_array_equal(ll.cpu().numpy(), sl)
+        np.testing.assert_array_equal(g.cpu().numpy(), sg)
+    lls2, grads2, _ = abi.loglik_grad_grouped(systems, params, grad=False)
+    for (sl, _), ll in zip(singles, lls2):
+        np.testing.assert_array_equal(ll.cpu().numpy(), sl)
+    for s in systems:
+        s.close()
+
+
+@pytest.mark.parametrize("cfg,nsample", [(2, 24), (3, 3), (5, 2)])
+def test_full_size_configs_sampled(abi, cfg, nsample):
+    """Full batch sizes in the launch configuration of the benchmark; the oracle
+    checks a seeded sample of the vectors one by one."""
+    c = inputs.CONFIGS[cfg]
+    spec, B = c["spec"], c["B"]
+    truth, image, psf = make_system(spec, cfg * 1000)
+    rng = np.random.default_rng(cfg)
+    if c["draw"] == "box":
+        params = inputs.draw_box(rng, B).astype(np.float32)
+    else:
+        params = inputs.draw_perturbed(rng, truth, B).astype(np.float32)
+    ll, g = _gpu(abi, spec, image, psf, params)
+    assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
+    idx = np.sort(rng.choice(B, nsample, replace=False))
+    idx[-1] = B - 1  # include the last vector of the batch
+    rl, _, rg = oracle_eval(spec, image, psf, params[idx])
+    assert_parity(ll[idx], g[idx], rl, rg, "config %d sample" % cfg)
