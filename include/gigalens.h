@@ -160,6 +160,33 @@ int gl_loglik_grad_grouped(gl_system* const* systems, const float* const* params
                            double* const* loglik_out, double* const* chi2_out, double* const* grad_out, int n,
                            void* stream);
 
+/*
+ * gl_loglik_grad_noalloc - gl_loglik_grad for callers that cannot allocate
+ * device memory while they evaluate the likelihood: code running inside an
+ * allocator or memory-pool callback, processes whose device memory is
+ * entirely held by another framework's caching allocator, and hosts that
+ * forbid allocation after start-up. The paper has no counterpart; it is a
+ * deployment variant of the same computation.
+ *
+ * Arguments, results and errors are those of gl_loglik_grad. The call
+ * allocates nothing: the kernels' scratch (per-vector constants, image work
+ * buffer, per-tile gradient partials) lives in one static device array of
+ * 32 MiB (33,554,432 bytes), which every GPU that loads
+ * the library holds until the process exits. A batch whose scratch does not
+ * fit is rejected with GL_ERR_INVALID_ARG before anything is launched (about
+ * 2,000 vectors of a 60 x 60 image; scratch per vector is roughly
+ * 4*H*W + 800 bytes).
+ *
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call shares the one array and leaves its
+ * contents behind; nothing in it has to start at zero. Calls whose kernels
+ * overlap on the GPU (two streams, or two host threads) race on the array:
+ * issue them on one stream.
+ */
+int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* loglik_out, double* chi2_out,
+                           double* grad_out, void* stream);
+
 /* Name of a status code (static string). */
 const char* gl_error_string(int code);
 

@@ -44,6 +44,7 @@ SIGNATURES = {
     "gl_loglik_grad_host": ([_vp, _vp, _i, _vp, _vp, _vp, _vp], _i),
     "gl_simulate": ([_vp, _vp, _i, _vp, _vp], _i),
     "gl_loglik_grad_grouped": ([_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
+    "gl_loglik_grad_noalloc": ([_vp, _vp, _i, _vp, _vp, _vp, _vp], _i),
     "gl_error_string": ([_i], ctypes.c_char_p),
     "gl_last_error_message": ([], ctypes.c_char_p),
     "gl_profile_enable": ([_i], _i),

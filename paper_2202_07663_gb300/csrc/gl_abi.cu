@@ -205,6 +205,26 @@ int run_one(gl_system* s, const float* params, int B, double* ll, double* c2, do
 
 }  // namespace
 
+// Internal helpers for other translation units of the library (not ABI).
+namespace gl_internal {
+
+// Segment of a call on sys with every scratch pointer left null.
+gl::Seg seg_without_scratch(const gl_system* s, const float* params, int B) {
+  Seg g = make_seg(s, params, B);
+  g.vc = nullptr;
+  g.work = nullptr;
+  g.partial = nullptr;
+  return g;
+}
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+int cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+gl::Hooks* hooks() { return &g_prof; }
+
+}  // namespace gl_internal
+
 extern "C" {
 
 int gl_system_create(gl_system** out, const float* image, const float* noise_map, float sigma_bkg, int H, int W,

@@ -1,0 +1,23 @@
+// gl_internal.h - helpers shared between the library's translation units (not ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gl_device.cuh"
+#include "gl_launch.h"
+
+struct gl_system;
+
+namespace gl_internal {
+
+// Segment of a call on sys (system data, tile plan) with null scratch pointers.
+gl::Seg seg_without_scratch(const gl_system* s, const float* params, int B);
+
+// Record the calling thread's error message and return code.
+int set_error(int code, const char* msg);
+int cuda_error(cudaError_t e, const char* what);
+
+// Launch hooks of the library (launch counting, optional event timing).
+gl::Hooks* hooks();
+
+}  // namespace gl_internal
