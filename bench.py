@@ -48,7 +48,7 @@ def flops_ray_fwd(N):
 
 
 def flops_ray_adj(N):
-    return 306 + 31 * N
+    return 318 + 21 * N
 
 
 def flops_conv_pixel(K, grad):
@@ -62,17 +62,16 @@ NMAX = 64
 def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
     """Per-vector EPL series length, the rules the setup kernel applies:
     forward  smallest N >= 0 with f^(N+1)/(1-f) <= tol,
-    adjoint  smallest N >= 1 with (N+1) f^N/(1-f)^2 <= tol."""
+    adjoint  the same N, at least 1."""
     f = np.hypot(params[:, 2].astype(np.float64), params[:, 3].astype(np.float64))
     N = np.arange(0, NMAX + 1)[None, :]
     with np.errstate(divide="ignore"):
         lf = np.where(f > 0, np.log(np.maximum(f, 1e-300)), -1e300)[:, None]
     l1f = np.log1p(-np.minimum(f, 0.999999))[:, None]
-    if adjoint:
-        good = (np.log(N + 1.0) + N * lf - 2 * l1f <= np.log(SERIES_TOL)) & (N >= 1)
-    else:
-        good = (N + 1) * lf - l1f <= np.log(SERIES_TOL)
+    good = (N + 1) * lf - l1f <= np.log(SERIES_TOL)
     first = np.where(good.any(axis=1), good.argmax(axis=1), NMAX)
+    if adjoint:
+        first = np.maximum(first, 1)
     return first.astype(np.int64)
 
 

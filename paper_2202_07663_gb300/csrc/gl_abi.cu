@@ -176,6 +176,7 @@ Seg make_seg(const gl_system* s, const float* params, int B) {
   g.vc = s->d_vc;
   g.work = s->d_work;
   g.partial = s->d_partial;
+  g.conv_two_buf = gl::conv_two_buf(s->H, s->W, s->K) ? 1 : 0;
   return g;
 }
 
@@ -255,7 +256,7 @@ int gl_system_create(gl_system** out, const float* image, const float* noise_map
   }
   int dev = 0;
   GL_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
-  const size_t smem = gl::conv_smem_bytes(H, W, K) + CONV_STATIC_SMEM;
+  const size_t smem = gl::conv_smem_bytes(H, W, K, false) + CONV_STATIC_SMEM;
   if (smem > size_t(max_smem_optin(dev)))
     return fail(GL_ERR_UNSUPPORTED, "padded %dx%d image with K=%d needs %zu B of shared memory (> %d)", H, W, K,
                 smem, max_smem_optin(dev));
@@ -438,7 +439,7 @@ int gl_loglik_grad_grouped(gl_system* const* systems, const float* const* params
       vec_total += sg.B;
       ray_total += sg.B * sg.ntiles;
       r.nitems += sg.B;
-      const size_t sm = gl::conv_smem_bytes(sg.H, sg.W, sg.K);
+      const size_t sm = gl::conv_smem_bytes(sg.H, sg.W, sg.K, sg.conv_two_buf != 0);
       r.smem = sm > r.smem ? sm : r.smem;
       segs.push_back(sg);
     }

@@ -71,8 +71,13 @@ struct __align__(16) VecConst {
   float inv_1me2;          // 1 / (1 - |eps|^2)
   float g1, g2;            // external shear
   int nterms;              // series terms of F (0 <= N <= NMAX); < 0 marks an invalid vector
-  int nterms_adj;          // series terms of F, dF/du and dF/dt in the adjoint (1 <= N <= NMAX)
-  int pad_[3];
+  int nterms_adj;          // series terms in the adjoint, max(N, 1)
+  float th;                // t / 2
+  float kc;                // (1 - t/2) c_1, for dF/du = [(t/2) F - (1 - t/2) c_1 h_1] / (1 - u)
+  float kap_c;             // (2 - t) / 2: kappa = kap_c (thetaE/rho)^t
+  float omt;               // 1 - t
+  float e1i, e2i;          // e1, e2 times 1 / (1 - |eps|^2)
+  float pad_[3];
   LightC light[2];         // [0] lens light at theta, [1] source at beta
   float cn[NMAX];          // c_n, n = 1..N at index n-1
   float cnt[NMAX];         // d c_n / d t
@@ -106,6 +111,7 @@ struct Seg {
   int vec_begin;           // per-vector kernels
   int ray_begin;           // ray kernels (B * ntiles items)
   int conv_begin;          // convolution kernel of this segment's PSF class
+  int conv_two_buf;        // 1: pixel adjoint kept in a second shared-memory buffer
 };
 
 // ---------------------------------------------------------------- MUFU ----
@@ -124,6 +130,89 @@ __device__ __forceinline__ float rcp(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+
+// --------------------------------------------------------- packed pairs ---
+// Two rays of one parameter vector evaluated in lockstep with Blackwell's
+// packed FP32 instructions (one f32x2 FMA/MUL/ADD does the arithmetic of two
+// rays in one issue slot). The ray kernels are issue-bound, so pairing rays
+// halves the issue cost of their FP32 arithmetic. Special-function (MUFU)
+// instructions and comparisons act on each half.
+struct F2 {
+  float2 v;
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a) { return {__fmul2_rn(a.v, make_float2(-1.f, -1.f))}; }
+
+template <class T> __device__ __forceinline__ T sp(float a);
+template <> __device__ __forceinline__ float sp<float>(float a) { return a; }
+template <> __device__ __forceinline__ F2 sp<F2>(float a) { return {make_float2(a, a)}; }
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ F2 fmaT(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ float ex2T(float a) { return ex2(a); }
+__device__ __forceinline__ F2 ex2T(F2 a) { return {make_float2(ex2(a.v.x), ex2(a.v.y))}; }
+__device__ __forceinline__ float lg2T(float a) { return lg2(a); }
+__device__ __forceinline__ F2 lg2T(F2 a) { return {make_float2(lg2(a.v.x), lg2(a.v.y))}; }
+__device__ __forceinline__ float rcpT(float a) { return rcp(a); }
+__device__ __forceinline__ F2 rcpT(F2 a) { return {make_float2(rcp(a.v.x), rcp(a.v.y))}; }
+__device__ __forceinline__ float maxT(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ F2 maxT(F2 a, F2 b) { return {make_float2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y))}; }
+// 1 where a >= b, else 0
+__device__ __forceinline__ float geT(float a, float b) { return a >= b ? 1.f : 0.f; }
+__device__ __forceinline__ F2 geT(F2 a, F2 b) {
+  return {make_float2(a.v.x >= b.v.x ? 1.f : 0.f, a.v.y >= b.v.y ? 1.f : 0.f)};
+}
+
+// Elliptical Sersic at (px, py), generic in the ray type.
+template <class T>
+__device__ __forceinline__ T sersic_fwd_T(const LightC& L, T px, T py) {
+  const T dx = px - sp<T>(L.x), dy = py - sp<T>(L.y);
+  T r2 = fmaT(sp<T>(L.A) * dx, dx, fmaT(sp<T>(L.B2) * dx, dy, sp<T>(L.C) * dy * dy));
+  r2 = maxT(r2, sp<T>(RHO2_MIN));
+  const T s = ex2T(fmaT(sp<T>(L.c1), lg2T(r2), sp<T>(L.c0)));
+  return sp<T>(L.I0) * ex2T(fmaT(sp<T>(-L.k1), s, sp<T>(L.k1)));
+}
+
+// EPL deflection, generic in the ray type. A ray inside rho < 1e-6 arcsec gets
+// zero deflection (mask), computed without a branch so pairs stay in lockstep.
+template <class T>
+__device__ __forceinline__ void epl_fwd_T(const VecConst& V, const float* cn, T x, T y, T& ax, T& ay) {
+  const T dx = x - sp<T>(V.xc), dy = y - sp<T>(V.yc);
+  const T wr = fmaT(sp<T>(V.om1), dx, sp<T>(-V.e2) * dy);
+  const T wi = fmaT(sp<T>(V.op1), dy, sp<T>(-V.e2) * dx);
+  const T w2 = fmaT(wr, wr, wi * wi);
+  const T r2raw = w2 * sp<T>(V.inv_1me2);
+  const T keep = geT(r2raw, sp<T>(RHO2_MIN));
+  const T r2 = maxT(r2raw, sp<T>(RHO2_MIN));
+  const T S = keep * ex2T(sp<T>(V.t) * fmaT(sp<T>(-0.5f), lg2T(r2), sp<T>(V.log2_thetaE)));
+  const T iw2 = rcpT(maxT(w2, sp<T>(1e-30f)));
+  const T vr = fmaT(wr, wr, -(wi * wi)) * iw2;
+  const T vi = sp<T>(2.f) * wr * wi * iw2;
+  const T ur = -fmaT(sp<T>(V.e1), vr, sp<T>(V.e2) * vi);
+  const T ui = fmaT(sp<T>(V.e2), vr, sp<T>(-V.e1) * vi);
+  T hr = sp<T>(1.f), hi = sp<T>(0.f);
+#pragma unroll 2
+  for (int n = V.nterms; n >= 1; --n) {
+    const T c = sp<T>(cn[n - 1]);
+    const T tr = fmaT(ur, hr, -(ui * hi));
+    const T ti = fmaT(ur, hi, ui * hr);
+    hr = fmaT(c, tr, sp<T>(1.f));
+    hi = c * ti;
+  }
+  ax = S * fmaT(wr, hr, -(wi * hi));
+  ay = S * fmaT(wr, hi, wi * hr);
+}
+
+template <class T>
+__device__ __forceinline__ T ray_intensity_T(const VecConst& V, const float* cn, T x, T y) {
+  T ax, ay;
+  epl_fwd_T(V, cn, x, y, ax, ay);
+  const T bx = x - ax - fmaT(sp<T>(V.g1), x, sp<T>(V.g2) * y);
+  const T by = y - ay - fmaT(sp<T>(V.g2), x, sp<T>(-V.g1) * y);
+  return sersic_fwd_T(V.light[1], bx, by) + sersic_fwd_T(V.light[0], x, y);
 }
 
 // ------------------------------------------------------------ forward -----

@@ -109,17 +109,17 @@ __device__ void setup_light(const double* p, LightC& L, bool& ok) {
   L.C2 = float(4.0 * e2 * (1.0 + e1) * iD2);
 }
 
-// Truncation target of the EPL series. The forward pass keeps the smallest N
-// with |F - F_N| <= f^(N+1)/(1-f) <= SERIES_TOL; the adjoint also needs
-// dF/du = sum n a_n u^(n-1), whose tail is <= (N+1) f^N/(1-f)^2, so it keeps
-// the smallest N >= 1 with that bound <= SERIES_TOL.
+// Truncation target of the EPL series: the smallest N with
+// |F - F_N| <= f^(N+1)/(1-f) <= SERIES_TOL. The adjoint uses the same N (at
+// least 1): its dF/du comes from F and h_1 in closed form, and the tail of
+// dF/dt exceeds that of F only by a logarithmic factor.
 constexpr double SERIES_TOL = 2e-8;
 
 // One warp per vector. GB300's FP64 rate is a small fraction of its FP32
 // rate, so the FP64 work is spread over lanes instead of repeated on each:
 // lanes 0..21 check one parameter each, lane 0 derives the EPL constants,
 // lanes 1 and 2 the two light profiles (FP64); all lanes compute series
-// coefficients and, by ballot, the two term counts (FP32 suffices for both).
+// coefficients and, by ballot, the term count (FP32 suffices for both).
 template <class Src>
 __global__ void k_setup(const __grid_constant__ Src src) {
   const int lane = threadIdx.x & 31;
@@ -146,6 +146,12 @@ __global__ void k_setup(const __grid_constant__ Src src) {
       V->inv_1me2 = float(1.0 / (1.0 - e2s));
       V->g1 = pp[6];
       V->g2 = pp[7];
+      V->th = float(0.5 * t);
+      V->kc = float((1.0 - 0.5 * t) * t / (4.0 - t));
+      V->kap_c = float(0.5 * (2.0 - t));
+      V->omt = float(1.0 - t);
+      V->e1i = float(e1 / (1.0 - e2s));
+      V->e2i = float(e2 / (1.0 - e2s));
     } else if (lane == 1 || lane == 2) {
       double q[7];
       for (int i = 0; i < 7; ++i) q[i] = pp[(lane == 1 ? 8 : 15) + i];
@@ -154,18 +160,14 @@ __global__ void k_setup(const __grid_constant__ Src src) {
       V->light[lane - 1] = L;
     }
     ok = __all_sync(0xffffffffu, ok);
-    // term counts: lane tests N = lane + 1 and lane + 33 (adjoint), N = lane and lane + 32 (forward)
+    // term count: lane tests N = lane and N = lane + 32
     const float f = sqrtf(e1f * e1f + e2f * e2f);
     const float lf = f > 0.f ? logf(f) : -1e30f;
     const float l1f = log1pf(-fminf(f, 0.999999f));
     const float ltol = logf(float(SERIES_TOL));
-    auto adj_ok = [&](int N) { return logf(float(N + 1)) + N * lf - 2.f * l1f <= ltol; };
     auto fwd_ok = [&](int N) { return (N + 1) * lf - l1f <= ltol; };
-    const unsigned a_lo = __ballot_sync(0xffffffffu, adj_ok(lane + 1));
-    const unsigned a_hi = __ballot_sync(0xffffffffu, adj_ok(lane + 33));
     const unsigned f_lo = __ballot_sync(0xffffffffu, fwd_ok(lane));
     const unsigned f_hi = __ballot_sync(0xffffffffu, fwd_ok(lane + 32));
-    const int n_adj = a_lo ? __ffs(a_lo) : (a_hi ? 32 + __ffs(a_hi) : NMAX);
     const int n_fwd = f_lo ? __ffs(f_lo) - 1 : (f_hi ? 32 + __ffs(f_hi) - 1 : NMAX);
     for (int n = lane + 1; n <= NMAX; n += 32) {
       const float den = 2.f * n + 2.f - tf;
@@ -175,7 +177,7 @@ __global__ void k_setup(const __grid_constant__ Src src) {
     }
     if (lane == 0) {
       V->nterms = ok ? min(n_fwd, NMAX) : -1;
-      V->nterms_adj = min(max(n_adj, 1), NMAX);
+      V->nterms_adj = max(min(n_fwd, NMAX), 1);
     }
   }
 }
@@ -188,8 +190,8 @@ __global__ void __launch_bounds__(RAY_THREADS) k_ray_fwd(const __grid_constant__
   __shared__ Seg ss;
   for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
     int local;
-    const Seg* sp = src.ray_seg(item, local);
-    block_copy(&ss, sp);
+    const Seg* segp = src.ray_seg(item, local);
+    block_copy(&ss, segp);
     __syncthreads();
     const int b = local / ss.ntiles, tile = local - b * ss.ntiles;
     block_copy(&sv, ss.vc + b);
@@ -200,22 +202,29 @@ __global__ void __launch_bounds__(RAY_THREADS) k_ray_fwd(const __grid_constant__
     const float inv_k2 = 1.0f / float(k * k);
     const bool valid = sv.nterms >= 0;
     float* out = ss.work + size_t(b) * HW;
-    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-      const int i = p / W, j = p - i * W;
-      float acc = 0.f;
+    // two pixels per thread and step (p and p + blockDim), their rays paired in f32x2
+    const int stride = blockDim.x;
+    for (int p = p0 + threadIdx.x; p < p1; p += 2 * stride) {
+      const int q = p + stride;
+      const bool has_q = q < p1;
+      const int qq = has_q ? q : p;
+      const int ip = p / W, jp = p - ip * W;
+      const int iq = qq / W, jq = qq - iq * W;
+      F2 acc = sp<F2>(0.f);
       if (valid) {
         for (int a = 0; a < k; ++a) {
-          const float y = fmaf(float(i * k + a), ss.sub, ss.y0);
+          const F2 y = {make_float2(fmaf(float(ip * k + a), ss.sub, ss.y0), fmaf(float(iq * k + a), ss.sub, ss.y0))};
           for (int c = 0; c < k; ++c) {
-            const float x = fmaf(float(j * k + c), ss.sub, ss.x0);
-            acc += ray_intensity(sv, sv.cn, x, y);
+            const F2 x = {make_float2(fmaf(float(jp * k + c), ss.sub, ss.x0), fmaf(float(jq * k + c), ss.sub, ss.x0))};
+            acc = acc + ray_intensity_T(sv, sv.cn, x, y);
           }
         }
-        acc *= inv_k2;
+        acc = acc * sp<F2>(inv_k2);
       } else {
-        acc = __int_as_float(0x7fc00000);
+        acc = sp<F2>(__int_as_float(0x7fc00000));
       }
-      out[p] = acc;
+      out[p] = acc.v.x;
+      if (has_q) out[q] = acc.v.y;
     }
     __syncthreads();
   }
@@ -279,20 +288,32 @@ __device__ __forceinline__ void ray_adj(const VecConst& V, const float* cn, cons
     const float vi = 2.f * wr * wi * iw2;
     const float ur = -fmaf(V.e1, vr, V.e2 * vi);
     const float ui = fmaf(V.e2, vr, -V.e1 * vi);
-    // Horner for F, dF/du and dF/dt
-    float hr = 1.f, hi = 0.f, pr = 0.f, pi = 0.f, tr = 0.f, ti = 0.f;
-    for (int n = V.nterms_adj; n >= 1; --n) {
+    // Horner for F and dF/dt down to h_1, then the last step (n = 1)
+    float hr = 1.f, hi = 0.f, tr = 0.f, ti = 0.f;
+    for (int n = V.nterms_adj; n >= 2; --n) {
       const float c = cn[n - 1], ct = cnt[n - 1];
       const float uhr = fmaf(ur, hr, -ui * hi), uhi = fmaf(ur, hi, ui * hr);
-      const float upr = fmaf(ur, pr, -ui * pi), upi = fmaf(ur, pi, ui * pr);
       const float utr = fmaf(ur, tr, -ui * ti), uti = fmaf(ur, ti, ui * tr);
-      pr = c * (hr + upr);
-      pi = c * (hi + upi);
       tr = fmaf(ct, uhr, c * utr);
       ti = fmaf(ct, uhi, c * uti);
       hr = fmaf(c, uhr, 1.f);
       hi = c * uhi;
     }
+    const float c1 = cn[0], ct1 = cnt[0];
+    const float h1r = hr, h1i = hi;
+    {
+      const float uhr = fmaf(ur, hr, -ui * hi), uhi = fmaf(ur, hi, ui * hr);
+      const float utr = fmaf(ur, tr, -ui * ti), uti = fmaf(ur, ti, ui * tr);
+      tr = fmaf(ct1, uhr, c1 * utr);
+      ti = fmaf(ct1, uhi, c1 * uti);
+      hr = fmaf(c1, uhr, 1.f);
+      hi = c1 * uhi;
+    }
+    // dF/du = [(t/2) F - (1 - t/2) c_1 h_1] / (1 - u)   (Gauss contiguous relation)
+    const float nr = fmaf(V.th, hr, -V.kc * h1r), ni = fmaf(V.th, hi, -V.kc * h1i);
+    const float dr = 1.f - ur, di = -ui;
+    const float idd = rcp(fmaf(dr, dr, di * di));
+    const float pr = fmaf(nr, dr, ni * di) * idd, pi = fmaf(ni, dr, -nr * di) * idd;
     const float swr = S * wr, swi = S * wi;     // S w
     ar = fmaf(swr, hr, -swi * hi);
     ai = fmaf(swr, hi, swi * hr);
@@ -302,8 +323,8 @@ __device__ __forceinline__ void ray_adj(const VecConst& V, const float* cn, cons
     dti = fmaf(ai, lnr, fmaf(swr, ti, swi * tr));
     // e1, e2
     const float Pr = fmaf(wr, dx, -wi * dy), Pi = fmaf(wr, dy, wi * dx);   // w z
-    const float a1 = V.t * fmaf(Pr, iw2, -V.e1 * V.inv_1me2);             // d ln S / d e1
-    const float a2 = V.t * fmaf(Pi, iw2, -V.e2 * V.inv_1me2);             // d ln S / d e2
+    const float a1 = V.t * fmaf(Pr, iw2, -V.e1i);                          // d ln S / d e1
+    const float a2 = V.t * fmaf(Pi, iw2, -V.e2i);                          // d ln S / d e2
     const float sfr = S * hr, sfi = S * hi;                                // S F
     const float swpr = fmaf(swr, pr, -swi * pi), swpi = fmaf(swr, pi, swi * pr);  // S w F'
     const float k1 = 2.f * Pi * iw2, k2 = 2.f * Pr * iw2;
@@ -315,9 +336,9 @@ __device__ __forceinline__ void ray_adj(const VecConst& V, const float* cn, cons
     d2r = fmaf(ar, a2, fmaf(sfr, -dy, sfi * dx)) + fmaf(swpr, du2r, -swpi * du2i);
     d2i = fmaf(ai, a2, fmaf(sfr, -dx, sfi * -dy)) + fmaf(swpr, du2i, swpi * du2r);
     // centre: kappa and shear of the EPL from homogeneity, z kappa + conj(z) gamma = (1-t) alpha
-    const float kap = 0.5f * (2.f - V.t) * S;
+    const float kap = V.kap_c * S;
     const float iz2 = rcp(fmaf(dx, dx, dy * dy));
-    const float Qr = fmaf(1.f - V.t, ar, -kap * dx), Qi = fmaf(1.f - V.t, ai, -kap * dy);
+    const float Qr = fmaf(V.omt, ar, -kap * dx), Qi = fmaf(V.omt, ai, -kap * dy);
     const float gr = fmaf(Qr, dx, -Qi * dy) * iz2, gi = fmaf(Qr, dy, Qi * dx) * iz2;   // Q z / |z|^2
     dxr = -(kap + gr);
     dxi = -gi;
@@ -348,8 +369,8 @@ __global__ void __launch_bounds__(RAY_THREADS) k_ray_adj(const __grid_constant__
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
     int local;
-    const Seg* sp = src.ray_seg(item, local);
-    block_copy(&ss, sp);
+    const Seg* segp = src.ray_seg(item, local);
+    block_copy(&ss, segp);
     __syncthreads();
     const int b = local / ss.ntiles, tile = local - b * ss.ntiles;
     block_copy(&sv, ss.vc + b);
@@ -374,10 +395,13 @@ __global__ void __launch_bounds__(RAY_THREADS) k_ray_adj(const __grid_constant__
         }
       }
     }
+    // pairwise FP32 sums within the warp (GB300's FP64 pipe is narrow), FP64 across warps
 #pragma unroll
     for (int a = 0; a < NACC; ++a) {
-      const double v = warp_sum(double(acc[a]));
-      if (lane == 0) red[warp][a] = v;
+      float v = acc[a];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][a] = double(v);
     }
     __syncthreads();
     if (threadIdx.x < NACC) {
@@ -436,8 +460,20 @@ __device__ __forceinline__ void corr_strip_any(const float* in, int Wp, const fl
   }
 }
 
-// One vector: image in shared memory (zero halo), PSF flipped for the
-// convolution, then (gradient) the adjoint correlated with the unflipped PSF.
+// Columns per strip row of work units: a multiple of 32, so that a warp's
+// lanes read 32 consecutive shared-memory words of one image row.
+__device__ __forceinline__ int conv_row_units(int W) { return (W + 31) & ~31; }
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One vector. Shared memory: PSF flipped (convolution) and as given
+// (correlation), the zero-padded binned image and, when it fits
+// (s.conv_two_buf), a second zero-padded buffer for the pixel adjoint;
+// otherwise the adjoint goes through this vector's global work slot.
 // K > 0: compile-time PSF side; K == 0: any odd side (s.K).
 template <int K, int R>
 __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* red2) {
@@ -446,29 +482,40 @@ __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* 
   const int nstrip = (H + R - 1) / R;
   const int Hp = nstrip * R + Kk - 1, Wp = W + Kk - 1;
   const int c = (Kk - 1) / 2;
-  float* ker = smem;
-  float* img = smem + ((Kk * Kk + 3) & ~3);
+  const int K2 = (Kk * Kk + 3) & ~3;
+  float* kerF = smem;
+  float* kerU = smem + K2;
+  float* img = smem + 2 * K2;
+  float* img2 = img + Hp * Wp;
   float* work = s.work + size_t(b) * HW;
   const bool want_sim = (mode == MODE_SIM);
   const bool want_grad = (mode == MODE_GRAD);
+  const bool two = want_grad && s.conv_two_buf;
 
-  for (int i = threadIdx.x; i < Kk * Kk; i += blockDim.x) ker[i] = s.psf[Kk * Kk - 1 - i];  // flipped
-  for (int i = threadIdx.x; i < Hp * Wp; i += blockDim.x) img[i] = 0.f;
+  for (int i = threadIdx.x; i < Kk * Kk; i += blockDim.x) {
+    kerF[i] = s.psf[Kk * Kk - 1 - i];
+    kerU[i] = s.psf[i];
+  }
+  const int nz = (two ? 2 : 1) * Hp * Wp;
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) img[i] = 0.f;
   __syncthreads();
+#pragma unroll 4
   for (int p = threadIdx.x; p < HW; p += blockDim.x) {
     const int i = p / W, j = p - i * W;
     img[(i + c) * Wp + j + c] = work[p];
   }
   __syncthreads();
 
-  double ll = 0.0, c2 = 0.0;
-  const int units = nstrip * W;
+  float ll = 0.f, c2 = 0.f;
+  const int Wr = conv_row_units(W);
+  const int units = nstrip * Wr;
   float acc[R];
   for (int u = threadIdx.x; u < units; u += blockDim.x) {
-    const int strip = u / W, j = u - strip * W;
+    const int strip = u / Wr, j = u - strip * Wr;
+    if (j >= W) continue;
     const int i0 = strip * R;
-    if (K > 0) corr_strip<(K > 0 ? K : 1), R>(img, Wp, ker, i0, j, acc);
-    else corr_strip_any<R>(img, Wp, ker, Kk, i0, j, acc);
+    if (K > 0) corr_strip<(K > 0 ? K : 1), R>(img, Wp, kerF, i0, j, acc);
+    else corr_strip_any<R>(img, Wp, kerF, Kk, i0, j, acc);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = i0 + r;
@@ -482,24 +529,26 @@ __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* 
           const float res = s.image[p] - M;
           const float iv = 1.0f / v;
           const float t2 = res * res * iv;
-          c2 += double(t2);
-          ll += double(t2) + double(logf(6.28318530717958648f * v));
+          c2 += t2;
+          ll += t2 + logf(6.28318530717958648f * v);
           if (want_grad) {
             // d log L / d M = res/v + (res^2/v^2 - 1/v) / (2 G t_exp)
             const float gm = fmaf(0.5f * s.inv_gain, fmaf(t2, iv, -iv), res * iv);
-            work[p] = gm;
+            if (two) img2[(i + c) * Wp + j + c] = gm;
+            else work[p] = gm;
           }
         }
       }
     }
   }
   if (!want_sim) {
-    ll = warp_sum(ll);
-    c2 = warp_sum(c2);
+    // FP32 within a thread (a few tens of pixels) and a warp (pairwise), FP64 across warps
+    ll = warp_sum_f(ll);
+    c2 = warp_sum_f(c2);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-      red2[2 * warp] = ll;
-      red2[2 * warp + 1] = c2;
+      red2[2 * warp] = double(ll);
+      red2[2 * warp + 1] = double(c2);
     }
   }
   __syncthreads();
@@ -515,18 +564,23 @@ __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* 
   if (!want_grad) return;
 
   // adjoint: gpre = (PSF correlated with dlogL/dM) / k^2
-  for (int i = threadIdx.x; i < Kk * Kk; i += blockDim.x) ker[i] = s.psf[i];
-  for (int p = threadIdx.x; p < HW; p += blockDim.x) {
-    const int i = p / W, j = p - i * W;
-    img[(i + c) * Wp + j + c] = work[p];
+  float* gsrc = img2;
+  if (!two) {
+#pragma unroll 4
+    for (int p = threadIdx.x; p < HW; p += blockDim.x) {
+      const int i = p / W, j = p - i * W;
+      img[(i + c) * Wp + j + c] = work[p];
+    }
+    __syncthreads();
+    gsrc = img;
   }
-  __syncthreads();
   const float inv_k2 = 1.0f / float(s.k * s.k);
   for (int u = threadIdx.x; u < units; u += blockDim.x) {
-    const int strip = u / W, j = u - strip * W;
+    const int strip = u / Wr, j = u - strip * Wr;
+    if (j >= W) continue;
     const int i0 = strip * R;
-    if (K > 0) corr_strip<(K > 0 ? K : 1), R>(img, Wp, ker, i0, j, acc);
-    else corr_strip_any<R>(img, Wp, ker, Kk, i0, j, acc);
+    if (K > 0) corr_strip<(K > 0 ? K : 1), R>(gsrc, Wp, kerU, i0, j, acc);
+    else corr_strip_any<R>(gsrc, Wp, kerU, Kk, i0, j, acc);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = i0 + r;
@@ -535,16 +589,16 @@ __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* 
   }
 }
 
-template <int K, int R, int NT, class Src>
-__global__ void __launch_bounds__(NT) k_conv(const __grid_constant__ Src src, int mode) {
+template <int K, int R, int NT, int MINB, class Src>
+__global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src src, int mode) {
   extern __shared__ float4 smem4[];
   float* smem = reinterpret_cast<float*>(smem4);
   __shared__ double red2[2 * (NT / 32)];
   __shared__ Seg ss;
   for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x) {
     int b;
-    const Seg* sp = src.conv_seg(item, b);
-    block_copy(&ss, sp);
+    const Seg* segp = src.conv_seg(item, b);
+    block_copy(&ss, segp);
     __syncthreads();
     conv_vector<K, R>(ss, b, mode, smem, red2);
     __syncthreads();
@@ -614,16 +668,18 @@ static int num_sms() {
 struct ConvClass {
   int K, R, NT;
 };
-static constexpr ConvClass kConvClasses[3] = {{11, 16, 128}, {21, 16, 256}, {0, 8, 128}};
+static constexpr ConvClass kConvClasses[3] = {{11, 16, 128}, {21, 16, 256}, {0, 8, 128}};  // see launch_conv_class
 
 int conv_class(int K) { return K == 11 ? 0 : (K == 21 ? 1 : 2); }
 
-size_t conv_smem_bytes(int H, int W, int K) {
+size_t conv_smem_bytes(int H, int W, int K, bool two_buf) {
   const int R = kConvClasses[conv_class(K)].R;
   const int nstrip = (H + R - 1) / R;
   const size_t Hp = size_t(nstrip) * R + K - 1, Wp = size_t(W) + K - 1;
-  return (size_t((K * K + 3) & ~3) + Hp * Wp) * sizeof(float);
+  return (2 * size_t((K * K + 3) & ~3) + (two_buf ? 2 : 1) * Hp * Wp) * sizeof(float);
 }
+
+bool conv_two_buf(int H, int W, int K) { return conv_smem_bytes(H, W, K, true) <= CONV_TWO_BUF_MAX_SMEM; }
 
 void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix) {
   const int HW = H * W;
@@ -639,18 +695,18 @@ void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix) {
   *ntiles = (HW + tp - 1) / tp;
 }
 
-template <int K, int R, int NT, class Src>
+template <int K, int R, int NT, int MINB, class Src>
 static cudaError_t launch_conv(const Src& src, int nitems, size_t smem, int mode, cudaStream_t st, bool persistent) {
   static size_t attr = 48 * 1024;
   if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv<K, R, NT, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_conv<K, R, NT, MINB, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return e;
     attr = smem;
   }
   int grid = nitems;
   if (persistent) grid = grid < num_sms() * 4 ? grid : num_sms() * 4;
-  k_conv<K, R, NT, Src><<<grid, NT, smem, st>>>(src, mode);
+  k_conv<K, R, NT, MINB, Src><<<grid, NT, smem, st>>>(src, mode);
   return cudaSuccess;
 }
 
@@ -658,9 +714,9 @@ template <class Src>
 static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t smem, int mode, cudaStream_t st,
                                      bool persistent) {
   switch (cls) {
-    case 0: return launch_conv<11, 16, 128>(src, nitems, smem, mode, st, persistent);
-    case 1: return launch_conv<21, 16, 256>(src, nitems, smem, mode, st, persistent);
-    default: return launch_conv<0, 8, 128>(src, nitems, smem, mode, st, persistent);
+    case 0: return launch_conv<11, 16, 128, 5>(src, nitems, smem, mode, st, persistent);
+    case 1: return launch_conv<21, 16, 256, 1>(src, nitems, smem, mode, st, persistent);
+    default: return launch_conv<0, 8, 128, 4>(src, nitems, smem, mode, st, persistent);
   }
 }
 
@@ -703,7 +759,8 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false);
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_CONV, st);
-  e = launch_conv_class(conv_class(s.K), src, s.B, conv_smem_bytes(s.H, s.W, s.K), mode, st, false);
+  e = launch_conv_class(conv_class(s.K), src, s.B, conv_smem_bytes(s.H, s.W, s.K, s.conv_two_buf != 0), mode, st,
+                        false);
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD) return cudaSuccess;

@@ -20,8 +20,15 @@ struct Hooks {
   virtual ~Hooks() = default;
 };
 
-// Dynamic shared memory of the convolution stage for an H x W image, K x K PSF.
-size_t conv_smem_bytes(int H, int W, int K);
+// Dynamic shared memory of the convolution stage for an H x W image, K x K
+// PSF, with or without the second buffer that keeps the pixel adjoint on chip.
+size_t conv_smem_bytes(int H, int W, int K, bool two_buf);
+
+// Largest dynamic shared memory for which the second buffer is used.
+constexpr size_t CONV_TWO_BUF_MAX_SMEM = 200 * 1024;
+
+// Whether the convolution of an H x W image, K x K PSF uses the second buffer.
+bool conv_two_buf(int H, int W, int K);
 
 // Convolution kernel class of a PSF side (0: K = 11, 1: K = 21, 2: any other odd K).
 int conv_class(int K);
