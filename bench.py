@@ -147,6 +147,26 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_param_seed(rank: int) -> int:
+    """Seed of rank r's parameter batch: every rank evaluates its own B vectors."""
+    return CONFIG * 1000 + 17 + rank
+
+
+def max_over_ranks(value: float, device, world: int) -> float:
+    """Max of a per-rank float over all ranks (the timing rule of the benchmark)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, per_rank_units: int, seconds: float) -> float:
+    """Units processed by all ranks per second of the slowest rank (weak scaling)."""
+    return world * per_rank_units / seconds
+
+
 def make_workload(device, rank: int):
     """Synthetic lens system (observed image from the GPU model + seeded noise) and B vectors."""
     import torch
@@ -161,7 +181,7 @@ def make_workload(device, rank: int):
     model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
     s0.close()
     image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
-    params = inputs.draw_box(np.random.default_rng(CONFIG * 1000 + 17 + rank), B).astype(np.float32)
+    params = inputs.draw_box(np.random.default_rng(rank_param_seed(rank)), B).astype(np.float32)
     return spec, B, truth, psf, image, params
 
 
@@ -196,7 +216,7 @@ def run_reference(args):
     psf = inputs.make_psf(spec).astype(np.float32)
     model = oracle.simulate(truth, spec.H, spec.W, psf, spec.pixel_scale, spec.k)[0]
     image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
-    params = inputs.draw_box(np.random.default_rng(CONFIG * 1000 + 17), B).astype(np.float32)
+    params = inputs.draw_box(np.random.default_rng(rank_param_seed(0)), B).astype(np.float32)
     nt = oracle.max_threads()
     a = (image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k, spec.gain_exposure)
     per_step = max(nt * 2, 32)
@@ -291,12 +311,8 @@ def main():
     launches = abi.gl_launch_count() - n0
     prof = abi.gl_profile_read()
     abi.gl_profile_enable(False)
-    step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    t_rank = torch.tensor([step_ms], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-    step_ms = float(t_rank.item())
-    value = world * B / (step_ms * 1e-3)
+    step_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / args.steps, device, world)
+    value = whole_job_rate(world, B, step_ms * 1e-3)
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     hp = torch.from_numpy(params).pin_memory()
@@ -310,11 +326,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         sysm.loglik_grad_host(hp_np, hl_np, hg_np)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * B / float(te.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, device, world)
+    e2e_value = whole_job_rate(world, B, e2e_s)
 
     # ---- roofline of the dominant kernel, from the live event timings
     n_adj, ms_adj = prof["k_ray_adj"]
