@@ -77,7 +77,7 @@ def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
 
 # DRAM bytes per launch of k_ray_adj from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 prefix of gl_kernels.cu + gl_device.cuh).
-TRAFFIC = {}
+TRAFFIC = {"2e72f963fc12e356": 62.170624e6}   # ncu dram read + write, one launch at B = 4096
 
 
 def kernel_source_hash() -> str:
@@ -342,6 +342,8 @@ def main():
     achieved = flop_adj / adj_s / 1e12
     th = kernel_source_hash()
     traffic = TRAFFIC.get(th)
+    if traffic is not None:
+        traffic = traffic * B / 4096.0   # captured at B = 4096; DRAM bytes scale with the vectors of a launch
     kern = {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items() if v[0] > 0}
     tot = sum(v[1] for v in prof.values())
     for k in kern:

@@ -189,20 +189,22 @@ __device__ __forceinline__ void epl_fwd_T(const VecConst& V, const float* cn, T 
   const T r2 = maxT(r2raw, sp<T>(RHO2_MIN));
   const T S = keep * ex2T(sp<T>(V.t) * fmaT(sp<T>(-0.5f), lg2T(r2), sp<T>(V.log2_thetaE)));
   const T iw2 = rcpT(maxT(w2, sp<T>(1e-30f)));
-  const T vr = fmaT(wr, wr, -(wi * wi)) * iw2;
+  const T nwi = -wi;
+  const T vr = fmaT(wr, wr, nwi * wi) * iw2;
   const T vi = sp<T>(2.f) * wr * wi * iw2;
-  const T ur = -fmaT(sp<T>(V.e1), vr, sp<T>(V.e2) * vi);
+  const T ur = fmaT(sp<T>(-V.e1), vr, sp<T>(-V.e2) * vi);
   const T ui = fmaT(sp<T>(V.e2), vr, sp<T>(-V.e1) * vi);
+  const T nui = fmaT(sp<T>(-V.e2), vr, sp<T>(V.e1) * vi);   // -ui: packed FMAs take no negated operands
   T hr = sp<T>(1.f), hi = sp<T>(0.f);
 #pragma unroll 2
   for (int n = V.nterms; n >= 1; --n) {
     const T c = sp<T>(cn[n - 1]);
-    const T tr = fmaT(ur, hr, -(ui * hi));
+    const T tr = fmaT(ur, hr, nui * hi);
     const T ti = fmaT(ur, hi, ui * hr);
     hr = fmaT(c, tr, sp<T>(1.f));
     hi = c * ti;
   }
-  ax = S * fmaT(wr, hr, -(wi * hi));
+  ax = S * fmaT(wr, hr, nwi * hi);
   ay = S * fmaT(wr, hi, wi * hr);
 }
 

@@ -20,6 +20,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "gl_device.cuh"
 #include "gl_launch.h"
@@ -85,28 +86,29 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // ------------------------------------------------------------- k_setup ----
 
-__device__ void setup_light(const double* p, LightC& L, bool& ok) {
-  const double R = p[0], n = p[1], e1 = p[2], e2 = p[3];
-  const double e2s = e1 * e1 + e2 * e2;
-  ok = ok && R > 0.0 && n > 0.0 && e2s < 1.0;
-  const double D = 1.0 - e2s, iD = 1.0 / D, iD2 = iD * iD;
-  L.A = float((1.0 + e2s - 2.0 * e1) * iD);
-  L.B2 = float(-4.0 * e2 * iD);
-  L.C = float((1.0 + e2s + 2.0 * e1) * iD);
-  L.x = float(p[4]);
-  L.y = float(p[5]);
-  L.c1 = float(0.5 / n);
-  L.c0 = float(-log2(R) / n);
-  const double bn = 1.9992 * n - 0.3271;
-  L.k1 = float(bn / 0.69314718055994530942);
-  L.I0 = float(p[6]);
+// Derived constants of one Sersic profile (R_eff, n, e1, e2, xc, yc, I0).
+__device__ void setup_light(const float* p, LightC& L, bool& ok) {
+  const float R = p[0], n = p[1], e1 = p[2], e2 = p[3];
+  const float e2s = fmaf(e1, e1, e2 * e2);
+  ok = ok && R > 0.f && n > 0.f && e2s < 1.f;
+  const float iD = 1.0f / (1.0f - e2s), iD2 = iD * iD;
+  L.A = (1.f + e2s - 2.f * e1) * iD;
+  L.B2 = -4.f * e2 * iD;
+  L.C = (1.f + e2s + 2.f * e1) * iD;
+  L.x = p[4];
+  L.y = p[5];
+  L.c1 = 0.5f / n;
+  L.c0 = -log2f(R) / n;
+  const float bn = fmaf(1.9992f, n, -0.3271f);
+  L.k1 = bn * 1.44269504088896341f;   // b_n / ln 2
+  L.I0 = p[6];
   // derivatives of (A, 2B, C) with respect to e1 and e2
-  L.A1 = float(2.0 * (e2 * e2 - (1.0 - e1) * (1.0 - e1)) * iD2);
-  L.B21 = float(-8.0 * e1 * e2 * iD2);
-  L.C1 = float(2.0 * ((1.0 + e1) * (1.0 + e1) - e2 * e2) * iD2);
-  L.A2 = float(4.0 * e2 * (1.0 - e1) * iD2);
-  L.B22 = float(-4.0 * (1.0 - e1 * e1 + e2 * e2) * iD2);
-  L.C2 = float(4.0 * e2 * (1.0 + e1) * iD2);
+  L.A1 = 2.f * (e2 * e2 - (1.f - e1) * (1.f - e1)) * iD2;
+  L.B21 = -8.f * e1 * e2 * iD2;
+  L.C1 = 2.f * ((1.f + e1) * (1.f + e1) - e2 * e2) * iD2;
+  L.A2 = 4.f * e2 * (1.f - e1) * iD2;
+  L.B22 = -4.f * (1.f - e1 * e1 + e2 * e2) * iD2;
+  L.C2 = 4.f * e2 * (1.f + e1) * iD2;
 }
 
 // Truncation target of the EPL series: the smallest N with
@@ -115,11 +117,10 @@ __device__ void setup_light(const double* p, LightC& L, bool& ok) {
 // dF/dt exceeds that of F only by a logarithmic factor.
 constexpr double SERIES_TOL = 2e-8;
 
-// One warp per vector. GB300's FP64 rate is a small fraction of its FP32
-// rate, so the FP64 work is spread over lanes instead of repeated on each:
-// lanes 0..21 check one parameter each, lane 0 derives the EPL constants,
-// lanes 1 and 2 the two light profiles (FP64); all lanes compute series
-// coefficients and, by ballot, the term count (FP32 suffices for both).
+// One warp per vector: lanes 0..21 check one parameter each, lane 0 derives
+// the EPL constants, lanes 1 and 2 the two light profiles; all lanes compute
+// series coefficients and, by ballot, the term count. FP32 throughout: every
+// constant feeds FP32 arithmetic, and GB300's FP64 pipe is narrow.
 template <class Src>
 __global__ void k_setup(const __grid_constant__ Src src) {
   const int lane = threadIdx.x & 31;
@@ -130,38 +131,37 @@ __global__ void k_setup(const __grid_constant__ Src src) {
     VecConst* V = s->vc + b;
     const float* pp = s->params + size_t(b) * NPARAM;
     bool ok = lane >= NPARAM || isfinite(pp[lane]);
-    const float e1f = pp[2], e2f = pp[3], tf = pp[1] - 1.0f;
+    const float e1 = pp[2], e2 = pp[3], t = pp[1] - 1.0f;
+    const float e2s = fmaf(e1, e1, e2 * e2);
     if (lane == 0) {
-      const double thetaE = pp[0], t = double(pp[1]) - 1.0, e1 = pp[2], e2 = pp[3];
-      const double e2s = e1 * e1 + e2 * e2;
-      ok = ok && thetaE > 0.0 && e2s < 1.0 && t > -1.0 && t < 3.0;
+      const float thetaE = pp[0];
+      ok = ok && thetaE > 0.f && e2s < 1.f && t > -1.f && t < 3.f;
+      const float i1me2 = 1.0f / (1.0f - e2s);
       V->xc = pp[4];
       V->yc = pp[5];
-      V->e1 = float(e1);
-      V->e2 = float(e2);
-      V->om1 = float(1.0 - e1);
-      V->op1 = float(1.0 + e1);
-      V->t = float(t);
-      V->log2_thetaE = float(log2(thetaE));
-      V->inv_1me2 = float(1.0 / (1.0 - e2s));
+      V->e1 = e1;
+      V->e2 = e2;
+      V->om1 = 1.f - e1;
+      V->op1 = 1.f + e1;
+      V->t = t;
+      V->log2_thetaE = log2f(thetaE);
+      V->inv_1me2 = i1me2;
       V->g1 = pp[6];
       V->g2 = pp[7];
-      V->th = float(0.5 * t);
-      V->kc = float((1.0 - 0.5 * t) * t / (4.0 - t));
-      V->kap_c = float(0.5 * (2.0 - t));
-      V->omt = float(1.0 - t);
-      V->e1i = float(e1 / (1.0 - e2s));
-      V->e2i = float(e2 / (1.0 - e2s));
+      V->th = 0.5f * t;
+      V->kc = (1.f - 0.5f * t) * t / (4.f - t);
+      V->kap_c = 0.5f * (2.f - t);
+      V->omt = 1.f - t;
+      V->e1i = e1 * i1me2;
+      V->e2i = e2 * i1me2;
     } else if (lane == 1 || lane == 2) {
-      double q[7];
-      for (int i = 0; i < 7; ++i) q[i] = pp[(lane == 1 ? 8 : 15) + i];
       LightC L;
-      setup_light(q, L, ok);
+      setup_light(pp + (lane == 1 ? 8 : 15), L, ok);
       V->light[lane - 1] = L;
     }
     ok = __all_sync(0xffffffffu, ok);
     // term count: lane tests N = lane and N = lane + 32
-    const float f = sqrtf(e1f * e1f + e2f * e2f);
+    const float f = sqrtf(e2s);
     const float lf = f > 0.f ? logf(f) : -1e30f;
     const float l1f = log1pf(-fminf(f, 0.999999f));
     const float ltol = logf(float(SERIES_TOL));
@@ -170,9 +170,9 @@ __global__ void k_setup(const __grid_constant__ Src src) {
     const unsigned f_hi = __ballot_sync(0xffffffffu, fwd_ok(lane + 32));
     const int n_fwd = f_lo ? __ffs(f_lo) - 1 : (f_hi ? 32 + __ffs(f_hi) - 1 : NMAX);
     for (int n = lane + 1; n <= NMAX; n += 32) {
-      const float den = 2.f * n + 2.f - tf;
+      const float den = 2.f * n + 2.f - t;
       const float iden = 1.0f / den;
-      V->cn[n - 1] = (2.f * n - 2.f + tf) * iden;
+      V->cn[n - 1] = (2.f * n - 2.f + t) * iden;
       V->cnt[n - 1] = 4.f * n * iden * iden;
     }
     if (lane == 0) {
@@ -184,8 +184,16 @@ __global__ void k_setup(const __grid_constant__ Src src) {
 
 // ----------------------------------------------------------- k_ray_fwd ----
 
+#ifndef GL_FWD_THREADS
+#define GL_FWD_THREADS 128
+#endif
+#ifndef GL_FWD_MINB
+#define GL_FWD_MINB 4
+#endif
+constexpr int FWD_THREADS = GL_FWD_THREADS;
+
 template <class Src>
-__global__ void __launch_bounds__(RAY_THREADS) k_ray_fwd(const __grid_constant__ Src src) {
+__global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd(const __grid_constant__ Src src) {
   __shared__ VecConst sv;
   __shared__ Seg ss;
   for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
@@ -235,137 +243,157 @@ __global__ void __launch_bounds__(RAY_THREADS) k_ray_fwd(const __grid_constant__
 // Lens or source light: accumulates R, n (two terms), e1, e2, x, y, I0 slots
 // and returns (Gx, Gy) = s I / rho^2 (A dx + B dy, B dx + C dy), so that
 // dI/d(centre) = (b_n/n) (Gx, Gy) and dI/d(position) = -(b_n/n) (Gx, Gy).
-__device__ __forceinline__ void light_adj(const LightC& L, float px, float py, float g, float* acc,
-                                          float& Gx, float& Gy) {
-  const float dx = px - L.x, dy = py - L.y;
-  const float dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
-  float r2 = fmaf(L.A, dxx, fmaf(L.B2, dxy, L.C * dyy));
-  const bool floored = r2 < RHO2_MIN;
-  r2 = fmaxf(r2, RHO2_MIN);
-  const float ls = fmaf(L.c1, lg2(r2), L.c0);
-  const float s = ex2(ls);
-  const float e = ex2(fmaf(-L.k1, s, L.k1));
-  const float I = L.I0 * e;
-  const float hI = g * I;
-  const float hs = hI * s;
-  acc[0] += hs;
-  acc[1] = fmaf(hI, s - 1.f, acc[1]);
-  acc[2] = fmaf(hs, ls, acc[2]);
-  const float q = floored ? 0.f : s * I * rcp(r2);
+// Generic in the ray type (float or a packed pair).
+template <class T>
+__device__ __forceinline__ void light_adj(const LightC& L, T px, T py, T g, T* acc, T& Gx, T& Gy) {
+  const T dx = px - sp<T>(L.x), dy = py - sp<T>(L.y);
+  const T dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
+  const T r2raw = fmaT(sp<T>(L.A), dxx, fmaT(sp<T>(L.B2), dxy, sp<T>(L.C) * dyy));
+  const T keep = geT(r2raw, sp<T>(RHO2_MIN));      // 0 where the radius is floored
+  const T r2 = maxT(r2raw, sp<T>(RHO2_MIN));
+  const T ls = fmaT(sp<T>(L.c1), lg2T(r2), sp<T>(L.c0));
+  const T s = ex2T(ls);
+  const T e = ex2T(fmaT(sp<T>(-L.k1), s, sp<T>(L.k1)));
+  const T I = sp<T>(L.I0) * e;
+  const T hI = g * I;
+  const T hs = hI * s;
+  acc[0] = acc[0] + hs;
+  acc[1] = fmaT(hI, s - sp<T>(1.f), acc[1]);
+  acc[2] = fmaT(hs, ls, acc[2]);
+  const T q = keep * s * I * rcpT(r2);
   const float Bh = 0.5f * L.B2;
-  Gx = q * fmaf(L.A, dx, Bh * dy);
-  Gy = q * fmaf(Bh, dx, L.C * dy);
-  const float gq = g * q;
-  acc[3] = fmaf(gq, fmaf(L.A1, dxx, fmaf(L.B21, dxy, L.C1 * dyy)), acc[3]);
-  acc[4] = fmaf(gq, fmaf(L.A2, dxx, fmaf(L.B22, dxy, L.C2 * dyy)), acc[4]);
-  acc[5] = fmaf(g, Gx, acc[5]);
-  acc[6] = fmaf(g, Gy, acc[6]);
-  acc[7] = fmaf(g, e, acc[7]);
+  Gx = q * fmaT(sp<T>(L.A), dx, sp<T>(Bh) * dy);
+  Gy = q * fmaT(sp<T>(Bh), dx, sp<T>(L.C) * dy);
+  const T gq = g * q;
+  acc[3] = fmaT(gq, fmaT(sp<T>(L.A1), dxx, fmaT(sp<T>(L.B21), dxy, sp<T>(L.C1) * dyy)), acc[3]);
+  acc[4] = fmaT(gq, fmaT(sp<T>(L.A2), dxx, fmaT(sp<T>(L.B22), dxy, sp<T>(L.C2) * dyy)), acc[4]);
+  acc[5] = fmaT(g, Gx, acc[5]);
+  acc[6] = fmaT(g, Gy, acc[6]);
+  acc[7] = fmaT(g, e, acc[7]);
 }
 
-// One ray: adds g x (derivatives of its intensity) to the 24 accumulators.
-__device__ __forceinline__ void ray_adj(const VecConst& V, const float* cn, const float* cnt, float x, float y,
-                                        float g, float* acc) {
-  float Gx, Gy;
+// One ray (or a packed pair): adds g x (derivatives of its intensity) to the
+// 24 accumulators. Branch-free: a ray inside rho < 1e-6 arcsec has S = 0,
+// which zeroes its deflection and every EPL derivative (all carry S).
+template <class T>
+__device__ __forceinline__ void ray_adj(const VecConst& V, const float* cn, const float* cnt, T x, T y, T g, T* acc) {
+  T Gx, Gy;
   light_adj(V.light[0], x, y, g, acc + A_L_R, Gx, Gy);
 
   // EPL deflection with the pieces of its parameter derivatives
-  const float dx = x - V.xc, dy = y - V.yc;
-  const float wr = fmaf(V.om1, dx, -V.e2 * dy);
-  const float wi = fmaf(V.op1, dy, -V.e2 * dx);
-  const float w2 = fmaf(wr, wr, wi * wi);
-  const float r2 = w2 * V.inv_1me2;
-  const bool inside = r2 < RHO2_MIN;
-  float ar = 0.f, ai = 0.f;
-  // d alpha / d (t, e1, e2, xc, yc), complex; d/d thetaE = (t/thetaE) alpha
-  float dtr = 0.f, dti = 0.f, d1r = 0.f, d1i = 0.f, d2r = 0.f, d2i = 0.f;
-  float dxr = 0.f, dxi = 0.f, dyr = 0.f, dyi = 0.f;
-  if (!inside) {
-    const float lrho = fmaf(-0.5f, lg2(r2), V.log2_thetaE);  // log2(thetaE / rho)
-    const float S = ex2(V.t * lrho);
-    const float iw2 = rcp(w2);
-    const float vr = (wr * wr - wi * wi) * iw2;
-    const float vi = 2.f * wr * wi * iw2;
-    const float ur = -fmaf(V.e1, vr, V.e2 * vi);
-    const float ui = fmaf(V.e2, vr, -V.e1 * vi);
-    // Horner for F and dF/dt down to h_1, then the last step (n = 1)
-    float hr = 1.f, hi = 0.f, tr = 0.f, ti = 0.f;
-    for (int n = V.nterms_adj; n >= 2; --n) {
-      const float c = cn[n - 1], ct = cnt[n - 1];
-      const float uhr = fmaf(ur, hr, -ui * hi), uhi = fmaf(ur, hi, ui * hr);
-      const float utr = fmaf(ur, tr, -ui * ti), uti = fmaf(ur, ti, ui * tr);
-      tr = fmaf(ct, uhr, c * utr);
-      ti = fmaf(ct, uhi, c * uti);
-      hr = fmaf(c, uhr, 1.f);
-      hi = c * uhi;
-    }
-    const float c1 = cn[0], ct1 = cnt[0];
-    const float h1r = hr, h1i = hi;
-    {
-      const float uhr = fmaf(ur, hr, -ui * hi), uhi = fmaf(ur, hi, ui * hr);
-      const float utr = fmaf(ur, tr, -ui * ti), uti = fmaf(ur, ti, ui * tr);
-      tr = fmaf(ct1, uhr, c1 * utr);
-      ti = fmaf(ct1, uhi, c1 * uti);
-      hr = fmaf(c1, uhr, 1.f);
-      hi = c1 * uhi;
-    }
-    // dF/du = [(t/2) F - (1 - t/2) c_1 h_1] / (1 - u)   (Gauss contiguous relation)
-    const float nr = fmaf(V.th, hr, -V.kc * h1r), ni = fmaf(V.th, hi, -V.kc * h1i);
-    const float dr = 1.f - ur, di = -ui;
-    const float idd = rcp(fmaf(dr, dr, di * di));
-    const float pr = fmaf(nr, dr, ni * di) * idd, pi = fmaf(ni, dr, -nr * di) * idd;
-    const float swr = S * wr, swi = S * wi;     // S w
-    ar = fmaf(swr, hr, -swi * hi);
-    ai = fmaf(swr, hi, swi * hr);
-    // t: alpha ln(thetaE/rho) + S w dF/dt
-    const float lnr = 0.69314718f * lrho;
-    dtr = fmaf(ar, lnr, fmaf(swr, tr, -swi * ti));
-    dti = fmaf(ai, lnr, fmaf(swr, ti, swi * tr));
-    // e1, e2
-    const float Pr = fmaf(wr, dx, -wi * dy), Pi = fmaf(wr, dy, wi * dx);   // w z
-    const float a1 = V.t * fmaf(Pr, iw2, -V.e1i);                          // d ln S / d e1
-    const float a2 = V.t * fmaf(Pi, iw2, -V.e2i);                          // d ln S / d e2
-    const float sfr = S * hr, sfi = S * hi;                                // S F
-    const float swpr = fmaf(swr, pr, -swi * pi), swpi = fmaf(swr, pi, swi * pr);  // S w F'
-    const float k1 = 2.f * Pi * iw2, k2 = 2.f * Pr * iw2;
-    const float du1r = fmaf(-k1, ui, -vr), du1i = fmaf(k1, ur, -vi);      // du/de1 = -V + i k1 u
-    const float du2r = fmaf(k2, ui, -vi), du2i = fmaf(-k2, ur, vr);       // du/de2 = iV - i k2 u
-    // dw/de1 = (-dx, dy), dw/de2 = (-dy, -dx)
-    d1r = fmaf(ar, a1, fmaf(sfr, -dx, -sfi * dy)) + fmaf(swpr, du1r, -swpi * du1i);
-    d1i = fmaf(ai, a1, fmaf(sfr, dy, sfi * -dx)) + fmaf(swpr, du1i, swpi * du1r);
-    d2r = fmaf(ar, a2, fmaf(sfr, -dy, sfi * dx)) + fmaf(swpr, du2r, -swpi * du2i);
-    d2i = fmaf(ai, a2, fmaf(sfr, -dx, sfi * -dy)) + fmaf(swpr, du2i, swpi * du2r);
-    // centre: kappa and shear of the EPL from homogeneity, z kappa + conj(z) gamma = (1-t) alpha
-    const float kap = V.kap_c * S;
-    const float iz2 = rcp(fmaf(dx, dx, dy * dy));
-    const float Qr = fmaf(V.omt, ar, -kap * dx), Qi = fmaf(V.omt, ai, -kap * dy);
-    const float gr = fmaf(Qr, dx, -Qi * dy) * iz2, gi = fmaf(Qr, dy, Qi * dx) * iz2;   // Q z / |z|^2
-    dxr = -(kap + gr);
-    dxi = -gi;
-    dyr = -gi;
-    dyi = -(kap - gr);
+  const T dx = x - sp<T>(V.xc), dy = y - sp<T>(V.yc);
+  const T wr = fmaT(sp<T>(V.om1), dx, sp<T>(-V.e2) * dy);
+  const T wi = fmaT(sp<T>(V.op1), dy, sp<T>(-V.e2) * dx);
+  const T w2 = fmaT(wr, wr, wi * wi);
+  const T r2raw = w2 * sp<T>(V.inv_1me2);
+  const T keep = geT(r2raw, sp<T>(RHO2_MIN));
+  const T r2 = maxT(r2raw, sp<T>(RHO2_MIN));
+  const T lrho = fmaT(sp<T>(-0.5f), lg2T(r2), sp<T>(V.log2_thetaE));  // log2(thetaE / rho)
+  const T S = keep * ex2T(sp<T>(V.t) * lrho);
+  const T iw2 = rcpT(maxT(w2, sp<T>(1e-30f)));
+  const T nwi = -wi;
+  const T vr = fmaT(wr, wr, nwi * wi) * iw2;
+  const T vi = sp<T>(2.f) * wr * wi * iw2;
+  const T ur = fmaT(sp<T>(-V.e1), vr, sp<T>(-V.e2) * vi);
+  const T ui = fmaT(sp<T>(V.e2), vr, sp<T>(-V.e1) * vi);
+  const T nui = fmaT(sp<T>(-V.e2), vr, sp<T>(V.e1) * vi);   // -ui: packed FMAs take no negated operands
+  // Horner for F and dF/dt down to h_1, then the last step (n = 1)
+  T hr = sp<T>(1.f), hi = sp<T>(0.f), tr = sp<T>(0.f), ti = sp<T>(0.f);
+#pragma unroll 2
+  for (int n = V.nterms_adj; n >= 2; --n) {
+    const T c = sp<T>(cn[n - 1]), ct = sp<T>(cnt[n - 1]);
+    const T uhr = fmaT(ur, hr, nui * hi), uhi = fmaT(ur, hi, ui * hr);
+    const T utr = fmaT(ur, tr, nui * ti), uti = fmaT(ur, ti, ui * tr);
+    tr = fmaT(ct, uhr, c * utr);
+    ti = fmaT(ct, uhi, c * uti);
+    hr = fmaT(c, uhr, sp<T>(1.f));
+    hi = c * uhi;
   }
+  const T h1r = hr, h1i = hi;
+  {
+    const T c = sp<T>(cn[0]), ct = sp<T>(cnt[0]);
+    const T uhr = fmaT(ur, hr, nui * hi), uhi = fmaT(ur, hi, ui * hr);
+    const T utr = fmaT(ur, tr, nui * ti), uti = fmaT(ur, ti, ui * tr);
+    tr = fmaT(ct, uhr, c * utr);
+    ti = fmaT(ct, uhi, c * uti);
+    hr = fmaT(c, uhr, sp<T>(1.f));
+    hi = c * uhi;
+  }
+  // dF/du = [(t/2) F - (1 - t/2) c_1 h_1] / (1 - u)   (Gauss contiguous relation)
+  const T nr = fmaT(sp<T>(V.th), hr, sp<T>(-V.kc) * h1r), ni = fmaT(sp<T>(V.th), hi, sp<T>(-V.kc) * h1i);
+  const T dr = sp<T>(1.f) - ur;                 // 1 - u = (dr, -ui) = (dr, nui)
+  const T idd = rcpT(fmaT(dr, dr, ui * ui));
+  const T pr = fmaT(nr, dr, ni * nui) * idd, pi = fmaT(ni, dr, nr * ui) * idd;
+  const T swr = S * wr, swi = S * wi, nswi = S * nwi;   // S w
+  const T ar = fmaT(swr, hr, nswi * hi);
+  const T ai = fmaT(swr, hi, swi * hr);
+  // t: alpha ln(thetaE/rho) + S w dF/dt
+  const T lnr = sp<T>(0.69314718f) * lrho;
+  const T dtr = fmaT(ar, lnr, fmaT(swr, tr, nswi * ti));
+  const T dti = fmaT(ai, lnr, fmaT(swr, ti, swi * tr));
+  // e1, e2
+  const T Pr = fmaT(wr, dx, nwi * dy), Pi = fmaT(wr, dy, wi * dx);   // w z
+  const T a1 = sp<T>(V.t) * fmaT(Pr, iw2, sp<T>(-V.e1i));             // d ln S / d e1
+  const T a2 = sp<T>(V.t) * fmaT(Pi, iw2, sp<T>(-V.e2i));             // d ln S / d e2
+  const T sfr = S * hr, sfi = S * hi;                                  // S F
+  const T swpr = fmaT(swr, pr, nswi * pi), swpi = fmaT(swr, pi, swi * pr);  // S w F'
+  const T nswpi = -swpi, ndx = -dx, ndy = -dy, nsfi = -sfi;
+  const T k1 = sp<T>(2.f) * Pi * iw2, nk1 = sp<T>(-2.f) * Pi * iw2;
+  const T k2 = sp<T>(2.f) * Pr * iw2, nk2 = sp<T>(-2.f) * Pr * iw2;
+  const T nvr = -vr, nvi = -vi;
+  const T du1r = fmaT(nk1, ui, nvr), du1i = fmaT(k1, ur, nvi);        // du/de1 = -V + i k1 u
+  const T du2r = fmaT(k2, ui, nvi), du2i = fmaT(nk2, ur, vr);         // du/de2 = iV - i k2 u
+  // dw/de1 = (-dx, dy), dw/de2 = (-dy, -dx)
+  const T d1r = fmaT(ar, a1, fmaT(sfr, ndx, nsfi * dy)) + fmaT(swpr, du1r, nswpi * du1i);
+  const T d1i = fmaT(ai, a1, fmaT(sfr, dy, nsfi * dx)) + fmaT(swpr, du1i, swpi * du1r);
+  const T d2r = fmaT(ar, a2, fmaT(sfr, ndy, sfi * dx)) + fmaT(swpr, du2r, nswpi * du2i);
+  const T d2i = fmaT(ai, a2, fmaT(sfr, ndx, nsfi * dy)) + fmaT(swpr, du2i, swpi * du2r);
+  // centre: kappa and shear of the EPL from homogeneity, z kappa + conj(z) gamma = (1-t) alpha
+  const T kap = sp<T>(V.kap_c) * S;
+  const T iz2 = rcpT(maxT(fmaT(dx, dx, dy * dy), sp<T>(1e-30f)));
+  const T nkap = sp<T>(-V.kap_c) * S;
+  const T Qr = fmaT(sp<T>(V.omt), ar, nkap * dx), Qi = fmaT(sp<T>(V.omt), ai, nkap * dy);
+  const T gr = fmaT(Qr, dx, Qi * ndy) * iz2, gi = fmaT(Qr, dy, Qi * dx) * iz2;   // Q z / |z|^2
   // lens equation with external shear, source at beta
-  const float bx = x - ar - fmaf(V.g1, x, V.g2 * y);
-  const float by = y - ai - fmaf(V.g2, x, -V.g1 * y);
+  const T bx = x - ar - fmaT(sp<T>(V.g1), x, sp<T>(V.g2) * y);
+  const T by = y - ai - fmaT(sp<T>(V.g2), x, sp<T>(-V.g1) * y);
   light_adj(V.light[1], bx, by, g, acc + A_S_R, Gx, Gy);
-  // mass: g Ghat . d alpha / d p  (times b_s/n_s in the chain rule)
-  const float gx = g * Gx, gy = g * Gy;
-  acc[A_THETAE] = fmaf(gx, ar, fmaf(gy, ai, acc[A_THETAE]));
-  acc[A_T] = fmaf(gx, dtr, fmaf(gy, dti, acc[A_T]));
-  acc[A_E1] = fmaf(gx, d1r, fmaf(gy, d1i, acc[A_E1]));
-  acc[A_E2] = fmaf(gx, d2r, fmaf(gy, d2i, acc[A_E2]));
-  acc[A_XC] = fmaf(gx, dxr, fmaf(gy, dxi, acc[A_XC]));
-  acc[A_YC] = fmaf(gx, dyr, fmaf(gy, dyi, acc[A_YC]));
-  acc[A_G1] = fmaf(gx, x, fmaf(-gy, y, acc[A_G1]));
-  acc[A_G2] = fmaf(gx, y, fmaf(gy, x, acc[A_G2]));
+  // mass: g Ghat . d alpha / d p  (times b_s/n_s in the chain rule);
+  // d alpha/d xc = -(kappa + gamma), d alpha/d yc = -i (kappa - gamma)
+  const T gx = g * Gx, gy = g * Gy;
+  acc[A_THETAE] = fmaT(gx, ar, fmaT(gy, ai, acc[A_THETAE]));
+  acc[A_T] = fmaT(gx, dtr, fmaT(gy, dti, acc[A_T]));
+  acc[A_E1] = fmaT(gx, d1r, fmaT(gy, d1i, acc[A_E1]));
+  acc[A_E2] = fmaT(gx, d2r, fmaT(gy, d2i, acc[A_E2]));
+  acc[A_XC] = acc[A_XC] - fmaT(gx, kap + gr, gy * gi);
+  acc[A_YC] = acc[A_YC] - fmaT(gx, gi, gy * (kap - gr));
+  acc[A_G1] = fmaT(gx, x, fmaT(-gy, y, acc[A_G1]));
+  acc[A_G2] = fmaT(gx, y, fmaT(gy, x, acc[A_G2]));
 }
 
+// Ray type of the adjoint kernel: float (one ray per thread per step) or F2
+// (two pixels per step, their rays paired in packed f32x2 arithmetic), with
+// its block size and minimum resident blocks.
+#ifndef GL_ADJ_PAIRED
+#define GL_ADJ_PAIRED 1
+#endif
+#ifndef GL_ADJ_THREADS
+#define GL_ADJ_THREADS 128
+#endif
+#ifndef GL_ADJ_MINB
+#define GL_ADJ_MINB 2
+#endif
+constexpr int ADJ_THREADS = GL_ADJ_THREADS;
+
+__device__ __forceinline__ float lane_sum(float v) { return v; }
+__device__ __forceinline__ float lane_sum(F2 v) { return v.v.x + v.v.y; }
+
 template <class Src>
-__global__ void __launch_bounds__(RAY_THREADS) k_ray_adj(const __grid_constant__ Src src) {
+__global__ void __launch_bounds__(ADJ_THREADS, GL_ADJ_MINB) k_ray_adj(const __grid_constant__ Src src) {
+  using RT = typename std::conditional<GL_ADJ_PAIRED != 0, F2, float>::type;
   __shared__ VecConst sv;
   __shared__ Seg ss;
-  __shared__ double red[RAY_THREADS / 32][NACC];
+  __shared__ double red[ADJ_THREADS / 32][NACC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
     int local;
@@ -375,30 +403,55 @@ __global__ void __launch_bounds__(RAY_THREADS) k_ray_adj(const __grid_constant__
     const int b = local / ss.ntiles, tile = local - b * ss.ntiles;
     block_copy(&sv, ss.vc + b);
     __syncthreads();
-    float acc[NACC];
+    RT acc[NACC];
 #pragma unroll
-    for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
+    for (int a = 0; a < NACC; ++a) acc[a] = sp<RT>(0.f);
     const int HW = ss.H * ss.W, W = ss.W, k = ss.k;
     const int p0 = tile * ss.tile_pix;
     const int p1 = min(HW, p0 + ss.tile_pix);
     const float* gpre = ss.work + size_t(b) * HW;
     if (sv.nterms >= 0) {
-      for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const int i = p / W, j = p - i * W;
-        const float g = gpre[p];
-        for (int a = 0; a < k; ++a) {
-          const float y = fmaf(float(i * k + a), ss.sub, ss.y0);
-          for (int c = 0; c < k; ++c) {
-            const float x = fmaf(float(j * k + c), ss.sub, ss.x0);
-            ray_adj(sv, sv.cn, sv.cnt, x, y, g, acc);
+      const int stride = blockDim.x;
+#if GL_ADJ_PAIRED
+      {
+        // two pixels per thread and step (p and p + blockDim), their rays paired in f32x2;
+        // a missing second pixel repeats the first with zero weight
+        for (int p = p0 + threadIdx.x; p < p1; p += 2 * stride) {
+          const int q = p + stride;
+          const bool has_q = q < p1;
+          const int qq = has_q ? q : p;
+          const int ip = p / W, jp = p - ip * W;
+          const int iq = qq / W, jq = qq - iq * W;
+          const F2 g = {make_float2(gpre[p], has_q ? gpre[q] : 0.f)};
+          for (int a = 0; a < k; ++a) {
+            const F2 y = {make_float2(fmaf(float(ip * k + a), ss.sub, ss.y0), fmaf(float(iq * k + a), ss.sub, ss.y0))};
+            for (int c = 0; c < k; ++c) {
+              const F2 x = {make_float2(fmaf(float(jp * k + c), ss.sub, ss.x0), fmaf(float(jq * k + c), ss.sub, ss.x0))};
+              ray_adj(sv, sv.cn, sv.cnt, x, y, g, acc);
+            }
           }
         }
       }
+#else
+      {
+        for (int p = p0 + threadIdx.x; p < p1; p += stride) {
+          const int i = p / W, j = p - i * W;
+          const float g = gpre[p];
+          for (int a = 0; a < k; ++a) {
+            const float y = fmaf(float(i * k + a), ss.sub, ss.y0);
+            for (int c = 0; c < k; ++c) {
+              const float x = fmaf(float(j * k + c), ss.sub, ss.x0);
+              ray_adj(sv, sv.cn, sv.cnt, x, y, g, acc);
+            }
+          }
+        }
+      }
+#endif
     }
     // pairwise FP32 sums within the warp (GB300's FP64 pipe is narrow), FP64 across warps
 #pragma unroll
     for (int a = 0; a < NACC; ++a) {
-      float v = acc[a];
+      float v = lane_sum(acc[a]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) red[warp][a] = double(v);
@@ -739,12 +792,12 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
     k_setup<Src><<<sgrid, vthreads, 0, st>>>(src);
     if ((e = hooks->after(GL_K_SETUP, st)) != cudaSuccess) return e;
     hooks->before(GL_K_RAY_FWD, st);
-    k_ray_fwd<Src><<<rgrid, RAY_THREADS, 0, st>>>(src);
+    k_ray_fwd<Src><<<rgrid, FWD_THREADS, 0, st>>>(src);
     return hooks->after(GL_K_RAY_FWD, st);
   }
   if (adj_final) {
     hooks->before(GL_K_RAY_ADJ, st);
-    k_ray_adj<Src><<<rgrid, RAY_THREADS, 0, st>>>(src);
+    k_ray_adj<Src><<<rgrid, ADJ_THREADS, 0, st>>>(src);
     if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
     hooks->before(GL_K_FINAL, st);
     k_final<Src><<<fgrid, vthreads, 0, st>>>(src);
