@@ -185,6 +185,78 @@ def make_workload(device, rank: int):
     return spec, B, truth, psf, image, params
 
 
+def synthetic_system(cfg: int, device):
+    """(spec, truth, psf, image) of a config: GPU model of a seeded truth + seeded noise."""
+    import torch
+    from paper_2202_07663_gb300 import abi
+    spec = inputs.CONFIGS[cfg]["spec"]
+    rng = inputs.rng_for(cfg, 0)
+    truth = inputs.draw_truth(rng)
+    psf = inputs.make_psf(spec).astype(np.float32)
+    blank = np.zeros((spec.H, spec.W), np.float32)
+    s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
+    s0.close()
+    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
+    return spec, truth, psf, image
+
+
+def run_hmc_workload(device, iterations: int = 200, chains: int = 512, leapfrog: int = 8):
+    """Config 3: HMC through the adjoint, 100x100 pixels, k = 4, 21x21 Moffat PSF."""
+    import torch
+    from paper_2202_07663_gb300 import abi, hmc
+    spec, truth, psf, image = synthetic_system(3, device)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    s.reserve(chains)
+    q0 = torch.from_numpy(inputs.draw_perturbed(np.random.default_rng(3017), truth, chains, frac=0.002)).to(device)
+    inv_mass = hmc.laplace_inv_mass(s, torch.from_numpy(truth).to(device))
+    sampler = hmc.HMC(q0, inv_mass, 0.05, leapfrog, system=s, seed=3)
+    eps = sampler.tune_step_size(rounds=5, iters=2)
+    st = sampler.run(iterations)
+    s.close()
+    return {"workload": "hmc-100x100-k4-moffat21", "chains": chains, "leapfrog": leapfrog,
+            "iterations": iterations, "grad_evals": st.grad_evals, "seconds": st.seconds,
+            "evals_per_s": st.evals_per_s, "acceptance": st.acceptance, "step_size": eps,
+            "mass": "diagonal, 1/|d2 logL/dq2| at the truth (Laplace)",
+            "log_density": "log L (flat prior), physical parameters"}
+
+
+def run_stress_workload(device, steps: int = 3):
+    """Config 5: 200x200 pixels, k = 4, 21x21 PSF, B = 16384 vectors per call."""
+    import torch
+    from paper_2202_07663_gb300 import abi
+    spec, truth, psf, image = synthetic_system(5, device)
+    B = inputs.CONFIGS[5]["B"]
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    s.reserve(B)
+    params = inputs.draw_box(np.random.default_rng(5017), B).astype(np.float32)
+    p = torch.from_numpy(params).to(device)
+    ll = torch.empty(B, dtype=torch.float64, device=device)
+    g = torch.empty(B, 22, dtype=torch.float64, device=device)
+    s.loglik_grad(p, out=(ll, g, None))
+    torch.cuda.synchronize()
+    abi.gl_profile_reset()
+    abi.gl_profile_enable(True)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        s.loglik_grad(p, out=(ll, g, None))
+    e.record()
+    torch.cuda.synchronize()
+    prof = abi.gl_profile_read()
+    abi.gl_profile_enable(False)
+    ms = a.elapsed_time(e) / steps
+    n_adj, ms_adj = prof["k_ray_adj"]
+    N = series_terms(params, adjoint=True)
+    rays = spec.H * spec.W * spec.k * spec.k
+    adj_tflops = rays * float(flops_ray_adj(N).sum()) / (ms_adj / n_adj * 1e-3) / 1e12
+    s.close()
+    return {"workload": "stress-200x200-k4-psf21-B16384", "B": B, "steps": steps, "ms_per_step": ms,
+            "evals_per_s": B / (ms * 1e-3), "k_ray_adj_tflops": adj_tflops,
+            "kernel_ms_per_step": {k: v[1] / steps for k, v in prof.items() if v[0] > 0},
+            "finite": bool(torch.isfinite(ll).all().item() and torch.isfinite(g).all().item())}
+
+
 def cpu_baseline(spec, psf, image, params, budget_s: float = 12.0):
     """The FP64 oracle (log L + gradient) on a bounded sample of the same workload."""
     import oracle
@@ -251,6 +323,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the HMC (100x100, k=4) and stress (200x200, B=16384) runs reported beside the metric")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -358,6 +432,9 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec, psf, image, params)
+    workloads = None
+    if world == 1 and not args.no_workloads:
+        workloads = {"hmc": run_hmc_workload(device), "stress": run_stress_workload(device)}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -376,6 +453,7 @@ def main():
                      "mean_series_terms": float(N.mean())},
         "kernels": kern,
         "cpu_baseline": cpu,
+        "workloads": workloads,
         "clocks": clocks,
         "gpu_launches": int(launches),
         "wall_s_timed": wall,

@@ -187,6 +187,32 @@ int gl_loglik_grad_grouped(gl_system* const* systems, const float* const* params
 int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* loglik_out, double* chi2_out,
                            double* grad_out, void* stream);
 
+/*
+ * Hamiltonian Monte Carlo around the gradient (Sec. 2.5; Table 1 sampler
+ * settings are the caller's). Chain state is FP64 on the device: positions
+ * q [B, d], momenta p [B, d], log density logp [B], its gradient [B, d];
+ * inv_mass [d] is the diagonal of the inverse mass matrix. The caller draws
+ * the random numbers (initial momenta, log-uniforms for the accept test).
+ *
+ * gl_hmc_leapfrog - one leapfrog update: p += kick * eps * grad, then
+ *   q += eps * inv_mass * p, and q32_out = (float)q for the next likelihood
+ *   call. kick = 0.5 for the first step of a trajectory, 1 afterwards (the
+ *   half kicks at both ends of consecutive steps merged).
+ *
+ * gl_hmc_finish - last half kick p += eps/2 * grad_new, Hamiltonians
+ *   H = -logp + 1/2 sum p^2 inv_mass of the start (p0, logp0) and end
+ *   (p, logp_new) points in FP64, accept where log_u < H_start - H_end (and
+ *   both are finite); accepted chains copy q_new, logp_new, grad_new into q,
+ *   logp, grad. accepted[b] is 1 or 0.
+ *
+ * All pointers are device memory; asynchronous on stream; 1 <= d <= 4096.
+ */
+int gl_hmc_leapfrog(int B, int d, double* q, double* p, const double* grad, const double* inv_mass, double eps,
+                    double kick, float* q32_out, void* stream);
+int gl_hmc_finish(int B, int d, const double* p0, const double* logp0, double* p, const double* grad_new,
+                  const double* logp_new, const double* q_new, const double* inv_mass, const double* log_u,
+                  double eps, double* q, double* logp, double* grad, int* accepted, void* stream);
+
 /* Name of a status code (static string). */
 const char* gl_error_string(int code);
 

@@ -45,6 +45,8 @@ SIGNATURES = {
     "gl_simulate": ([_vp, _vp, _i, _vp, _vp], _i),
     "gl_loglik_grad_grouped": ([_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
     "gl_loglik_grad_noalloc": ([_vp, _vp, _i, _vp, _vp, _vp, _vp], _i),
+    "gl_hmc_leapfrog": ([_i, _i, _vp, _vp, _vp, _vp, _d, _d, _vp, _vp], _i),
+    "gl_hmc_finish": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_error_string": ([_i], ctypes.c_char_p),
     "gl_last_error_message": ([], ctypes.c_char_p),
     "gl_profile_enable": ([_i], _i),
@@ -145,6 +147,17 @@ def gl_loglik_grad_host(handle, params_ptr, B, loglik_ptr, chi2_ptr, grad_ptr, s
 
 def gl_simulate(handle, params_ptr, B, images_ptr, stream):
     _check(lib_handle().gl_simulate(handle, params_ptr, B, images_ptr, stream), "gl_simulate")
+
+
+def gl_hmc_leapfrog(B, d, q, p, grad, inv_mass, eps, kick, q32, stream):
+    _check(lib_handle().gl_hmc_leapfrog(B, d, q, p, grad, inv_mass, float(eps), float(kick), q32, stream),
+           "gl_hmc_leapfrog")
+
+
+def gl_hmc_finish(B, d, p0, logp0, p, grad_new, logp_new, q_new, inv_mass, log_u, eps, q, logp, grad, accepted,
+                  stream):
+    _check(lib_handle().gl_hmc_finish(B, d, p0, logp0, p, grad_new, logp_new, q_new, inv_mass, log_u, float(eps), q,
+                                      logp, grad, accepted, stream), "gl_hmc_finish")
 
 
 def gl_profile_enable(on: bool) -> None:
