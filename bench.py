@@ -257,6 +257,28 @@ def run_stress_workload(device, steps: int = 3):
             "finite": bool(torch.isfinite(ll).all().item() and torch.isfinite(g).all().item())}
 
 
+def run_serving_workload(device, n_latency: int = 200, n_capacity: int = 1000):
+    """Config 4: the seeded stream of heterogeneous lenses (Poisson 20/s; sizes
+    40..120 px, k in {2, 4}, PSF 11 or 21, 256..2048 vectors per request).
+    Latency: the first n_latency requests at their arrival times through the
+    continuous-batching server. Capacity: n_capacity requests all at t = 0,
+    served (grouped, graph-replayed) and one gl_loglik_grad call per lens."""
+    from paper_2202_07663_gb300 import serving
+    stream = inputs.serving_stream(n=n_capacity)
+    reqs = serving.make_requests(stream, device)
+    srv = serving.LensServer(budget_bytes=16 << 30, arena_bytes=4 << 30, max_segments=64, chunk=2048)
+    lat, _ = srv.serve(reqs[:n_latency], realtime=True)
+    cap, _ = srv.serve(reqs, realtime=False)
+    srv.close()
+    base_lat = serving.serve_one_call_per_lens(reqs[:n_latency], realtime=True)
+    base_cap = serving.serve_one_call_per_lens(reqs, realtime=False)
+    return {"workload": "serving-poisson20-40..120px-k2|4-psf11|21-B256..2048",
+            "latency_stream": dict(lat.summary(), arrivals="first %d requests at 20/s" % n_latency),
+            "capacity": dict(cap.summary(), arrivals="%d requests at t=0" % n_capacity),
+            "one_call_per_lens": {"latency_stream": base_lat.summary(), "capacity": base_cap.summary()},
+            "speedup_lenses_per_s": cap.lenses_per_s / base_cap.lenses_per_s}
+
+
 def cpu_baseline(spec, psf, image, params, budget_s: float = 12.0):
     """The FP64 oracle (log L + gradient) on a bounded sample of the same workload."""
     import oracle
@@ -324,7 +346,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-workloads", action="store_true",
-                    help="skip the HMC (100x100, k=4) and stress (200x200, B=16384) runs reported beside the metric")
+                    help="skip the HMC (100x100, k=4), stress (200x200, B=16384) and serving runs reported beside the metric")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -434,7 +456,8 @@ def main():
         cpu = cpu_baseline(spec, psf, image, params)
     workloads = None
     if world == 1 and not args.no_workloads:
-        workloads = {"hmc": run_hmc_workload(device), "stress": run_stress_workload(device)}
+        workloads = {"hmc": run_hmc_workload(device), "stress": run_stress_workload(device),
+                     "serving": run_serving_workload(device)}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",

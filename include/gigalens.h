@@ -188,6 +188,39 @@ int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* l
                            double* grad_out, void* stream);
 
 /*
+ * Continuous batching (serving). A gl_batcher evaluates log-likelihood and
+ * gradient for up to max_segments (system, vector range) segments in one
+ * replay of a CUDA graph captured at creation. The graph's kernels use
+ * persistent grids and read the batch composition from a device-resident
+ * table, so every batch composition replays the same graph. The batcher owns
+ * the scratch of a batch: arena_bytes of device memory shared by all its
+ * segments (gl_batcher_segment_bytes gives one segment's share), so memory
+ * scales with the vectors in flight, not with the number of resident systems.
+ *
+ * gl_batcher_create - allocates the arena, the device table and two pinned
+ *   staging buffers, and captures the graph. Images up to max_H x max_W and
+ *   PSFs up to max_K (odd) are accepted later. Errors: GL_ERR_INVALID_ARG,
+ *   GL_ERR_UNSUPPORTED (max image too large for the shared-memory
+ *   convolution), GL_ERR_OOM, GL_ERR_CUDA.
+ *
+ * gl_batcher_run - one batch: for segment s, params[s] device float32
+ *   [B[s], 22], loglik_out[s] device float64 [B[s]], grad_out[s] device
+ *   float64 [B[s], 22], chi2_out NULL or per segment NULL / [B[s]]. A system
+ *   may appear in several segments. Host arrays are read before return; the
+ *   work is asynchronous on stream. All runs of one batcher must be issued on
+ *   one stream (they share the arena and the device table). The call blocks
+ *   only if the staging buffer it reuses is still being copied (two batches
+ *   back). Errors: GL_ERR_BUDGET if the segments' scratch exceeds the arena,
+ *   GL_ERR_UNSUPPORTED for a segment beyond max_H/max_W/max_K.
+ */
+typedef struct gl_batcher gl_batcher;
+int gl_batcher_create(gl_batcher** out, int max_segments, size_t arena_bytes, int max_H, int max_W, int max_K);
+int gl_batcher_destroy(gl_batcher* b);
+size_t gl_batcher_segment_bytes(const gl_system* sys, int B);
+int gl_batcher_run(gl_batcher* b, gl_system* const* systems, const float* const* params, const int* B,
+                   double* const* loglik_out, double* const* chi2_out, double* const* grad_out, int n, void* stream);
+
+/*
  * Hamiltonian Monte Carlo around the gradient (Sec. 2.5; Table 1 sampler
  * settings are the caller's). Chain state is FP64 on the device: positions
  * q [B, d], momenta p [B, d], log density logp [B], its gradient [B, d];

@@ -45,6 +45,10 @@ SIGNATURES = {
     "gl_simulate": ([_vp, _vp, _i, _vp, _vp], _i),
     "gl_loglik_grad_grouped": ([_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
     "gl_loglik_grad_noalloc": ([_vp, _vp, _i, _vp, _vp, _vp, _vp], _i),
+    "gl_batcher_create": ([ctypes.POINTER(_vp), _i, ctypes.c_size_t, _i, _i, _i], _i),
+    "gl_batcher_destroy": ([_vp], _i),
+    "gl_batcher_segment_bytes": ([_vp, _i], ctypes.c_size_t),
+    "gl_batcher_run": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
     "gl_hmc_leapfrog": ([_i, _i, _vp, _vp, _vp, _vp, _d, _d, _vp, _vp], _i),
     "gl_hmc_finish": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_error_string": ([_i], ctypes.c_char_p),
@@ -303,3 +307,44 @@ def loglik_grad_grouped(systems: Sequence[GLSystem], params: Sequence, grad: boo
                                                ctypes.addressof(gp) if grad else None, n, _stream_ptr(dev))
     _check(code, "gl_loglik_grad_grouped")
     return lls, grads, c2s
+
+
+class Batcher:
+    """Graph-replayed grouped launches over (system, vector range) segments."""
+
+    def __init__(self, max_segments: int, arena_bytes: int, max_H: int, max_W: int, max_K: int):
+        h = _vp()
+        _check(lib_handle().gl_batcher_create(ctypes.byref(h), int(max_segments), int(arena_bytes), int(max_H),
+                                              int(max_W), int(max_K)), "gl_batcher_create")
+        self._h = h.value
+        self.max_segments = int(max_segments)
+        self.arena_bytes = int(arena_bytes)
+
+    @staticmethod
+    def segment_bytes(system: GLSystem, B: int) -> int:
+        return int(lib_handle().gl_batcher_segment_bytes(system.handle, int(B)))
+
+    def run(self, systems, params_ptrs, Bs, loglik_ptrs, grad_ptrs, stream=None) -> None:
+        """One batch. params/loglik/grad are device pointers (ints) per segment."""
+        import torch
+        n = len(systems)
+        hs = (_vp * n)(*[s.handle for s in systems])
+        pp = (_vp * n)(*params_ptrs)
+        bb = (_i * n)(*Bs)
+        lp = (_vp * n)(*loglik_ptrs)
+        gp = (_vp * n)(*grad_ptrs)
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        _check(lib_handle().gl_batcher_run(self._h, ctypes.addressof(hs), ctypes.addressof(pp), ctypes.addressof(bb),
+                                           ctypes.addressof(lp), None, ctypes.addressof(gp), n, st),
+               "gl_batcher_run")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _check(lib_handle().gl_batcher_destroy(self._h), "gl_batcher_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

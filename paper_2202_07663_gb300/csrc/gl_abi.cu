@@ -224,6 +224,8 @@ int cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
 
 gl::Hooks* hooks() { return &g_prof; }
 
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 }  // namespace gl_internal
 
 extern "C" {

@@ -114,6 +114,16 @@ struct Seg {
   int conv_two_buf;        // 1: pixel adjoint kept in a second shared-memory buffer
 };
 
+// Header of a device-resident segment table whose item counts the kernels
+// read at run time (graph-replayed grouped launches).
+constexpr int N_CONV_CLASSES = 3;
+struct TableHdr {
+  int nseg, vec_total, ray_total, pad_;
+  int conv_first[N_CONV_CLASSES];
+  int conv_nseg[N_CONV_CLASSES];
+  int conv_total[N_CONV_CLASSES];
+};
+
 // ---------------------------------------------------------------- MUFU ----
 // Single hardware instructions of the special-function unit.
 __device__ __forceinline__ float ex2(float x) {

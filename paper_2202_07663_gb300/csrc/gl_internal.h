@@ -20,4 +20,7 @@ int cuda_error(cudaError_t e, const char* what);
 // Launch hooks of the library (launch counting, optional event timing).
 gl::Hooks* hooks();
 
+// Add kernels launched outside the hooks (graph replays) to the launch count.
+void count_launches(long long n);
+
 }  // namespace gl_internal

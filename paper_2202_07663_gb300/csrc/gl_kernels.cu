@@ -69,7 +69,40 @@ struct SegTable {
   }
 };
 
-// Copy a struct of 4-byte words into shared memory with the whole block.
+// Segment table and item counts in device memory, read when the kernels run,
+// so that one captured graph serves every batch composition.
+struct DevTable {
+  const TableHdr* hdr;
+  const Seg* segs;     // sorted by PSF class, then vec_begin / ray_begin ascending
+  int cls;             // convolution class of this launch (conv kernel only)
+  __device__ __forceinline__ int nvec() const { return hdr->vec_total; }
+  __device__ __forceinline__ int nray() const { return hdr->ray_total; }
+  __device__ __forceinline__ int nconv() const { return hdr->conv_total[cls]; }
+  __device__ __forceinline__ const Seg* vec_seg(int item, int& local) const {
+    const int n = hdr->nseg;
+    int lo = 0;
+    for (int i = 1; i < n; ++i) lo = (segs[i].vec_begin <= item) ? i : lo;
+    local = item - segs[lo].vec_begin;
+    return segs + lo;
+  }
+  __device__ __forceinline__ const Seg* ray_seg(int item, int& local) const {
+    const int n = hdr->nseg;
+    int lo = 0;
+    for (int i = 1; i < n; ++i) lo = (segs[i].ray_begin <= item) ? i : lo;
+    local = item - segs[lo].ray_begin;
+    return segs + lo;
+  }
+  __device__ __forceinline__ const Seg* conv_seg(int item, int& local) const {
+    const Seg* c = segs + hdr->conv_first[cls];
+    const int n = hdr->conv_nseg[cls];
+    int lo = 0;
+    for (int i = 1; i < n; ++i) lo = (c[i].conv_begin <= item) ? i : lo;
+    local = item - c[lo].conv_begin;
+    return c + lo;
+  }
+};
+
+// Copy a struct of 4-byte words into shared memory with the whole block.// Copy a struct of 4-byte words into shared memory with the whole block.
 template <class T>
 __device__ __forceinline__ void block_copy(T* dst, const T* src) {
   static_assert(sizeof(T) % 4 == 0, "word copy");
@@ -838,6 +871,49 @@ cudaError_t launch_table(const Seg* d_segs, int nseg, int vec_total, int ray_tot
   }
   if (mode != MODE_GRAD) return cudaSuccess;
   return run_rays(src, vec_total, ray_total, false, true, st, hooks, true);
+}
+
+// Grouped launch whose counts live in device memory: fixed persistent grids,
+// every convolution class launched (an empty class exits at once). Safe to
+// capture into a CUDA graph; conv_smem[c] is the dynamic shared memory of
+// class c and must cover every segment of that class.
+template <int K, int R, int NT, int MINB>
+static cudaError_t set_devtable_attr(size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_conv<K, R, NT, MINB, DevTable>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+cudaError_t prepare_devtable(const size_t* conv_smem) {
+  cudaError_t e;
+  if ((e = set_devtable_attr<11, 16, 128, 5>(conv_smem[0])) != cudaSuccess) return e;
+  if ((e = set_devtable_attr<21, 16, 256, 1>(conv_smem[1])) != cudaSuccess) return e;
+  return set_devtable_attr<0, 8, 128, 4>(conv_smem[2]);
+}
+
+cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size_t* conv_smem, cudaStream_t st,
+                            Hooks* hooks) {
+  const int sms = num_sms();
+  cudaError_t e;
+  DevTable src{d_hdr, d_segs, 0};
+  hooks->before(GL_K_SETUP, st);
+  k_setup<DevTable><<<sms * 4, 128, 0, st>>>(src);
+  if ((e = hooks->after(GL_K_SETUP, st)) != cudaSuccess) return e;
+  hooks->before(GL_K_RAY_FWD, st);
+  k_ray_fwd<DevTable><<<sms * GL_FWD_MINB, FWD_THREADS, 0, st>>>(src);
+  if ((e = hooks->after(GL_K_RAY_FWD, st)) != cudaSuccess) return e;
+  for (int c = 0; c < N_CONV_CLASSES; ++c) {
+    DevTable cs{d_hdr, d_segs, c};
+    hooks->before(GL_K_CONV, st);
+    e = launch_conv_class(c, cs, 1 << 30, conv_smem[c], MODE_GRAD, st, true);
+    if (e != cudaSuccess) return e;
+    if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
+  }
+  hooks->before(GL_K_RAY_ADJ, st);
+  k_ray_adj<DevTable><<<sms * GL_ADJ_MINB, ADJ_THREADS, 0, st>>>(src);
+  if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
+  hooks->before(GL_K_FINAL, st);
+  k_final<DevTable><<<sms, 128, 0, st>>>(src);
+  return hooks->after(GL_K_FINAL, st);
 }
 
 }  // namespace gl

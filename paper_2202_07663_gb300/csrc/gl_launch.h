@@ -52,4 +52,17 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks);
 cudaError_t launch_table(const Seg* d_segs, int nseg, int vec_total, int ray_total, const ConvRun* conv, int nconv,
                          int mode, cudaStream_t st, Hooks* hooks);
 
+struct TableHdr;
+
+// Set the kernel attributes a launch_devtable with these shared-memory sizes
+// needs (call before capturing it).
+cudaError_t prepare_devtable(const size_t* conv_smem);
+
+// Grouped launch reading its item counts from device memory (graph-capturable).
+cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size_t* conv_smem, cudaStream_t st,
+                            Hooks* hooks);
+
+// Kernels launched by one launch_devtable call.
+constexpr int DEVTABLE_LAUNCHES = 4 + CONV_CLASSES;
+
 }  // namespace gl
