@@ -165,6 +165,53 @@ def add_noise(rng: np.random.Generator, model: np.ndarray, sigma_bkg: float, gai
     return out + rng.normal(0.0, sigma_bkg, model.shape)
 
 
+# The paper's simulation distribution and (broader) prior, Eq. sim-dist
+# (Sec. 2.1.2), as samplers: ("n", mu, sd), ("ln", median, sd of log),
+# ("tn", mu, sd, lo, hi), ("u", lo, hi). Used to draw synthetic systems and
+# multi-start initial points; the methods evaluate their own densities.
+PAPER_SIM = [
+    ("ln", 1.25, 0.25), ("tn", 2.0, 0.25, 1.0, 3.0), ("n", 0.0, 0.1), ("n", 0.0, 0.1), ("n", 0.0, 0.03),
+    ("n", 0.0, 0.03), ("n", 0.0, 0.05), ("n", 0.0, 0.05),
+    ("ln", 1.6, 0.15), ("u", 2.0, 6.0), ("tn", 0.0, 0.05, -0.15, 0.15), ("tn", 0.0, 0.05, -0.15, 0.15),
+    ("n", 0.0, 0.01), ("n", 0.0, 0.01), ("ln", 300.0, 0.3),
+    ("ln", 0.25, 0.15), ("u", 0.5, 4.0), ("tn", 0.0, 0.15, -0.5, 0.5), ("tn", 0.0, 0.15, -0.5, 0.5),
+    ("n", 0.0, 0.25), ("n", 0.0, 0.25), ("ln", 150.0, 0.5),
+]
+PAPER_PRIOR_DRAW = [
+    ("ln", 1.25, 0.4), ("tn", 2.0, 0.5, 1.0, 3.0), ("n", 0.0, 0.2), ("n", 0.0, 0.2), ("n", 0.0, 0.06),
+    ("n", 0.0, 0.06), ("n", 0.0, 0.1), ("n", 0.0, 0.1),
+    ("ln", 1.6, 0.25), ("u", 0.5, 8.0), ("tn", 0.0, 0.1, -0.15, 0.15), ("tn", 0.0, 0.1, -0.15, 0.15),
+    ("n", 0.0, 0.02), ("n", 0.0, 0.02), ("ln", 300.0, 0.5),
+    ("ln", 0.25, 0.25), ("u", 0.5, 8.0), ("tn", 0.0, 0.3, -0.5, 0.5), ("tn", 0.0, 0.3, -0.5, 0.5),
+    ("n", 0.0, 0.5), ("n", 0.0, 0.5), ("ln", 150.0, 0.9),
+]
+
+# Sec. 3 simulated sample: 80x80 pixels at 0.065", sigma_bkg 0.2, t_exp 100 s, G = 1, k = 2
+PAPER_SAMPLE_SPEC = SystemSpec(80, 80, 2, 11, "gaussian", PIXEL_SCALE, 0.2, 100.0)
+
+
+def draw_table(rng: np.random.Generator, table, n: int) -> np.ndarray:
+    """n independent draws from a per-parameter distribution table."""
+    out = np.empty((n, len(table)))
+    for j, d in enumerate(table):
+        kind = d[0]
+        if kind == "n":
+            out[:, j] = rng.normal(d[1], d[2], n)
+        elif kind == "ln":
+            out[:, j] = np.exp(rng.normal(math.log(d[1]), d[2], n))
+        elif kind == "u":
+            out[:, j] = rng.uniform(d[1], d[2], n)
+        elif kind == "tn":
+            col = np.empty(0)
+            while col.size < n:   # rejection from the normal
+                x = rng.normal(d[1], d[2], 4 * n)
+                col = np.concatenate([col, x[(x >= d[3]) & (x <= d[4])]])
+            out[:, j] = col[:n]
+        else:
+            raise ValueError(kind)
+    return out
+
+
 @dataclasses.dataclass
 class LensRequest:
     """One request of the serving stream."""

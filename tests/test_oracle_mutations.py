@@ -66,3 +66,44 @@ def test_every_planted_mistake_fails_a_pin():
             results = dict(f.result() for f in futs)
     survivors = [n for n, rc in results.items() if rc == 0]
     assert not survivors, "mutants not caught by any pin: %s" % survivors
+
+
+MAP_MUTANTS = {
+    "prior_sd": ('("normal", 0.0, 0.06), ("normal", 0.0, 0.06),  # x_epl, y_epl',
+                 '("normal", 0.0, 0.03), ("normal", 0.0, 0.06),  # x_epl, y_epl'),
+    "lognormal_grad": ("g[:, j] = -(np.log(x) - math.log(e[1])) / (e[2] ** 2 * x) - 1.0 / x",
+                       "g[:, j] = -(np.log(x) - math.log(e[1])) / (e[2] ** 2 * x)"),
+    "sigmoid_jacobian": ("dlj[:, j] = 1.0 - 2.0 * s", "dlj[:, j] = 2.0 * s - 1.0"),
+    "objective_drops_logJ": ("f = -(np.asarray(loglik_theta) + lp + lj)", "f = -(np.asarray(loglik_theta) + lp)"),
+    "gradient_drops_dlogJ": ("g = -((np.asarray(grad_theta) + glp) * d + dlj)", "g = -((np.asarray(grad_theta) + glp) * d)"),
+    "adam_no_bias_correction": ("mhat = m / (1.0 - ADAM_B1 ** t)", "mhat = m"),
+    "schedule_reversed": ("return LR_START + (LR_END - LR_START) * frac", "return LR_END + (LR_START - LR_END) * frac"),
+    "sigmoid_bounds": ('return ("sigmoid", entry[3], entry[4])', 'return ("sigmoid", entry[4], entry[3])'),
+}
+
+
+def _run_map_mutant(name, old, new, tmp):
+    import shutil
+    dst = os.path.join(tmp, name)
+    shutil.copytree(ROOT, dst, ignore=shutil.ignore_patterns(".git", "_work", "gpurun_out", "*.so", "_build",
+                                                               "__pycache__", ".pytest_cache"))
+    path = os.path.join(dst, "oracle", "map_oracle.py")
+    src = open(path).read()
+    assert src.count(old) == 1, "mutation anchor for %s not unique/present" % name
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    import oracle as real
+    env = dict(os.environ, GL_ORACLE_LIB=real.build())
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(dst, "tests", "test_map_oracle.py")],
+                       cwd=dst, env=env, capture_output=True, text=True, timeout=600)
+    return name, r.returncode
+
+
+def test_every_planted_map_mistake_fails_a_pin():
+    with tempfile.TemporaryDirectory() as tmp:
+        with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+            futs = [ex.submit(_run_map_mutant, n, o, w, tmp) for n, (o, w) in MAP_MUTANTS.items()]
+            results = dict(f.result() for f in futs)
+    survivors = [n for n, rc in results.items() if rc == 0]
+    assert not survivors, "MAP mutants not caught by any pin: %s" % survivors
