@@ -279,6 +279,40 @@ def run_serving_workload(device, n_latency: int = 200, n_capacity: int = 1000):
             "speedup_lenses_per_s": cap.lenses_per_s / base_cap.lenses_per_s}
 
 
+def run_map_workload(device, n_starts: int = 300, steps=(300, 1000)):
+    """Sec. 2.3 / Table 1: multi-start MAP, 300 starts drawn from the prior, on
+    a system drawn from the paper's simulation distribution (80x80, k = 2,
+    sigma_bkg = 0.2, t_exp = 100 s, G = 1). Reports time and the fraction of
+    starts that end in the truth's basin (every parameter within 5% of
+    |truth| + 0.05)."""
+    import torch
+    from paper_2202_07663_gb300 import abi, map as gmap
+    spec = inputs.PAPER_SAMPLE_SPEC
+    rng = np.random.default_rng(202)
+    truth = inputs.draw_table(rng, inputs.PAPER_SIM, 1)[0]
+    psf = inputs.make_psf(spec).astype(np.float32)
+    blank = np.zeros((spec.H, spec.W), np.float32)
+    s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
+    s0.close()
+    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    s.reserve(n_starts)
+    th0 = torch.from_numpy(inputs.draw_table(np.random.default_rng(13), inputs.PAPER_PRIOR_DRAW,
+                                             n_starts).astype(np.float32)).to(device)
+    out = {"workload": "map-multistart-80x80-k2-psf11-paper-noise", "starts": n_starts, "runs": []}
+    for k in steps:
+        gmap.MultiStartMAP(s, steps=5).run(th0[:8])   # warm-up
+        r = gmap.MultiStartMAP(s, steps=k).run(th0)
+        th = r.theta.cpu().numpy()
+        in_basin = np.all(np.abs(th - truth[None]) / (np.abs(truth[None]) + 0.05) < 0.05, axis=1)
+        out["runs"].append({"iterations": k, "seconds": r.seconds, "evals_per_s": r.grad_evals / r.seconds,
+                            "fraction_in_truth_basin": float(in_basin.mean()),
+                            "best_objective": float(np.nanmin(r.objective.cpu().numpy()))})
+    s.close()
+    return out
+
+
 def cpu_baseline(spec, psf, image, params, budget_s: float = 12.0):
     """The FP64 oracle (log L + gradient) on a bounded sample of the same workload."""
     import oracle
@@ -457,7 +491,7 @@ def main():
     workloads = None
     if world == 1 and not args.no_workloads:
         workloads = {"hmc": run_hmc_workload(device), "stress": run_stress_workload(device),
-                     "serving": run_serving_workload(device)}
+                     "serving": run_serving_workload(device), "map": run_map_workload(device)}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",

@@ -221,6 +221,46 @@ int gl_batcher_run(gl_batcher* b, gl_system* const* systems, const float* const*
                    double* const* loglik_out, double* const* chi2_out, double* const* grad_out, int n, void* stream);
 
 /*
+ * Multi-start MAP (Sec. 2.3) in the unconstrained parameters of Sec. 2.2.
+ *
+ * gl_prior_entry describes one parameter's prior marginal (Eq. sim-dist):
+ *   GL_PRIOR_NORMAL       a = mean, b = standard deviation
+ *   GL_PRIOR_LOGNORMAL    a = median, b = standard deviation of the log
+ *   GL_PRIOR_TRUNCNORMAL  a = mean, b = standard deviation, [c, d] = support
+ *   GL_PRIOR_UNIFORM      [a, b] = support
+ * The bijector g (Sec. 2.2, Eq. exp, Eq. sigmoid) follows the support:
+ * exp for log-normal, a + (b - a) sigmoid(z) for truncated-normal and
+ * uniform, identity for normal. prior points to GL_NPARAM host entries.
+ *
+ * gl_map_inverse   - z = g^-1(theta) for theta device float32 [B, 22]
+ *                    (start points drawn in physical parameters).
+ * gl_map_transform - theta = g(z) as float32, for the likelihood call.
+ * gl_map_adam_step - given log L and d log L / d theta at theta = g(z)
+ *   (device float64 [B], [B, 22]), computes the objective
+ *   f(z) = -(log L + log p(g(z)) + log|J|) of Eq. obj-fun into
+ *   objective_out (may be NULL), its gradient in z, the Adam update
+ *   m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ *   z -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+ *   with step count t >= 1 (skipped when m and v are NULL), and writes
+ *   theta_out = g(z) after the update (may be NULL). State z, m, v is device
+ *   float64 [B, 22]. FP64 arithmetic, one warp per start.
+ */
+#define GL_PRIOR_NORMAL 0
+#define GL_PRIOR_LOGNORMAL 1
+#define GL_PRIOR_TRUNCNORMAL 2
+#define GL_PRIOR_UNIFORM 3
+typedef struct gl_prior_entry {
+  int kind;
+  int reserved;
+  double a, b, c, d;
+} gl_prior_entry;
+int gl_map_inverse(int B, const float* theta, const gl_prior_entry* prior, double* z_out, void* stream);
+int gl_map_transform(int B, const double* z, const gl_prior_entry* prior, float* theta_out, void* stream);
+int gl_map_adam_step(int B, double* z, double* m, double* v, int t, double lr, double beta1, double beta2, double eps,
+                     const double* loglik, const double* grad_theta, const gl_prior_entry* prior,
+                     double* objective_out, float* theta_out, void* stream);
+
+/*
  * Hamiltonian Monte Carlo around the gradient (Sec. 2.5; Table 1 sampler
  * settings are the caller's). Chain state is FP64 on the device: positions
  * q [B, d], momenta p [B, d], log density logp [B], its gradient [B, d];

@@ -49,6 +49,9 @@ SIGNATURES = {
     "gl_batcher_destroy": ([_vp], _i),
     "gl_batcher_segment_bytes": ([_vp, _i], ctypes.c_size_t),
     "gl_batcher_run": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp], _i),
+    "gl_map_inverse": ([_i, _vp, _vp, _vp, _vp], _i),
+    "gl_map_transform": ([_i, _vp, _vp, _vp, _vp], _i),
+    "gl_map_adam_step": ([_i, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_leapfrog": ([_i, _i, _vp, _vp, _vp, _vp, _d, _d, _vp, _vp], _i),
     "gl_hmc_finish": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_error_string": ([_i], ctypes.c_char_p),
@@ -59,6 +62,15 @@ SIGNATURES = {
     "gl_kernel_name": ([_i], ctypes.c_char_p),
     "gl_launch_count": ([], ctypes.c_longlong),
 }
+
+
+class PriorEntry(ctypes.Structure):
+    """gl_prior_entry of include/gigalens.h."""
+    _fields_ = [("kind", ctypes.c_int), ("reserved", ctypes.c_int), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("c", ctypes.c_double), ("d", ctypes.c_double)]
+
+
+GL_PRIOR_NORMAL, GL_PRIOR_LOGNORMAL, GL_PRIOR_TRUNCNORMAL, GL_PRIOR_UNIFORM = range(4)
 
 
 class GLError(RuntimeError):

@@ -1,0 +1,220 @@
+// gl_map.cu - multi-start MAP around the batched gradient (arXiv:2202.07663,
+// Sec. 2.2-2.3): component-wise bijectors, the prior's log density and the
+// Adam update, one warp per start, one lane per parameter, FP64.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "../../include/gigalens.h"
+#include "gl_internal.h"
+
+namespace {
+
+struct PriorTable {
+  gl_prior_entry e[GL_NPARAM];
+};
+
+constexpr double kLnSqrt2Pi = 0.91893853320467274178;
+
+// Bijector decided by the prior's support (Sec. 2.2): (0, inf) -> exp,
+// (a, b) -> a + (b - a) sigmoid(z), R -> identity.
+__device__ __forceinline__ void bij(const gl_prior_entry& e, double z, double& th, double& dth, double& lj,
+                                    double& dlj) {
+  if (e.kind == GL_PRIOR_LOGNORMAL) {
+    th = exp(z);
+    dth = th;
+    lj = z;
+    dlj = 1.0;
+  } else if (e.kind == GL_PRIOR_TRUNCNORMAL || e.kind == GL_PRIOR_UNIFORM) {
+    const double lo = e.kind == GL_PRIOR_UNIFORM ? e.a : e.c, hi = e.kind == GL_PRIOR_UNIFORM ? e.b : e.d;
+    const double s = 1.0 / (1.0 + exp(-z));
+    th = lo + (hi - lo) * s;
+    dth = (hi - lo) * s * (1.0 - s);
+    // log s + log(1 - s) = -softplus(-z) - softplus(z)
+    const double sp_p = z > 0 ? z + log1p(exp(-z)) : log1p(exp(z));
+    const double sp_m = z > 0 ? log1p(exp(-z)) : -z + log1p(exp(z));
+    lj = log(hi - lo) - sp_m - sp_p;
+    dlj = 1.0 - 2.0 * s;
+  } else {
+    th = z;
+    dth = 1.0;
+    lj = 0.0;
+    dlj = 0.0;
+  }
+}
+
+__device__ __forceinline__ double inv_bij(const gl_prior_entry& e, double th) {
+  if (e.kind == GL_PRIOR_LOGNORMAL) return log(th);
+  if (e.kind == GL_PRIOR_TRUNCNORMAL || e.kind == GL_PRIOR_UNIFORM) {
+    const double lo = e.kind == GL_PRIOR_UNIFORM ? e.a : e.c, hi = e.kind == GL_PRIOR_UNIFORM ? e.b : e.d;
+    const double s = (th - lo) / (hi - lo);
+    return log(s) - log1p(-s);
+  }
+  return th;
+}
+
+// log density of one prior marginal and its derivative (Eq. sim-dist).
+__device__ __forceinline__ void logpdf(const gl_prior_entry& e, double x, double& lp, double& dlp) {
+  switch (e.kind) {
+    case GL_PRIOR_NORMAL: {
+      const double r = (x - e.a) / e.b;
+      lp = -0.5 * r * r - log(e.b) - kLnSqrt2Pi;
+      dlp = -r / e.b;
+      break;
+    }
+    case GL_PRIOR_LOGNORMAL: {
+      const double r = (log(x) - log(e.a)) / e.b;
+      lp = -0.5 * r * r - log(x) - log(e.b) - kLnSqrt2Pi;
+      dlp = -r / (e.b * x) - 1.0 / x;
+      break;
+    }
+    case GL_PRIOR_TRUNCNORMAL: {
+      const double r = (x - e.a) / e.b;
+      const double Z = 0.5 * (erf((e.d - e.a) / (e.b * 1.41421356237309504880)) -
+                              erf((e.c - e.a) / (e.b * 1.41421356237309504880)));
+      const bool in = x >= e.c && x <= e.d;
+      lp = in ? -0.5 * r * r - log(e.b) - kLnSqrt2Pi - log(Z) : -INFINITY;
+      dlp = -r / e.b;
+      break;
+    }
+    default: {  // uniform
+      const bool in = x >= e.a && x <= e.b;
+      lp = in ? -log(e.b - e.a) : -INFINITY;
+      dlp = 0.0;
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_map_inverse(int B, const float* __restrict__ theta, double* __restrict__ z, PriorTable P) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb)
+    if (lane < GL_NPARAM) z[size_t(b) * GL_NPARAM + lane] = inv_bij(P.e[lane], double(theta[size_t(b) * GL_NPARAM + lane]));
+}
+
+__global__ void k_map_transform(int B, const double* __restrict__ z, float* __restrict__ theta, PriorTable P) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb)
+    if (lane < GL_NPARAM) {
+      double th, d, lj, dlj;
+      bij(P.e[lane], z[size_t(b) * GL_NPARAM + lane], th, d, lj, dlj);
+      theta[size_t(b) * GL_NPARAM + lane] = float(th);
+    }
+}
+
+// Objective f(z) = -(log L + log p(g(z)) + log|J|) at the current z (Eq.
+// obj-fun), its gradient, the Adam update (when m != null) and g(z_new).
+__global__ void k_map_step(int B, double* __restrict__ z, double* __restrict__ m, double* __restrict__ v, double c1,
+                           double c2, double lr, double b1, double b2, double eps, const double* __restrict__ loglik,
+                           const double* __restrict__ grad, double* __restrict__ f_out, float* __restrict__ theta,
+                           PriorTable P) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb) {
+    const size_t i = size_t(b) * GL_NPARAM + lane;
+    double part = 0.0, g = 0.0, zj = 0.0;
+    if (lane < GL_NPARAM) {
+      zj = z[i];
+      double th, d, lj, dlj, lp, dlp;
+      bij(P.e[lane], zj, th, d, lj, dlj);
+      logpdf(P.e[lane], th, lp, dlp);
+      part = lp + lj;
+      g = -((grad[i] + dlp) * d + dlj);
+    }
+    const double tot = warp_sum(part);
+    if (lane == 0 && f_out) f_out[b] = -(loglik[b] + tot);
+    if (lane < GL_NPARAM) {
+      if (m) {
+        const double mi = b1 * m[i] + (1.0 - b1) * g;
+        const double vi = b2 * v[i] + (1.0 - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        zj -= lr * (mi / c1) / (sqrt(vi / c2) + eps);
+        z[i] = zj;
+      }
+      if (theta) {
+        double th, d, lj, dlj;
+        bij(P.e[lane], zj, th, d, lj, dlj);
+        theta[i] = float(th);
+      }
+    }
+  }
+}
+
+int grid_for(int B) {
+  const int g = (B + 3) / 4;
+  return g < 1 ? 1 : (g > 4096 ? 4096 : g);
+}
+
+int table(const gl_prior_entry* prior, PriorTable& P) {
+  if (!prior) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null prior");
+  for (int j = 0; j < GL_NPARAM; ++j) {
+    const gl_prior_entry& e = prior[j];
+    const bool ok = (e.kind == GL_PRIOR_NORMAL && e.b > 0) || (e.kind == GL_PRIOR_LOGNORMAL && e.a > 0 && e.b > 0) ||
+                    (e.kind == GL_PRIOR_TRUNCNORMAL && e.b > 0 && e.c < e.d) ||
+                    (e.kind == GL_PRIOR_UNIFORM && e.a < e.b);
+    if (!ok) return gl_internal::set_error(GL_ERR_INVALID_ARG, "bad prior entry");
+    P.e[j] = e;
+  }
+  return GL_OK;
+}
+
+int finish(cudaStream_t st, const char* what) {
+  cudaError_t e = gl_internal::hooks()->after(GL_K_OTHER, st);
+  return e == cudaSuccess ? GL_OK : gl_internal::cuda_error(e, what);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gl_map_inverse(int B, const float* theta, const gl_prior_entry* prior, double* z_out, void* stream) {
+  PriorTable P;
+  int rc = table(prior, P);
+  if (rc != GL_OK) return rc;
+  if (B < 0) return gl_internal::set_error(GL_ERR_INVALID_ARG, "B < 0");
+  if (B == 0) return GL_OK;
+  if (!theta || !z_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gl_internal::hooks()->before(GL_K_OTHER, st);
+  k_map_inverse<<<grid_for(B), 128, 0, st>>>(B, theta, z_out, P);
+  return finish(st, "k_map_inverse");
+}
+
+int gl_map_transform(int B, const double* z, const gl_prior_entry* prior, float* theta_out, void* stream) {
+  PriorTable P;
+  int rc = table(prior, P);
+  if (rc != GL_OK) return rc;
+  if (B < 0) return gl_internal::set_error(GL_ERR_INVALID_ARG, "B < 0");
+  if (B == 0) return GL_OK;
+  if (!z || !theta_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gl_internal::hooks()->before(GL_K_OTHER, st);
+  k_map_transform<<<grid_for(B), 128, 0, st>>>(B, z, theta_out, P);
+  return finish(st, "k_map_transform");
+}
+
+int gl_map_adam_step(int B, double* z, double* m, double* v, int t, double lr, double beta1, double beta2, double eps,
+                     const double* loglik, const double* grad_theta, const gl_prior_entry* prior,
+                     double* objective_out, float* theta_out, void* stream) {
+  PriorTable P;
+  int rc = table(prior, P);
+  if (rc != GL_OK) return rc;
+  if (B < 0) return gl_internal::set_error(GL_ERR_INVALID_ARG, "B < 0");
+  if (B == 0) return GL_OK;
+  if (!z || !loglik || !grad_theta) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if ((m == nullptr) != (v == nullptr)) return gl_internal::set_error(GL_ERR_INVALID_ARG, "m and v go together");
+  if (m && t < 1) return gl_internal::set_error(GL_ERR_INVALID_ARG, "Adam step count t starts at 1");
+  const double c1 = m ? 1.0 - pow(beta1, t) : 1.0, c2 = m ? 1.0 - pow(beta2, t) : 1.0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gl_internal::hooks()->before(GL_K_OTHER, st);
+  k_map_step<<<grid_for(B), 128, 0, st>>>(B, z, m, v, c1, c2, lr, beta1, beta2, eps, loglik, grad_theta,
+                                          objective_out, theta_out, P);
+  return finish(st, "k_map_step");
+}
+
+}  // extern "C"

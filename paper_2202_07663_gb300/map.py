@@ -1,0 +1,116 @@
+"""Multi-start MAP (arXiv:2202.07663, Sec. 2.3) on the GPU.
+
+n starts drawn from the prior are optimised simultaneously with Adam in the
+unconstrained parameters of Sec. 2.2; every iteration is one batched
+log-likelihood + gradient call (the hot path) and one fused CUDA step that
+adds the prior and the log-Jacobian of the bijector, takes the Adam update
+and maps the new points back to physical parameters (``gl_map_*``). Table 1:
+300 starts, 300 iterations, learning rate 1e-2 -> 1e-3 linearly.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import time
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import abi
+
+NPARAM = abi.NPARAM
+
+# Prior of Eq. sim-dist (the broader values used for modelling), Table 2 order.
+_N, _LN, _TN, _U = abi.GL_PRIOR_NORMAL, abi.GL_PRIOR_LOGNORMAL, abi.GL_PRIOR_TRUNCNORMAL, abi.GL_PRIOR_UNIFORM
+PAPER_PRIOR = [
+    (_LN, 1.25, 0.4, 0, 0),        # theta_E ~ exp(N(ln 1.25, 0.4))
+    (_TN, 2.0, 0.5, 1.0, 3.0),     # gamma_epl ~ TN(2, 0.5; 1, 3)
+    (_N, 0.0, 0.2, 0, 0), (_N, 0.0, 0.2, 0, 0),       # e_epl1, e_epl2 ~ N(0, 0.2)
+    (_N, 0.0, 0.06, 0, 0), (_N, 0.0, 0.06, 0, 0),     # x_epl, y_epl ~ N(0, 0.06)
+    (_N, 0.0, 0.1, 0, 0), (_N, 0.0, 0.1, 0, 0),       # gamma_ext ~ N(0, 0.1)
+    (_LN, 1.6, 0.25, 0, 0),        # R_l ~ exp(N(ln 1.6, 0.25))
+    (_U, 0.5, 8.0, 0, 0),          # n_l ~ U(0.5, 8)
+    (_TN, 0.0, 0.1, -0.15, 0.15), (_TN, 0.0, 0.1, -0.15, 0.15),   # e_l ~ TN(0, 0.1; +-0.15)
+    (_N, 0.0, 0.02, 0, 0), (_N, 0.0, 0.02, 0, 0),     # x_l, y_l ~ N(0, 0.02)
+    (_LN, 300.0, 0.5, 0, 0),       # I_l ~ exp(N(ln 300, 0.5))
+    (_LN, 0.25, 0.25, 0, 0),       # R_s ~ exp(N(ln 0.25, 0.25))
+    (_U, 0.5, 8.0, 0, 0),          # n_s ~ U(0.5, 8)
+    (_TN, 0.0, 0.3, -0.5, 0.5), (_TN, 0.0, 0.3, -0.5, 0.5),       # e_s ~ TN(0, 0.3; +-0.5)
+    (_N, 0.0, 0.5, 0, 0), (_N, 0.0, 0.5, 0, 0),       # x_s, y_s ~ N(0, 0.5)
+    (_LN, 150.0, 0.9, 0, 0),       # I_s ~ exp(N(ln 150, 0.9))
+]
+
+ADAM = (0.9, 0.999, 1e-8)
+
+
+def prior_table(entries=PAPER_PRIOR):
+    arr = (abi.PriorEntry * NPARAM)()
+    for j, (kind, a, b, c, d) in enumerate(entries):
+        arr[j] = abi.PriorEntry(kind, 0, a, b, c, d)
+    return arr
+
+
+def linear_lr(t: int, start: float = 1e-2, end: float = 1e-3, steps: int = 300) -> float:
+    return start + (end - start) * min(t, steps) / steps
+
+
+@dataclasses.dataclass
+class MAPResult:
+    theta: torch.Tensor        # [n, 22] physical, float32 (last point)
+    z: torch.Tensor            # [n, 22] unconstrained, float64
+    objective: torch.Tensor    # [n] objective at the last point, float64
+    history: Optional[torch.Tensor]   # [steps, n] objective at each iterate, or None
+    seconds: float
+    grad_evals: int
+
+    @property
+    def best(self) -> int:
+        f = torch.nan_to_num(self.objective, nan=float("inf"))
+        return int(torch.argmin(f).item())
+
+
+class MultiStartMAP:
+    """Adam on f(z) = -(log L + log p + log|J|) for n starts of one lens system."""
+
+    def __init__(self, system, prior=PAPER_PRIOR, steps: int = 300, lr=(1e-2, 1e-3)):
+        self.system = system
+        self.prior = prior_table(prior)
+        self.steps = int(steps)
+        self.lr = lr
+
+    def _ptr(self):
+        return ctypes.addressof(self.prior)
+
+    def run(self, theta0: torch.Tensor, record: bool = False) -> MAPResult:
+        dev = theta0.device
+        n = theta0.shape[0]
+        st = torch.cuda.current_stream(dev).cuda_stream
+        lib = abi.lib_handle()
+        f64 = dict(dtype=torch.float64, device=dev)
+        z = torch.empty(n, NPARAM, **f64)
+        m = torch.zeros(n, NPARAM, **f64)
+        v = torch.zeros(n, NPARAM, **f64)
+        th = theta0.to(torch.float32).contiguous().clone()
+        ll = torch.empty(n, **f64)
+        g = torch.empty(n, NPARAM, **f64)
+        f = torch.empty(n, **f64)
+        hist = torch.empty(self.steps, n, **f64) if record else None
+        abi._check(lib.gl_map_inverse(n, th.data_ptr(), self._ptr(), z.data_ptr(), st), "gl_map_inverse")
+        abi._check(lib.gl_map_transform(n, z.data_ptr(), self._ptr(), th.data_ptr(), st), "gl_map_transform")
+        b1, b2, eps = ADAM
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for t in range(self.steps):
+            self.system.loglik_grad(th, out=(ll, g, None))
+            fo = hist[t] if record else f
+            abi._check(lib.gl_map_adam_step(n, z.data_ptr(), m.data_ptr(), v.data_ptr(), t + 1,
+                                            linear_lr(t, self.lr[0], self.lr[1], self.steps), b1, b2, eps,
+                                            ll.data_ptr(), g.data_ptr(), self._ptr(), fo.data_ptr(), th.data_ptr(),
+                                            st), "gl_map_adam_step")
+        self.system.loglik_grad(th, out=(ll, g, None))
+        abi._check(lib.gl_map_adam_step(n, z.data_ptr(), None, None, 0, 0.0, b1, b2, eps, ll.data_ptr(),
+                                        g.data_ptr(), self._ptr(), f.data_ptr(), None, st), "gl_map_adam_step")
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        return MAPResult(th, z, f, hist, dt, n * (self.steps + 1))
