@@ -261,6 +261,16 @@ int gl_map_adam_step(int B, double* z, double* m, double* v, int t, double lr, d
                      double* objective_out, float* theta_out, void* stream);
 
 /*
+ * gl_posterior_grad - the log density of the unconstrained parameters,
+ *   log p~(z) = log L + log p(g(z)) + log|J| (Eq. reparam-post; the
+ *   negative of the MAP objective), and its gradient in z, given log L and
+ *   d log L / d theta at theta = g(z). logp_out device float64 [B],
+ *   grad_z_out device float64 [B, 22]. Used by HMC on the posterior.
+ */
+int gl_posterior_grad(int B, const double* z, const double* loglik, const double* grad_theta,
+                      const gl_prior_entry* prior, double* logp_out, double* grad_z_out, void* stream);
+
+/*
  * Hamiltonian Monte Carlo around the gradient (Sec. 2.5; Table 1 sampler
  * settings are the caller's). Chain state is FP64 on the device: positions
  * q [B, d], momenta p [B, d], log density logp [B], its gradient [B, d];
@@ -269,14 +279,17 @@ int gl_map_adam_step(int B, double* z, double* m, double* v, int t, double lr, d
  *
  * gl_hmc_leapfrog - one leapfrog update: p += kick * eps * grad, then
  *   q += eps * inv_mass * p, and q32_out = (float)q for the next likelihood
- *   call. kick = 0.5 for the first step of a trajectory, 1 afterwards (the
- *   half kicks at both ends of consecutive steps merged).
+ *   call (q32_out may be NULL when q is not the likelihood's input, e.g.
+ *   unconstrained parameters). kick = 0.5 for the first step of a
+ *   trajectory, 1 afterwards (the half kicks at both ends of consecutive
+ *   steps merged).
  *
  * gl_hmc_finish - last half kick p += eps/2 * grad_new, Hamiltonians
  *   H = -logp + 1/2 sum p^2 inv_mass of the start (p0, logp0) and end
  *   (p, logp_new) points in FP64, accept where log_u < H_start - H_end (and
  *   both are finite); accepted chains copy q_new, logp_new, grad_new into q,
- *   logp, grad. accepted[b] is 1 or 0.
+ *   logp, grad. accepted[b] is 1 or 0; accept_prob[b] (may be NULL) receives
+ *   min(1, exp(H_start - H_end)), 0 for a non-finite Hamiltonian.
  *
  * All pointers are device memory; asynchronous on stream; 1 <= d <= 4096.
  */
@@ -284,7 +297,27 @@ int gl_hmc_leapfrog(int B, int d, double* q, double* p, const double* grad, cons
                     double kick, float* q32_out, void* stream);
 int gl_hmc_finish(int B, int d, const double* p0, const double* logp0, double* p, const double* grad_new,
                   const double* logp_new, const double* q_new, const double* inv_mass, const double* log_u,
-                  double eps, double* q, double* logp, double* grad, int* accepted, void* stream);
+                  double eps, double* q, double* logp, double* grad, int* accepted, double* accept_prob,
+                  void* stream);
+
+/*
+ * Dense preconditioning (Sec. 2.5: the mass matrix set to the inverse of a
+ * posterior covariance Sigma = L L^T, e.g. the variational one). HMC with
+ * identity mass on whitened coordinates x is HMC with mass Sigma^-1 on
+ * z = mu + L x, so the sampler keeps its diagonal kernels and the target
+ * maps through these two calls.
+ *
+ * gl_hmc_affine - z_out = mu + L x per chain; L lower triangular, row-major
+ *   d x d float64 (entries above the diagonal are ignored); z32_out
+ *   (may be NULL) receives (float)z. x [B, d], mu [d], z_out [B, d].
+ * gl_hmc_affine_pullback - grad_x_out = L^T grad_z per chain.
+ *
+ * Device pointers; outputs must not alias inputs; 1 <= d <= GL_HMC_AFFINE_MAX_D.
+ */
+#define GL_HMC_AFFINE_MAX_D 64
+int gl_hmc_affine(int B, int d, const double* x, const double* mu, const double* L, double* z_out, float* z32_out,
+                  void* stream);
+int gl_hmc_affine_pullback(int B, int d, const double* grad_z, const double* L, double* grad_x_out, void* stream);
 
 /* Name of a status code (static string). */
 const char* gl_error_string(int code);

@@ -53,7 +53,10 @@ SIGNATURES = {
     "gl_map_transform": ([_i, _vp, _vp, _vp, _vp], _i),
     "gl_map_adam_step": ([_i, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_leapfrog": ([_i, _i, _vp, _vp, _vp, _vp, _d, _d, _vp, _vp], _i),
-    "gl_hmc_finish": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp], _i),
+    "gl_hmc_finish": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "gl_hmc_affine": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "gl_hmc_affine_pullback": ([_i, _i, _vp, _vp, _vp, _vp], _i),
+    "gl_posterior_grad": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_error_string": ([_i], ctypes.c_char_p),
     "gl_last_error_message": ([], ctypes.c_char_p),
     "gl_profile_enable": ([_i], _i),
@@ -171,9 +174,17 @@ def gl_hmc_leapfrog(B, d, q, p, grad, inv_mass, eps, kick, q32, stream):
 
 
 def gl_hmc_finish(B, d, p0, logp0, p, grad_new, logp_new, q_new, inv_mass, log_u, eps, q, logp, grad, accepted,
-                  stream):
+                  stream, accept_prob=None):
     _check(lib_handle().gl_hmc_finish(B, d, p0, logp0, p, grad_new, logp_new, q_new, inv_mass, log_u, float(eps), q,
-                                      logp, grad, accepted, stream), "gl_hmc_finish")
+                                      logp, grad, accepted, accept_prob, stream), "gl_hmc_finish")
+
+
+def gl_hmc_affine(B, d, x, mu, L, z, z32, stream):
+    _check(lib_handle().gl_hmc_affine(B, d, x, mu, L, z, z32, stream), "gl_hmc_affine")
+
+
+def gl_hmc_affine_pullback(B, d, grad_z, L, grad_x, stream):
+    _check(lib_handle().gl_hmc_affine_pullback(B, d, grad_z, L, grad_x, stream), "gl_hmc_affine_pullback")
 
 
 def gl_profile_enable(on: bool) -> None:

@@ -23,7 +23,7 @@ __global__ void k_hmc_leapfrog(int n, int d, double* __restrict__ q, double* __r
     const double qi = q[i] + eps * inv_mass[i % d] * pi;
     p[i] = pi;
     q[i] = qi;
-    q32[i] = float(qi);
+    if (q32) q32[i] = float(qi);
   }
 }
 
@@ -34,7 +34,7 @@ __global__ void k_hmc_finish(int B, int d, const double* __restrict__ p0, const 
                              const double* __restrict__ logp_new, const double* __restrict__ q_new,
                              const double* __restrict__ inv_mass, const double* __restrict__ log_u, double eps,
                              double* __restrict__ q, double* __restrict__ logp, double* __restrict__ grad,
-                             int* __restrict__ accepted) {
+                             int* __restrict__ accepted, double* __restrict__ accept_prob) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb) {
@@ -64,6 +64,45 @@ __global__ void k_hmc_finish(int B, int d, const double* __restrict__ p0, const 
     if (lane == 0) {
       if (acc) logp[b] = logp_new[b];
       accepted[b] = acc ? 1 : 0;
+      if (accept_prob) accept_prob[b] = (isfinite(h1) && isfinite(h0)) ? fmin(1.0, exp(h0 - h1)) : 0.0;
+    }
+  }
+}
+
+// Whitened coordinates for a dense preconditioner: z = mu + L x with L lower
+// triangular (row-major d x d), and the gradient pull-back g_x = L^T g_z.
+// One warp per chain; L staged in shared memory.
+__global__ void k_affine(int B, int d, const double* __restrict__ x, const double* __restrict__ mu,
+                         const double* __restrict__ Lc, double* __restrict__ z, float* __restrict__ z32) {
+  extern __shared__ double sL[];
+  for (int i = threadIdx.x; i < d * d; i += blockDim.x) sL[i] = Lc[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb) {
+    const double* xb = x + size_t(b) * d;
+    for (int i = lane; i < d; i += 32) {
+      double acc = mu[i];
+      for (int j = 0; j <= i; ++j) acc += sL[i * d + j] * xb[j];
+      z[size_t(b) * d + i] = acc;
+      if (z32) z32[size_t(b) * d + i] = float(acc);
+    }
+  }
+}
+
+__global__ void k_affine_pullback(int B, int d, const double* __restrict__ gz, const double* __restrict__ Lc,
+                                  double* __restrict__ gx) {
+  extern __shared__ double sL[];
+  for (int i = threadIdx.x; i < d * d; i += blockDim.x) sL[i] = Lc[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb) {
+    const double* gb = gz + size_t(b) * d;
+    for (int j = lane; j < d; j += 32) {
+      double acc = 0.0;
+      for (int i = j; i < d; ++i) acc += sL[i * d + j] * gb[i];
+      gx[size_t(b) * d + j] = acc;
     }
   }
 }
@@ -81,8 +120,7 @@ int gl_hmc_leapfrog(int B, int d, double* q, double* p, const double* grad, cons
                     double kick, float* q32_out, void* stream) {
   if (B < 0 || d < 1 || d > 4096) return gl_internal::set_error(GL_ERR_INVALID_ARG, "bad B or d");
   if (B == 0) return GL_OK;
-  if (!q || !p || !grad || !inv_mass || !q32_out)
-    return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if (!q || !p || !grad || !inv_mass) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
   if (!std::isfinite(eps) || !std::isfinite(kick)) return gl_internal::set_error(GL_ERR_INVALID_ARG, "eps or kick");
   const long long n = (long long)B * d;
   gl::Hooks* h = gl_internal::hooks();
@@ -95,7 +133,7 @@ int gl_hmc_leapfrog(int B, int d, double* q, double* p, const double* grad, cons
 
 int gl_hmc_finish(int B, int d, const double* p0, const double* logp0, double* p, const double* grad_new,
                   const double* logp_new, const double* q_new, const double* inv_mass, const double* log_u, double eps,
-                  double* q, double* logp, double* grad, int* accepted, void* stream) {
+                  double* q, double* logp, double* grad, int* accepted, double* accept_prob, void* stream) {
   if (B < 0 || d < 1 || d > 4096) return gl_internal::set_error(GL_ERR_INVALID_ARG, "bad B or d");
   if (B == 0) return GL_OK;
   if (!p0 || !logp0 || !p || !grad_new || !logp_new || !q_new || !inv_mass || !log_u || !q || !logp || !grad ||
@@ -105,9 +143,39 @@ int gl_hmc_finish(int B, int d, const double* p0, const double* logp0, double* p
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->before(GL_K_OTHER, st);
   k_hmc_finish<<<grid_for((long long)B * 32, 128), 128, 0, st>>>(B, d, p0, logp0, p, grad_new, logp_new, q_new,
-                                                                  inv_mass, log_u, eps, q, logp, grad, accepted);
+                                                                  inv_mass, log_u, eps, q, logp, grad, accepted,
+                                                                  accept_prob);
   cudaError_t e = h->after(GL_K_OTHER, st);
   return e == cudaSuccess ? GL_OK : gl_internal::cuda_error(e, "k_hmc_finish");
+}
+
+int gl_hmc_affine(int B, int d, const double* x, const double* mu, const double* L, double* z_out, float* z32_out,
+                  void* stream) {
+  if (B < 0 || d < 1 || d > GL_HMC_AFFINE_MAX_D) return gl_internal::set_error(GL_ERR_INVALID_ARG, "bad B or d");
+  if (B == 0) return GL_OK;
+  if (!x || !mu || !L || !z_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if (x == z_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "x and z_out alias");
+  gl::Hooks* h = gl_internal::hooks();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->before(GL_K_OTHER, st);
+  k_affine<<<grid_for((long long)B * 32, 128), 128, size_t(d) * d * sizeof(double), st>>>(B, d, x, mu, L, z_out,
+                                                                                           z32_out);
+  cudaError_t e = h->after(GL_K_OTHER, st);
+  return e == cudaSuccess ? GL_OK : gl_internal::cuda_error(e, "k_affine");
+}
+
+int gl_hmc_affine_pullback(int B, int d, const double* grad_z, const double* L, double* grad_x_out, void* stream) {
+  if (B < 0 || d < 1 || d > GL_HMC_AFFINE_MAX_D) return gl_internal::set_error(GL_ERR_INVALID_ARG, "bad B or d");
+  if (B == 0) return GL_OK;
+  if (!grad_z || !L || !grad_x_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if (grad_z == grad_x_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "grad_z and grad_x_out alias");
+  gl::Hooks* h = gl_internal::hooks();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->before(GL_K_OTHER, st);
+  k_affine_pullback<<<grid_for((long long)B * 32, 128), 128, size_t(d) * d * sizeof(double), st>>>(B, d, grad_z, L,
+                                                                                                    grad_x_out);
+  cudaError_t e = h->after(GL_K_OTHER, st);
+  return e == cudaSuccess ? GL_OK : gl_internal::cuda_error(e, "k_affine_pullback");
 }
 
 }  // extern "C"

@@ -145,6 +145,26 @@ __global__ void k_map_step(int B, double* __restrict__ z, double* __restrict__ m
   }
 }
 
+// log p~(z) = log L + log p(g(z)) + log|J| (Eq. reparam-post) and its gradient in z.
+__global__ void k_posterior(int B, const double* __restrict__ z, const double* __restrict__ loglik,
+                            const double* __restrict__ grad, double* __restrict__ logp_out,
+                            double* __restrict__ grad_z, PriorTable P) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb) {
+    const size_t i = size_t(b) * GL_NPARAM + lane;
+    double part = 0.0;
+    if (lane < GL_NPARAM) {
+      double th, d, lj, dlj, lp, dlp;
+      bij(P.e[lane], z[i], th, d, lj, dlj);
+      logpdf(P.e[lane], th, lp, dlp);
+      part = lp + lj;
+      grad_z[i] = (grad[i] + dlp) * d + dlj;
+    }
+    const double tot = warp_sum(part);
+    if (lane == 0) logp_out[b] = loglik[b] + tot;
+  }
+}
+
 int grid_for(int B) {
   const int g = (B + 3) / 4;
   return g < 1 ? 1 : (g > 4096 ? 4096 : g);
@@ -215,6 +235,21 @@ int gl_map_adam_step(int B, double* z, double* m, double* v, int t, double lr, d
   k_map_step<<<grid_for(B), 128, 0, st>>>(B, z, m, v, c1, c2, lr, beta1, beta2, eps, loglik, grad_theta,
                                           objective_out, theta_out, P);
   return finish(st, "k_map_step");
+}
+
+int gl_posterior_grad(int B, const double* z, const double* loglik, const double* grad_theta,
+                      const gl_prior_entry* prior, double* logp_out, double* grad_z_out, void* stream) {
+  PriorTable P;
+  int rc = table(prior, P);
+  if (rc != GL_OK) return rc;
+  if (B < 0) return gl_internal::set_error(GL_ERR_INVALID_ARG, "B < 0");
+  if (B == 0) return GL_OK;
+  if (!z || !loglik || !grad_theta || !logp_out || !grad_z_out)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gl_internal::hooks()->before(GL_K_OTHER, st);
+  k_posterior<<<grid_for(B), 128, 0, st>>>(B, z, loglik, grad_theta, logp_out, grad_z_out, P);
+  return finish(st, "k_posterior");
 }
 
 }  // extern "C"

@@ -6,17 +6,30 @@ gradient; the adjoint recomputes every ray, none is stored) and its backward
 scales the stashed gradient by the incoming one.
 
 ``HMC`` runs many chains of Hamiltonian Monte Carlo (arXiv:2202.07663,
-Sec. 2.5) on the log-likelihood as log density: leapfrog updates and the FP64
-Hamiltonian/accept step are the library's CUDA kernels (``gl_hmc_*``); the
-random numbers (momenta, accept uniforms) come from a seeded torch generator
-and are passed in. The mass matrix is diagonal.
+Sec. 2.5): leapfrog updates and the FP64 Hamiltonian/accept step are the
+library's CUDA kernels (``gl_hmc_*``); the random numbers (momenta, accept
+uniforms) come from a seeded torch generator and are passed in. The mass
+matrix is diagonal. Targets:
+
+- ``LensTarget``: log L in the physical parameters (the config-3 workload);
+- ``PosteriorTarget``: the posterior of the unconstrained parameters,
+  log p~(z) = log L(g(z)) + log p(g(z)) + log|J| (Eq. reparam-post), through
+  ``gl_map_transform`` and ``gl_posterior_grad`` — the paper's sampler;
+- ``FunctionTarget``: any ``logp_grad(q32) -> (logp, grad)`` (tests).
+
+``run_adaptive`` adapts the step size by dual averaging (Hoffman & Gelman
+2014) during the first 80% of burn-in toward a target acceptance
+probability (0.75, Sec. 2.5), then fixes it.
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 import math
-from typing import Callable, Optional, Tuple
+import time
+from typing import Callable, Optional
 
+import numpy as np
 import torch
 
 from . import abi
@@ -48,6 +61,93 @@ def loglik(params, system):
     return LogLik.apply(params, system)
 
 
+# ------------------------------------------------------------- targets ----
+
+class LensTarget:
+    """log L in the physical parameters; consumes the leapfrog's FP32 positions."""
+    needs_q32 = True
+
+    def __init__(self, system):
+        self.system = system
+
+    def __call__(self, q64, q32, lp_out, g_out):
+        self.system.loglik_grad(q32, out=(lp_out, g_out, None))
+
+
+class PosteriorTarget:
+    """log p~(z) of the unconstrained parameters (Sec. 2.2) for one system."""
+    needs_q32 = False
+
+    def __init__(self, system, prior=None):
+        from . import map as gmap
+        self.system = system
+        self.prior = gmap.prior_table(prior if prior is not None else gmap.PAPER_PRIOR)
+        self._buf = None
+
+    def __call__(self, q64, q32, lp_out, g_out):
+        B = q64.shape[0]
+        if self._buf is None or self._buf[0].shape[0] != B:
+            dev = q64.device
+            self._buf = (torch.empty(B, NPARAM, dtype=torch.float32, device=dev),
+                         torch.empty(B, dtype=torch.float64, device=dev),
+                         torch.empty(B, NPARAM, dtype=torch.float64, device=dev))
+        th, ll, gt = self._buf
+        lib = abi.lib_handle()
+        st = torch.cuda.current_stream(q64.device).cuda_stream
+        pp = ctypes.addressof(self.prior)
+        abi._check(lib.gl_map_transform(B, q64.data_ptr(), pp, th.data_ptr(), st), "gl_map_transform")
+        self.system.loglik_grad(th, out=(ll, gt, None))
+        abi._check(lib.gl_posterior_grad(B, q64.data_ptr(), ll.data_ptr(), gt.data_ptr(), pp, lp_out.data_ptr(),
+                                         g_out.data_ptr(), st), "gl_posterior_grad")
+
+
+class FunctionTarget:
+    """Wraps ``logp_grad(q32) -> (logp float64 [B], grad float64 [B, d])``."""
+    needs_q32 = True
+
+    def __init__(self, fn: Callable):
+        self.fn = fn
+
+    def __call__(self, q64, q32, lp_out, g_out):
+        lp, g = self.fn(q32)
+        lp_out.copy_(lp)
+        g_out.copy_(g)
+
+
+class WhitenedTarget:
+    """A target seen through z = mu + L x (Sigma = L L^T): HMC with identity
+    mass on x is HMC with mass Sigma^-1 on z, the paper's preconditioning
+    (Sec. 2.5). log p is unchanged (constant Jacobian); grad_x = L^T grad_z."""
+    needs_q32 = False
+
+    def __init__(self, inner, mu: torch.Tensor, L: torch.Tensor):
+        self.inner = inner
+        self.mu = mu.to(torch.float64).contiguous()
+        self.L = torch.tril(L.to(torch.float64)).contiguous()
+        self.d = self.mu.shape[0]
+        self._buf = None
+
+    def to_z(self, x: torch.Tensor) -> torch.Tensor:
+        z = torch.empty_like(x, dtype=torch.float64)
+        abi.gl_hmc_affine(x.shape[0], self.d, x.contiguous().data_ptr(), self.mu.data_ptr(), self.L.data_ptr(),
+                          z.data_ptr(), None, torch.cuda.current_stream(x.device).cuda_stream)
+        return z
+
+    def __call__(self, q64, q32, lp_out, g_out):
+        B, d = q64.shape
+        if self._buf is None or self._buf[0].shape[0] != B:
+            dev = q64.device
+            self._buf = (torch.empty(B, d, dtype=torch.float64, device=dev),
+                         torch.empty(B, d, dtype=torch.float32, device=dev),
+                         torch.empty(B, d, dtype=torch.float64, device=dev))
+        z, z32, gz = self._buf
+        st = torch.cuda.current_stream(q64.device).cuda_stream
+        abi.gl_hmc_affine(B, d, q64.data_ptr(), self.mu.data_ptr(), self.L.data_ptr(), z.data_ptr(),
+                          z32.data_ptr() if self.inner.needs_q32 else None, st)
+        self.inner(z, z32, lp_out, gz)
+        abi.gl_hmc_affine_pullback(B, d, gz.data_ptr(), self.L.data_ptr(), g_out.data_ptr(), st)
+
+
 def laplace_inv_mass(system, q: torch.Tensor, rel_step: float = 1e-3, floor: float = 1e-12) -> torch.Tensor:
     """Diagonal inverse mass from the Hessian diagonal of log L at q [22]:
     central differences of the gradient, 44 vectors in one call; 1/|H_ii|."""
@@ -58,6 +158,67 @@ def laplace_inv_mass(system, q: torch.Tensor, rel_step: float = 1e-3, floor: flo
     _, g = system.loglik_grad(pts)
     hdiag = (g[:NPARAM].diagonal() - g[NPARAM:].diagonal()) / (2 * h)
     return 1.0 / torch.clamp(hdiag.abs(), min=floor)
+
+
+def laplace_inv_mass_target(target, q: torch.Tensor, step: float = 1e-4, floor: float = 1e-12) -> torch.Tensor:
+    """Diagonal inverse mass 1/|d2 logp/dq2| of any target at q [d] (central
+    differences of its gradient, 2d points in one evaluation)."""
+    q = q.to(torch.float64)
+    d = q.shape[0]
+    eye = torch.eye(d, dtype=torch.float64, device=q.device) * step
+    pts = torch.cat([q[None] + eye, q[None] - eye], 0).contiguous()
+    lp = torch.empty(2 * d, dtype=torch.float64, device=q.device)
+    g = torch.empty(2 * d, d, dtype=torch.float64, device=q.device)
+    target(pts, pts.to(torch.float32).contiguous(), lp, g)
+    hdiag = (g[:d].diagonal() - g[d:].diagonal()) / (2 * step)
+    return 1.0 / torch.clamp(hdiag.abs(), min=floor)
+
+
+def laplace_covariance(target, q: torch.Tensor, step: float = 1e-4) -> torch.Tensor:
+    """Covariance (-H)^-1 of a target at q [d] (a mode): the Hessian by central
+    differences of the gradient (2d points, one evaluation), symmetrised; a
+    non-positive-definite Hessian falls back to its diagonal. Setup of the
+    preconditioner when no variational covariance is at hand; float64 [d, d]."""
+    q = q.to(torch.float64)
+    d = q.shape[0]
+    eye = torch.eye(d, dtype=torch.float64, device=q.device) * step
+    pts = torch.cat([q[None] + eye, q[None] - eye], 0).contiguous()
+    lp = torch.empty(2 * d, dtype=torch.float64, device=q.device)
+    g = torch.empty(2 * d, d, dtype=torch.float64, device=q.device)
+    target(pts, pts.to(torch.float32).contiguous(), lp, g)
+    Hm = ((g[:d] - g[d:]) / (2 * step)).cpu().numpy()
+    Hm = -0.5 * (Hm + Hm.T)
+    try:
+        np.linalg.cholesky(Hm)
+        C = np.linalg.inv(Hm)
+    except np.linalg.LinAlgError:
+        C = np.diag(1.0 / np.maximum(np.abs(np.diag(Hm)), 1e-12))
+    return torch.from_numpy(0.5 * (C + C.T)).to(q.device)
+
+
+# ------------------------------------------------------------ sampler -----
+
+class DualAveraging:
+    """Step-size adaptation of Hoffman & Gelman (2014), Sec. 3.2.1."""
+
+    def __init__(self, eps0: float, target: float = 0.75, gamma: float = 0.05, t0: float = 10.0, kappa: float = 0.75):
+        self.mu = math.log(10.0 * eps0)
+        self.target, self.gamma, self.t0, self.kappa = target, gamma, t0, kappa
+        self.hbar = 0.0
+        self.log_eps_bar = 0.0
+        self.m = 0
+
+    def update(self, accept_prob: float) -> float:
+        self.m += 1
+        w = 1.0 / (self.m + self.t0)
+        self.hbar = (1.0 - w) * self.hbar + w * (self.target - accept_prob)
+        log_eps = self.mu - math.sqrt(self.m) / self.gamma * self.hbar
+        eta = self.m ** (-self.kappa)
+        self.log_eps_bar = eta * log_eps + (1.0 - eta) * self.log_eps_bar
+        return math.exp(log_eps)
+
+    def final(self) -> float:
+        return math.exp(self.log_eps_bar)
 
 
 @dataclasses.dataclass
@@ -73,21 +234,30 @@ class HMCStats:
         return self.grad_evals / self.seconds
 
 
+@dataclasses.dataclass
+class AdaptiveRun:
+    samples: torch.Tensor        # [n_samples, chains, d] float64 (positions of the target)
+    step_size: float
+    accept_burn: float
+    accept_samples: float
+    seconds: float
+    grad_evals: int
+
+
 class HMC:
-    """B chains of HMC with diagonal mass. ``logp_grad(q32) -> (logp f64 [B], grad f64 [B, d])``
-    defaults to the lens log-likelihood of ``system``; the leapfrog and accept
-    steps run in the library's kernels."""
+    """B chains of HMC with diagonal mass on a target (default: the lens log L of ``system``)."""
 
     def __init__(self, q0: torch.Tensor, inv_mass: torch.Tensor, step_size: float, n_leapfrog: int,
-                 system=None, logp_grad: Optional[Callable] = None, seed: int = 0):
+                 system=None, logp_grad: Optional[Callable] = None, target=None, seed: int = 0):
         self.q = q0.to(torch.float64).contiguous().clone()
         self.B, self.d = self.q.shape
         self.dev = self.q.device
         self.inv_mass = inv_mass.to(torch.float64).to(self.dev).contiguous()
         self.eps = float(step_size)
         self.L = int(n_leapfrog)
-        self.system = system
-        self.logp_grad = logp_grad or self._lens_logp_grad
+        if target is None:
+            target = FunctionTarget(logp_grad) if logp_grad is not None else LensTarget(system)
+        self.target = target
         self.gen = torch.Generator(device=self.dev)
         self.gen.manual_seed(seed)
         B, d = self.B, self.d
@@ -99,18 +269,14 @@ class HMC:
         self.lp_new = torch.empty(B, **f64)
         self.q32 = torch.empty(B, d, dtype=torch.float32, device=self.dev)
         self.accepted = torch.zeros(B, dtype=torch.int32, device=self.dev)
-        self.logp, self.grad = self.logp_grad(self.q.to(torch.float32).contiguous())
-        self.logp = self.logp.clone()
-        self.grad = self.grad.clone()
+        self.accept_prob = torch.zeros(B, **f64)
+        self.logp = torch.empty(B, **f64)
+        self.grad = torch.empty(B, d, **f64)
+        self.q32.copy_(self.q)
+        self.target(self.q, self.q32, self.logp, self.grad)
         self.n_accepted = 0
         self.n_proposed = 0
         self.grad_evals = 0
-
-    def _lens_logp_grad(self, q32):
-        return self.system.loglik_grad(q32)
-
-    def _lens_into(self, q32):
-        self.system.loglik_grad(q32, out=(self.lp_new, self.gp, None))
 
     def step(self) -> None:
         """One HMC iteration (L leapfrog steps + FP64 accept) for all chains."""
@@ -121,26 +287,20 @@ class HMC:
         self.p.copy_(self.p0)
         self.qp.copy_(self.q)
         self.gp.copy_(self.grad)
+        q32 = self.q32.data_ptr() if self.target.needs_q32 else None
         for l in range(self.L):
             abi.gl_hmc_leapfrog(B, d, self.qp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
-                                self.inv_mass.data_ptr(), self.eps, 0.5 if l == 0 else 1.0, self.q32.data_ptr(),
-                                stream)
-            if self.system is not None and self.logp_grad == self._lens_logp_grad:
-                self._lens_into(self.q32)
-            else:
-                lp, g = self.logp_grad(self.q32)
-                self.lp_new.copy_(lp)
-                self.gp.copy_(g)
+                                self.inv_mass.data_ptr(), self.eps, 0.5 if l == 0 else 1.0, q32, stream)
+            self.target(self.qp, self.q32, self.lp_new, self.gp)
         log_u = torch.rand(B, generator=self.gen, dtype=torch.float64, device=self.dev).log_()
         abi.gl_hmc_finish(B, d, self.p0.data_ptr(), self.logp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
                           self.lp_new.data_ptr(), self.qp.data_ptr(), self.inv_mass.data_ptr(), log_u.data_ptr(),
                           self.eps, self.q.data_ptr(), self.logp.data_ptr(), self.grad.data_ptr(),
-                          self.accepted.data_ptr(), stream)
+                          self.accepted.data_ptr(), stream, self.accept_prob.data_ptr())
         self.grad_evals += B * self.L
         self.n_proposed += B
 
     def run(self, n_iter: int) -> HMCStats:
-        import time
         torch.cuda.synchronize(self.dev)
         acc = torch.zeros((), dtype=torch.int64, device=self.dev)
         e0 = self.grad_evals
@@ -160,3 +320,67 @@ class HMC:
             st = self.run(iters)
             self.eps *= math.exp(1.5 * (st.acceptance - target))
         return self.eps
+
+    def run_adaptive(self, n_burn: int, n_samples: int, adapt_frac: float = 0.8,
+                     target_accept: float = 0.75) -> AdaptiveRun:
+        """Burn-in with dual-averaging step-size adaptation over its first
+        adapt_frac, then n_samples recorded iterations at the adapted step size.
+        The step size is shared by all chains and adapted on their mean
+        acceptance probability."""
+        torch.cuda.synchronize(self.dev)
+        t0 = time.perf_counter()
+        e0 = self.grad_evals
+        n_adapt = int(adapt_frac * n_burn)
+        da = DualAveraging(self.eps, target=target_accept)
+        ab = torch.zeros((), dtype=torch.float64, device=self.dev)
+        for i in range(n_burn):
+            self.step()
+            if i < n_adapt:
+                self.eps = da.update(float(self.accept_prob.mean().item()))
+                if i == n_adapt - 1:
+                    self.eps = da.final()
+            ab += self.accept_prob.mean()
+        out = torch.empty(n_samples, self.B, self.d, dtype=torch.float64, device=self.dev)
+        asum = torch.zeros((), dtype=torch.float64, device=self.dev)
+        for i in range(n_samples):
+            self.step()
+            out[i].copy_(self.q)
+            asum += self.accept_prob.mean()
+        torch.cuda.synchronize(self.dev)
+        return AdaptiveRun(out, self.eps, float(ab.item()) / max(1, n_burn), float(asum.item()) / max(1, n_samples),
+                           time.perf_counter() - t0, self.grad_evals - e0)
+
+
+@dataclasses.dataclass
+class PosteriorSamples:
+    theta: torch.Tensor          # [n_samples, chains, 22] float32, physical parameters
+    z: torch.Tensor              # [n_samples, chains, 22] float64, unconstrained
+    run: AdaptiveRun
+
+
+def sample_posterior(system, z_center: torch.Tensor, cov: torch.Tensor, chains: int = 50, n_burn: int = 250,
+                     n_samples: int = 750, n_leapfrog: int = 5, seed: int = 0, prior=None,
+                     step_size: float = 0.5) -> PosteriorSamples:
+    """The sampling step of the pipeline (Sec. 2.5, Table 1): chains drawn from
+    N(z_center, cov) (the variational posterior in the paper), HMC on log p~(z)
+    with mass cov^-1 (whitened coordinates), step size adapted by dual averaging
+    over the first 80% of burn-in toward acceptance 0.75, fixed trajectory
+    length n_leapfrog."""
+    from . import map as gmap
+    dev = z_center.device
+    L = torch.linalg.cholesky(cov.to(torch.float64).to(dev))
+    post = PosteriorTarget(system, prior)
+    target = WhitenedTarget(post, z_center.to(dev), L)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    x0 = torch.randn(chains, NPARAM, dtype=torch.float64, device=dev, generator=g)
+    sampler = HMC(x0, torch.ones(NPARAM, dtype=torch.float64, device=dev), step_size, n_leapfrog, target=target,
+                  seed=seed + 1)
+    run = sampler.run_adaptive(n_burn, n_samples)
+    n = n_samples * chains
+    z = target.to_z(run.samples.reshape(n, NPARAM))
+    th = torch.empty(n, NPARAM, dtype=torch.float32, device=dev)
+    pt = post.prior
+    abi._check(abi.lib_handle().gl_map_transform(n, z.data_ptr(), ctypes.addressof(pt), th.data_ptr(),
+                                                 torch.cuda.current_stream(dev).cuda_stream), "gl_map_transform")
+    return PosteriorSamples(th.reshape(n_samples, chains, NPARAM), z.reshape(n_samples, chains, NPARAM), run)

@@ -67,11 +67,13 @@ def _numpy_finish(p0, logp0, p, grad_new, logp_new, q_new, inv_mass, log_u, eps,
     p = p + 0.5 * eps * grad_new
     h0 = -logp0 + 0.5 * np.sum(p0 * p0 * inv_mass, axis=1)
     h1 = -logp_new + 0.5 * np.sum(p * p * inv_mass, axis=1)
-    acc = np.isfinite(h0) & np.isfinite(h1) & (log_u < h0 - h1)
+    fin = np.isfinite(h0) & np.isfinite(h1)
+    acc = fin & (log_u < h0 - h1)
+    aprob = np.where(fin, np.minimum(1.0, np.exp(np.where(fin, h0 - h1, 0.0))), 0.0)
     q = np.where(acc[:, None], q_new, q)
     grad = np.where(acc[:, None], grad_new, grad)
     logp = np.where(acc, logp_new, logp)
-    return p, q, logp, grad, acc.astype(np.int32)
+    return p, q, logp, grad, acc.astype(np.int32), aprob
 
 
 def test_finish_kernel_matches_numpy(mods):
@@ -92,15 +94,18 @@ def test_finish_kernel_matches_numpy(mods):
     tl0, tln, tim, tlu, tlp = (torch.from_numpy(x).cuda().contiguous() for x in (logp0, logp_new, inv_mass, log_u,
                                                                                    logp))
     acc = torch.empty(B, dtype=torch.int32, device="cuda")
+    aprob = torch.empty(B, dtype=torch.float64, device="cuda")
     abi.gl_hmc_finish(B, d, t["p0"].data_ptr(), tl0.data_ptr(), t["p"].data_ptr(), t["grad_new"].data_ptr(),
                       tln.data_ptr(), t["q_new"].data_ptr(), tim.data_ptr(), tlu.data_ptr(), eps, t["q"].data_ptr(),
-                      tlp.data_ptr(), t["grad"].data_ptr(), acc.data_ptr(), torch.cuda.current_stream().cuda_stream)
+                      tlp.data_ptr(), t["grad"].data_ptr(), acc.data_ptr(), torch.cuda.current_stream().cuda_stream,
+                      accept_prob=aprob.data_ptr())
     torch.cuda.synchronize()
     np.testing.assert_allclose(t["p"].cpu().numpy(), ref[0], rtol=1e-15, atol=1e-15)
     np.testing.assert_array_equal(acc.cpu().numpy(), ref[4])
     np.testing.assert_array_equal(t["q"].cpu().numpy(), ref[1])
     np.testing.assert_array_equal(tlp.cpu().numpy(), ref[2])
     np.testing.assert_array_equal(t["grad"].cpu().numpy(), ref[3])
+    np.testing.assert_allclose(aprob.cpu().numpy(), ref[5], rtol=1e-14, atol=0)
     assert 0 < ref[4].sum() < B and ref[4][:5].sum() == 0
 
 

@@ -1,0 +1,151 @@
+"""HMC on the posterior of the unconstrained parameters (Sec. 2.2, 2.5):
+
+- gl_posterior_grad against the MAP oracle's objective (log p~ = -f,
+  grad = -df/dz) on identical FP64 inputs;
+- the whitening kernels (z = mu + L x, g_x = L^T g_z) against torch FP64;
+- dual-averaging HMC through a dense preconditioner on a correlated Gaussian:
+  acceptance at the 0.75 target, sample mean and covariance of the target;
+- the paper's pipeline on a small lens system: Laplace covariance at the
+  truth as the preconditioner, chains drawn from it, adapted HMC; R-hat,
+  ESS and the sample covariance against the Laplace one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from oracle import map_oracle as mo  # noqa: E402
+from paper_2202_07663_gb300 import diagnostics as dg  # noqa: E402
+from paper_2202_07663_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_07663_gb300 import build
+    build.build()
+    oracle.build()
+    from paper_2202_07663_gb300 import abi, hmc, map as gmap
+    return abi, hmc, gmap
+
+
+def test_posterior_grad_matches_map_oracle(mods):
+    abi, _, gmap = mods
+    lib = abi.lib_handle()
+    rng = np.random.default_rng(21)
+    n = 301
+    theta = inputs.draw_table(rng, inputs.PAPER_PRIOR_DRAW, n)
+    z = mo.inverse_bijector(theta)
+    ll = rng.normal(size=n) * 1e3
+    gt = rng.normal(size=(n, 22)) * 1e2
+    pt = gmap.prior_table()
+    zd, lld, gtd = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (z, ll, gt))
+    lp = torch.empty(n, dtype=torch.float64, device="cuda")
+    gz = torch.empty(n, 22, dtype=torch.float64, device="cuda")
+    abi._check(lib.gl_posterior_grad(n, zd.data_ptr(), lld.data_ptr(), gtd.data_ptr(), gmap.ctypes.addressof(pt),
+                                     lp.data_ptr(), gz.data_ptr(), torch.cuda.current_stream().cuda_stream), "post")
+    f, g = mo.objective_grad(z, ll, gt)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(lp.cpu().numpy(), -f, rtol=1e-12)
+    np.testing.assert_allclose(gz.cpu().numpy(), -g, rtol=1e-11, atol=1e-11)
+
+
+def test_whitening_kernels_match_torch(mods):
+    abi, hmc, _ = mods
+    g = torch.Generator(device="cuda").manual_seed(5)
+    for d, B in ((22, 513), (40, 77), (1, 3)):
+        L = torch.randn(d, d, dtype=torch.float64, device="cuda", generator=g)   # upper part must be ignored
+        mu = torch.randn(d, dtype=torch.float64, device="cuda", generator=g)
+        x = torch.randn(B, d, dtype=torch.float64, device="cuda", generator=g)
+        gz = torch.randn(B, d, dtype=torch.float64, device="cuda", generator=g)
+        z = torch.empty(B, d, dtype=torch.float64, device="cuda")
+        z32 = torch.empty(B, d, dtype=torch.float32, device="cuda")
+        gx = torch.empty(B, d, dtype=torch.float64, device="cuda")
+        st = torch.cuda.current_stream().cuda_stream
+        abi.gl_hmc_affine(B, d, x.data_ptr(), mu.data_ptr(), L.contiguous().data_ptr(), z.data_ptr(), z32.data_ptr(),
+                          st)
+        abi.gl_hmc_affine_pullback(B, d, gz.data_ptr(), L.contiguous().data_ptr(), gx.data_ptr(), st)
+        Lt = torch.tril(L)
+        torch.testing.assert_close(z, mu + x @ Lt.T, rtol=1e-13, atol=1e-13)
+        torch.testing.assert_close(z32, z.float(), rtol=0, atol=0)
+        torch.testing.assert_close(gx, gz @ Lt, rtol=1e-13, atol=1e-13)
+
+
+def test_adaptive_hmc_with_dense_preconditioner_samples_a_correlated_gaussian(mods):
+    abi, hmc, _ = mods
+    d, B = 22, 256
+    g = torch.Generator(device="cuda").manual_seed(8)
+    A = torch.randn(d, d, dtype=torch.float64, device="cuda", generator=g)
+    cov = A @ A.T / d + 0.05 * torch.eye(d, dtype=torch.float64, device="cuda")   # condition number in the 100s
+    mu = torch.randn(d, dtype=torch.float64, device="cuda", generator=g)
+    prec = torch.linalg.inv(cov)
+
+    def lg(q32):
+        r = q32.double() - mu
+        return -0.5 * (r * (r @ prec)).sum(1), -(r @ prec)
+
+    L = torch.linalg.cholesky(cov)
+    target = hmc.WhitenedTarget(hmc.FunctionTarget(lg), mu, L)
+    x0 = torch.randn(B, d, dtype=torch.float64, device="cuda", generator=g)
+    sampler = hmc.HMC(x0, torch.ones(d, dtype=torch.float64, device="cuda"), 0.1, 5, target=target, seed=3)
+    run = sampler.run_adaptive(n_burn=150, n_samples=200)
+    assert 0.65 < run.accept_samples < 0.85, run
+    Z = target.to_z(run.samples.reshape(-1, d))
+    n_eff = float(dg.ess(run.samples.transpose(0, 1).cpu().numpy()).min())
+    assert n_eff > 2000
+    se = torch.sqrt(torch.diag(cov) / n_eff)
+    assert ((Z.mean(0) - mu).abs() / se).max().item() < 5.0
+    ratio = torch.diag(torch.cov(Z.T)) / torch.diag(cov)
+    assert torch.all((ratio > 0.9) & (ratio < 1.1)), ratio
+    R = dg.rhat(run.samples.transpose(0, 1).cpu().numpy())
+    assert R.max() < 1.02
+
+
+def _paper_system(H, seed, K=11):
+    spec = inputs.SystemSpec(H, H, 2, K, "gaussian", inputs.PIXEL_SCALE, 0.2, 100.0)
+    rng = np.random.default_rng(seed)
+    truth = inputs.draw_table(rng, inputs.PAPER_SIM, 1)[0]
+    psf = inputs.make_psf(spec).astype(np.float32)
+    model = oracle.simulate(truth, spec.H, spec.W, psf, spec.pixel_scale, spec.k)[0]
+    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
+    return spec, truth, psf, image
+
+
+def test_posterior_hmc_on_a_lens_system(mods):
+    abi, hmc, gmap = mods
+    spec, truth, psf, image = _paper_system(60, 7)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    post = hmc.PosteriorTarget(s)
+    z_truth = torch.from_numpy(mo.inverse_bijector(truth)[0]).cuda()
+    cov = hmc.laplace_covariance(post, z_truth)
+    L = torch.linalg.cholesky(cov)
+    target = hmc.WhitenedTarget(post, z_truth, L)
+    B, d = 32, 22
+    g = torch.Generator(device="cuda").manual_seed(4)
+    x0 = torch.randn(B, d, dtype=torch.float64, device="cuda", generator=g)
+    sampler = hmc.HMC(x0, torch.ones(d, dtype=torch.float64, device="cuda"), 0.3, 5, target=target, seed=6)
+    assert torch.isfinite(sampler.logp).all()
+    run = sampler.run_adaptive(n_burn=100, n_samples=200)
+    s.close()
+    assert torch.isfinite(sampler.logp).all()
+    assert 0.55 < run.accept_samples < 0.92, run
+    xs = run.samples.transpose(0, 1).cpu().numpy()
+    R = dg.rhat(xs)
+    n_eff = dg.ess(xs)
+    assert R.max() < 1.1, R
+    assert n_eff.min() > 100, n_eff
+    # the posterior is near-Gaussian at this signal-to-noise: whitened samples ~ N(m, I)
+    X = run.samples.reshape(-1, d)
+    v = X.var(0)
+    assert torch.all((v > 0.6) & (v < 1.6)), v
+    # truth within a few posterior standard deviations (theta space)
+    th = torch.from_numpy(mo.bijector(target.to_z(X).cpu().numpy())[0])
+    zt = (th.mean(0) - torch.from_numpy(truth)).abs() / th.std(0)
+    assert zt.max().item() < 5.0, zt
+    assert math.isfinite(run.step_size) and run.step_size > 0
