@@ -82,12 +82,12 @@ MAP_MUTANTS = {
 }
 
 
-def _run_map_mutant(name, old, new, tmp):
+def _run_map_mutant(name, old, new, tmp, module="map_oracle.py", test="test_map_oracle.py"):
     import shutil
     dst = os.path.join(tmp, name)
     shutil.copytree(ROOT, dst, ignore=shutil.ignore_patterns(".git", "_work", "gpurun_out", "*.so", "_build",
                                                                "__pycache__", ".pytest_cache"))
-    path = os.path.join(dst, "oracle", "map_oracle.py")
+    path = os.path.join(dst, "oracle", module)
     src = open(path).read()
     assert src.count(old) == 1, "mutation anchor for %s not unique/present" % name
     with open(path, "w") as f:
@@ -95,7 +95,7 @@ def _run_map_mutant(name, old, new, tmp):
     import oracle as real
     env = dict(os.environ, GL_ORACLE_LIB=real.build())
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(dst, "tests", "test_map_oracle.py")],
+                        os.path.join(dst, "tests", test)],
                        cwd=dst, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode
 
@@ -107,3 +107,30 @@ def test_every_planted_map_mistake_fails_a_pin():
             results = dict(f.result() for f in futs)
     survivors = [n for n, rc in results.items() if rc == 0]
     assert not survivors, "MAP mutants not caught by any pin: %s" % survivors
+
+
+VI_MUTANTS = {
+    "diagonal_not_exponentiated": ("L[i, j] = math.exp(phi[k]) if i == j else phi[k]", "L[i, j] = phi[k]"),
+    "score_drops_log_q": ("    f = log_q(z, mu, L) - np.asarray(logp, np.float64)\n    return f.mean(), (f[:, None]",
+                          "    f = -np.asarray(logp, np.float64)\n    return f.mean(), (f[:, None]"),
+    "pathwise_entropy_sign": ("- np.diag(1.0 / np.diag(L))\n    return f.mean(), _to_u",
+                              "+ np.diag(1.0 / np.diag(L))\n    return f.mean(), _to_u"),
+    "pathwise_mu_sign": ("gmu = -gz.mean(axis=0)", "gmu = gz.mean(axis=0)"),
+    "score_factor_order": ("np.outer(a, r) @ Linv_T", "np.outer(r, a) @ Linv_T"),
+    "chain_rule_drops_diagonal": ("            out.append(gL[i, j] * L[i, i] if i == j else gL[i, j])",
+                                  "            out.append(gL[i, j])"),
+    "log_q_drops_2pi": ("d * math.log(2.0 * math.pi) + logdet", "logdet"),
+    "schedule_linear": ("return LR_PEAK - LR_PEAK * (1.0 - frac) ** 2", "return LR_PEAK * frac"),
+    "sigma_init": ("SIGMA_INIT = 1e-6", "SIGMA_INIT = 1e-4"),
+    "pathwise_eps_transposed": ("gL = np.tril(-(gz.T @ eps)", "gL = np.tril(-(eps.T @ gz)"),
+}
+
+
+def test_every_planted_vi_mistake_fails_a_pin():
+    with tempfile.TemporaryDirectory() as tmp:
+        with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+            futs = [ex.submit(_run_map_mutant, n, o, w, tmp, "vi_oracle.py", "test_vi_oracle.py")
+                    for n, (o, w) in VI_MUTANTS.items()]
+            results = dict(f.result() for f in futs)
+    survivors = [n for n, rc in results.items() if rc == 0]
+    assert not survivors, "VI mutants not caught by any pin: %s" % survivors
