@@ -24,6 +24,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
+from scipy.linalg import solve_triangular
 
 from .map_oracle import adam_step
 
@@ -76,14 +77,14 @@ def learning_rate(t: int) -> float:
 
 
 def log_q(z, mu, L):
-    """log N(z; mu, L L^T) for z [n, d]: the textbook density, from Sigma."""
+    """log N(z; mu, L L^T) for z [n, d]: the textbook density written with the
+    Cholesky factor, -|L^-1 (z - mu)|^2 / 2 - log det L - d/2 log 2 pi
+    (triangular solves; forming Sigma = L L^T would square L's condition number)."""
     z = np.atleast_2d(np.asarray(z, np.float64))
     d = len(mu)
-    S = L @ L.T
-    r = z - mu
-    quad = np.einsum("ni,ni->n", r, np.linalg.solve(S, r.T).T)
-    _, logdet = np.linalg.slogdet(S)
-    return -0.5 * quad - 0.5 * (d * math.log(2.0 * math.pi) + logdet)
+    w = solve_triangular(L, (z - mu).T, lower=True)
+    logdet_L = np.sum(np.log(np.diag(L)))
+    return -0.5 * np.sum(w * w, axis=0) - logdet_L - 0.5 * d * math.log(2.0 * math.pi)
 
 
 def _to_u(gmu, gL, L):
@@ -98,15 +99,15 @@ def _to_u(gmu, gL, L):
 
 def grad_log_q(z, mu, L):
     """d log q(z; phi) / d phi with z held fixed, per sample: [n, P].
-    d/dmu = Sigma^-1 r; d/dL = lower part of Sigma^-1 r r^T L^-T - diag(1/L_ii)."""
+    With w = L^-1 r and a = L^-T w = Sigma^-1 r (r = z - mu):
+    d/dmu = a; d/dL = lower part of a w^T (= Sigma^-1 r r^T L^-T) - diag(1/L_ii)."""
     z = np.atleast_2d(np.asarray(z, np.float64))
-    S = L @ L.T
-    Linv_T = np.linalg.inv(L).T
     out = []
     for zs in z:
         r = zs - mu
-        a = np.linalg.solve(S, r)
-        gL = np.tril(np.outer(a, r) @ Linv_T) - np.diag(1.0 / np.diag(L))
+        w = solve_triangular(L, r, lower=True)
+        a = solve_triangular(L.T, w, lower=False)
+        gL = np.tril(np.outer(a, w)) - np.diag(1.0 / np.diag(L))
         out.append(_to_u(a, gL, L))
     return np.array(out)
 

@@ -116,10 +116,11 @@ VI_MUTANTS = {
     "pathwise_entropy_sign": ("- np.diag(1.0 / np.diag(L))\n    return f.mean(), _to_u",
                               "+ np.diag(1.0 / np.diag(L))\n    return f.mean(), _to_u"),
     "pathwise_mu_sign": ("gmu = -gz.mean(axis=0)", "gmu = gz.mean(axis=0)"),
-    "score_factor_order": ("np.outer(a, r) @ Linv_T", "np.outer(r, a) @ Linv_T"),
+    "score_factor_order": ("np.outer(a, w)", "np.outer(w, a)"),
     "chain_rule_drops_diagonal": ("            out.append(gL[i, j] * L[i, i] if i == j else gL[i, j])",
                                   "            out.append(gL[i, j])"),
-    "log_q_drops_2pi": ("d * math.log(2.0 * math.pi) + logdet", "logdet"),
+    "log_q_drops_2pi": ("- logdet_L - 0.5 * d * math.log(2.0 * math.pi)", "- logdet_L"),
+    "log_q_logdet_sign": ("- logdet_L - 0.5", "+ logdet_L - 0.5"),
     "schedule_linear": ("return LR_PEAK - LR_PEAK * (1.0 - frac) ** 2", "return LR_PEAK * frac"),
     "sigma_init": ("SIGMA_INIT = 1e-6", "SIGMA_INIT = 1e-4"),
     "pathwise_eps_transposed": ("gL = np.tril(-(gz.T @ eps)", "gL = np.tril(-(eps.T @ gz)"),
