@@ -14,6 +14,7 @@
 //   * ray trace + surface-brightness conservation + lens light Sec. 2.1.1 (first paragraph)
 //   * elliptical Sersic with b_n = 1.9992 n - 0.3271           Sec. 2.1.1, Eq. Sersic
 //   * k x k supersampling, then averaging down                 Sec. 2.1.1 (last paragraph)
+//   * times the pixel area: counts/s per pixel                 (reading below)
 //   * PSF convolution                                          Sec. 2.1.1 (first paragraph)
 //   * Gaussian log-likelihood with model-dependent variance    Sec. 2.1.2, Eq. model-def
 //   * gradient of log L with respect to the 22 parameters      Sec. 2.2 (the paper uses AD;
@@ -30,7 +31,14 @@
 //   * inside the elliptical radius rho = sqrt(q x^2 + y^2/q) < 1e-6 arcsec the
 //     EPL deflection is set to zero and the Sersic radius is floored at 1e-6;
 //   * the series is summed until a term (value and every derivative) falls
-//     below 1e-18 in magnitude; the summed function is O(1).
+//     below 1e-18 in magnitude; the summed function is O(1);
+//   * the amplitudes I_l, I_s are surface brightness in counts/s/arcsec^2 and a
+//     detector pixel records the flux falling on it, counts/s: the mean over
+//     its k x k subpixels times the pixel area (pixel scale squared). The
+//     paper's simulated sample (I_l ~ 300, I_s ~ 150, sigma_bkg = 0.2 counts/s,
+//     HST-like, Sec. 3) and the posterior widths behind its Table 3 fit this
+//     reading; sampling the brightness without the area would make those
+//     images about 240 times brighter per pixel.
 //
 // Parameter order (Table 2): thetaE, gamma_epl, e_epl1, e_epl2, x_epl, y_epl,
 // gamma_ext1, gamma_ext2, R_l, n_l, e_l1, e_l2, x_l, y_l, I_l,
@@ -325,6 +333,8 @@ void model_image(const System& s, const T* p, std::vector<T>& pre, std::vector<T
   pre.assign(size_t(s.H) * s.W, T(0.0));
   model.assign(size_t(s.H) * s.W, T(0.0));
   binned_image(p, s.H, s.W, s.k, s.dpix, pre.data());
+  const double area = s.dpix * s.dpix;
+  for (size_t i = 0; i < pre.size(); ++i) pre[i] = pre[i] * area;
   convolve(pre.data(), s.H, s.W, s.psf, s.K, model.data());
 }
 

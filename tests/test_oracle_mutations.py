@@ -35,6 +35,8 @@ MUTANTS = {
     "grid_transpose": ("const double x = (j * k + b - cx) * sub;", "const double x = (i * k + a - cx) * sub;"),
     "grid_offset": ("const double cx = (k * W - 1) * 0.5", "const double cx = (k * W) * 0.5"),
     "binning_norm": ("out[i * W + j] = acc / double(k * k);", "out[i * W + j] = acc / double(k);"),
+    "pixel_area_dropped": ("pre[i] = pre[i] * area;", "pre[i] = pre[i];"),
+    "pixel_area_subpixel": ("const double area = s.dpix * s.dpix;", "const double area = s.dpix * s.dpix / (s.k * s.k);"),
     "conv_no_flip": ("const int ii = i + c - a;", "const int ii = i - c + a;"),
     "conv_transpose": ("acc += psf[a * K + b] * img[ii * W + jj];", "acc += psf[b * K + a] * img[ii * W + jj];"),
     "poisson_term": ("var = var + model[i] / s.gain_exposure;", "var = var + model[i] * s.gain_exposure;"),

@@ -431,10 +431,25 @@ def _small_system(seed=0, H=14, W=14, k=2, K=5, gain=1000.0):
     return truth, D, psf
 
 
-def test_simulate_is_binning_then_convolution():
+def test_simulate_is_binning_then_area_then_convolution():
     truth, _, psf = _small_system()
     pre = oracle.binned_image(truth, 14, 14, 2, 0.065)
-    np.testing.assert_allclose(oracle.simulate(truth, 14, 14, psf, 0.065, 2)[0], oracle.convolve(pre, psf), rtol=1e-14)
+    np.testing.assert_allclose(oracle.simulate(truth, 14, 14, psf, 0.065, 2)[0],
+                               oracle.convolve(pre * 0.065 ** 2, psf), rtol=1e-14)
+
+
+def test_simulated_pixels_sum_to_the_total_flux():
+    """A pixel records the flux falling on it: with a delta PSF the pixel values
+    of a simulated light-only image sum to the Sersic total flux
+    2 pi n R^2 I0 e^{b_n} Gamma(2n) / b_n^{2n} (counts/s), for two pixel scales."""
+    R, n, I0 = 0.2, 1.5, 3.0
+    bn = 1.9992 * n - 0.3271
+    expect = 2 * math.pi * n * R * R * I0 * math.exp(bn) * math.gamma(2 * n) / bn ** (2 * n)
+    delta = np.zeros((1, 1))
+    delta[0, 0] = 1.0
+    for d, H in ((0.065, 81), (0.03, 161)):
+        img = oracle.simulate(_light_only(R=R, n=n, I0=I0, e1=0.1), H, H, delta, d, 4)[0]
+        assert img.sum() == pytest.approx(expect, rel=3e-3)
 
 
 def test_whole_model_rot90_covariance():
