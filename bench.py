@@ -282,9 +282,10 @@ def run_serving_workload(device, n_latency: int = 200, n_capacity: int = 1000):
 def run_map_workload(device, n_starts: int = 300, steps=(300, 1000)):
     """Sec. 2.3 / Table 1: multi-start MAP, 300 starts drawn from the prior, on
     a system drawn from the paper's simulation distribution (80x80, k = 2,
-    sigma_bkg = 0.2, t_exp = 100 s, G = 1). Reports time and the fraction of
-    starts that end in the truth's basin (every parameter within 5% of
-    |truth| + 0.05)."""
+    sigma_bkg = 0.2, t_exp = 100 s, G = 1). Reports time, the fraction of
+    starts that end at reduced chi^2 <= 1.01 (the paper's marker of runs that
+    reached the global mode, Sec. 2.3) and the fraction whose objective ends
+    within 1 of the best start's (the same optimum)."""
     import torch
     from paper_2202_07663_gb300 import abi, map as gmap
     spec = inputs.PAPER_SAMPLE_SPEC
@@ -304,11 +305,14 @@ def run_map_workload(device, n_starts: int = 300, steps=(300, 1000)):
     for k in steps:
         gmap.MultiStartMAP(s, steps=5).run(th0[:8])   # warm-up
         r = gmap.MultiStartMAP(s, steps=k).run(th0)
-        th = r.theta.cpu().numpy()
-        in_basin = np.all(np.abs(th - truth[None]) / (np.abs(truth[None]) + 0.05) < 0.05, axis=1)
+        _, c2 = s.loglik(r.theta, chi2=True)
+        chi2nu = c2.cpu().numpy() / (spec.H * spec.W - 22)
+        f = r.objective.cpu().numpy()
+        fbest = float(np.nanmin(f))
         out["runs"].append({"iterations": k, "seconds": r.seconds, "evals_per_s": r.grad_evals / r.seconds,
-                            "fraction_in_truth_basin": float(in_basin.mean()),
-                            "best_objective": float(np.nanmin(r.objective.cpu().numpy()))})
+                            "fraction_chi2nu_le_1.01": float(np.mean(chi2nu <= 1.01)),
+                            "fraction_at_best_objective": float(np.mean(f <= fbest + 1.0)),
+                            "best_objective": fbest, "best_chi2nu": float(chi2nu[int(np.nanargmin(f))])})
     s.close()
     return out
 

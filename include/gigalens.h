@@ -70,7 +70,10 @@ typedef struct gl_system gl_system;
  *  H, W          image size, 1 <= H, W <= 4096.
  *  psf           HOST float32 [K, K], used as given (not renormalised).
  *  K             PSF side, odd, 1 <= K <= 63.
- *  pixel_scale   arcsec per detector pixel (> 0).
+ *  pixel_scale   arcsec per detector pixel (> 0). The Sersic amplitudes are
+ *                surface brightness (counts/s/arcsec^2); a model pixel holds
+ *                the flux falling on it, the mean over its k x k subpixels
+ *                times pixel_scale^2 (counts/s), before the PSF.
  *  supersample   k_super >= 1 (<= 16).
  *  gain_exposure G * t_exp in seconds; <= 0 drops the Poisson term of the
  *                variance (sigma_tot^2 = sigma_bkg^2).
@@ -265,7 +268,9 @@ int gl_map_adam_step(int B, double* z, double* m, double* v, int t, double lr, d
  *   log p~(z) = log L + log p(g(z)) + log|J| (Eq. reparam-post; the
  *   negative of the MAP objective), and its gradient in z, given log L and
  *   d log L / d theta at theta = g(z). logp_out device float64 [B],
- *   grad_z_out device float64 [B, 22]. Used by HMC on the posterior.
+ *   grad_z_out device float64 [B, 22]. grad_theta may be NULL (then
+ *   grad_z_out is not written and may be NULL too): log density only. Used
+ *   by HMC on the posterior and by VI.
  */
 int gl_posterior_grad(int B, const double* z, const double* loglik, const double* grad_theta,
                       const gl_prior_entry* prior, double* logp_out, double* grad_z_out, void* stream);
@@ -318,6 +323,46 @@ int gl_hmc_finish(int B, int d, const double* p0, const double* logp0, double* p
 int gl_hmc_affine(int B, int d, const double* x, const double* mu, const double* L, double* z_out, float* z32_out,
                   void* stream);
 int gl_hmc_affine_pullback(int B, int d, const double* grad_z, const double* L, double* grad_x_out, void* stream);
+
+/*
+ * Full-rank variational inference (Sec. 2.4; Table 1 settings are the
+ * caller's). The surrogate posterior over the unconstrained parameters is
+ * q = N(mu, L L^T) with L from the Cholesky bijector: phi = [mu (d),
+ * u (d(d+1)/2)], u packed row by row, u[i(i+1)/2 + j] = L[i][j] for j < i and
+ * log L[i][i] for j = i. The caller draws eps ~ N(0, I) [n, d] and evaluates
+ * log p~ (and its gradient in z for the pathwise estimator) at the draws.
+ *
+ * gl_vi_param_count - d + d(d+1)/2 (0 for d outside 1..GL_VI_MAX_D).
+ * gl_vi_workspace_bytes - device scratch gl_vi_step needs for n draws.
+ *
+ * gl_vi_sample - z_out = mu + L eps per draw [n, d] float64; theta_out
+ *   (may be NULL) receives g(z) as float32 through the prior's bijector
+ *   when prior != NULL (then d must be GL_NPARAM), else (float)z.
+ *
+ * gl_vi_step - the ELBO loss estimate mean(log q(z_s) - log p~(z_s)) into
+ *   loss_out [1] and its gradient in phi into grad_out [P] by
+ *   GL_VI_SCORE: Eq. elbo-grad, mean((log q - log p~) d log q / d phi) with
+ *     the draws held fixed (grad_z unused, may be NULL); or
+ *   GL_VI_PATHWISE: the reparameterised gradient through z = mu + L eps
+ *     (grad_z [n, d] = d log p~ / dz required).
+ *   With m and v (both [P]) given, one Adam step t >= 1 updates phi in place:
+ *   m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ *   phi -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + adam_eps); with both
+ *   NULL phi is left alone. workspace: gl_vi_workspace_bytes(n, d) bytes of
+ *   device memory owned by the caller. Sums run in a fixed order: equal
+ *   inputs give equal outputs. logp, eps, grad_z, phi, m, v, grad_out,
+ *   loss_out are device float64; asynchronous on stream.
+ */
+#define GL_VI_MAX_D 32
+#define GL_VI_SCORE 0
+#define GL_VI_PATHWISE 1
+size_t gl_vi_param_count(int d);
+size_t gl_vi_workspace_bytes(int n, int d);
+int gl_vi_sample(int n, int d, const double* eps, const double* phi, const gl_prior_entry* prior, double* z_out,
+                 float* theta_out, void* stream);
+int gl_vi_step(int n, int d, const double* eps, const double* logp, const double* grad_z, int estimator,
+               double* phi, double* m, double* v, int t, double lr, double beta1, double beta2, double adam_eps,
+               double* grad_out, double* loss_out, void* workspace, void* stream);
 
 /* Name of a status code (static string). */
 const char* gl_error_string(int code);

@@ -56,6 +56,10 @@ SIGNATURES = {
     "gl_hmc_finish": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_affine": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_affine_pullback": ([_i, _i, _vp, _vp, _vp, _vp], _i),
+    "gl_vi_param_count": ([_i], ctypes.c_size_t),
+    "gl_vi_workspace_bytes": ([_i, _i], ctypes.c_size_t),
+    "gl_vi_sample": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "gl_vi_step": ([_i, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp], _i),
     "gl_posterior_grad": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_error_string": ([_i], ctypes.c_char_p),
     "gl_last_error_message": ([], ctypes.c_char_p),
@@ -259,12 +263,16 @@ class GLSystem:
             raise ValueError("params must be [B, 22]")
         return _dptr(params, torch.float32, name="params"), params.shape[0]
 
-    def loglik(self, params, chi2: bool = False):
+    def loglik(self, params, chi2: bool = False, out=None):
         import torch
         p, B = self._params(params)
-        ll = torch.empty(B, dtype=torch.float64, device=params.device)
+        if out is None:
+            ll = torch.empty(B, dtype=torch.float64, device=params.device)
+        else:
+            ll = out
         c2 = torch.empty(B, dtype=torch.float64, device=params.device) if chi2 else None
-        gl_loglik(self._h, p, B, ll.data_ptr(), c2.data_ptr() if chi2 else None, _stream_ptr(params.device))
+        gl_loglik(self._h, p, B, _dptr(ll, torch.float64, (B,), "loglik"), c2.data_ptr() if chi2 else None,
+                  _stream_ptr(params.device))
         return (ll, c2) if chi2 else ll
 
     def loglik_grad(self, params, chi2: bool = False, out=None):

@@ -262,6 +262,12 @@ int gl_system_create(gl_system** out, const float* image, const float* noise_map
   if (smem > size_t(max_smem_optin(dev)))
     return fail(GL_ERR_UNSUPPORTED, "padded %dx%d image with K=%d needs %zu B of shared memory (> %d)", H, W, K,
                 smem, max_smem_optin(dev));
+  // A detector pixel records the flux falling on it: the mean surface brightness
+  // over its subpixels times the pixel area. The convolution is linear, so the
+  // area is folded into the PSF weights once here.
+  const double area = pixel_scale * pixel_scale;
+  std::vector<float> psf_area(size_t(K) * K);
+  for (size_t i = 0; i < psf_area.size(); ++i) psf_area[i] = float(double(psf[i]) * area);
   gl_system* s = new gl_system();
   s->device = dev;
   s->H = H;
@@ -277,7 +283,7 @@ int gl_system_create(gl_system** out, const float* image, const float* noise_map
       (e = cudaMalloc(&s->d_psf, size_t(K) * K * sizeof(float))) != cudaSuccess ||
       (e = cudaMemcpyAsync(s->d_image, image, n * sizeof(float), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(s->d_sigma2, s2.data(), n * sizeof(float), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(s->d_psf, psf, size_t(K) * K * sizeof(float), cudaMemcpyHostToDevice, st)) !=
+      (e = cudaMemcpyAsync(s->d_psf, psf_area.data(), size_t(K) * K * sizeof(float), cudaMemcpyHostToDevice, st)) !=
           cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess) {
     gl_system_destroy(s);

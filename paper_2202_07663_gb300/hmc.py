@@ -96,6 +96,11 @@ class PosteriorTarget:
         st = torch.cuda.current_stream(q64.device).cuda_stream
         pp = ctypes.addressof(self.prior)
         abi._check(lib.gl_map_transform(B, q64.data_ptr(), pp, th.data_ptr(), st), "gl_map_transform")
+        if g_out is None:   # log density only (no adjoint pass)
+            self.system.loglik(th, out=ll)
+            abi._check(lib.gl_posterior_grad(B, q64.data_ptr(), ll.data_ptr(), None, pp, lp_out.data_ptr(), None, st),
+                       "gl_posterior_grad")
+            return
         self.system.loglik_grad(th, out=(ll, gt, None))
         abi._check(lib.gl_posterior_grad(B, q64.data_ptr(), ll.data_ptr(), gt.data_ptr(), pp, lp_out.data_ptr(),
                                          g_out.data_ptr(), st), "gl_posterior_grad")
@@ -111,7 +116,8 @@ class FunctionTarget:
     def __call__(self, q64, q32, lp_out, g_out):
         lp, g = self.fn(q32)
         lp_out.copy_(lp)
-        g_out.copy_(g)
+        if g_out is not None:
+            g_out.copy_(g)
 
 
 class WhitenedTarget:
@@ -128,9 +134,10 @@ class WhitenedTarget:
         self._buf = None
 
     def to_z(self, x: torch.Tensor) -> torch.Tensor:
-        z = torch.empty_like(x, dtype=torch.float64)
-        abi.gl_hmc_affine(x.shape[0], self.d, x.contiguous().data_ptr(), self.mu.data_ptr(), self.L.data_ptr(),
-                          z.data_ptr(), None, torch.cuda.current_stream(x.device).cuda_stream)
+        xc = x.to(torch.float64).contiguous()
+        z = torch.empty_like(xc)
+        abi.gl_hmc_affine(xc.shape[0], self.d, xc.data_ptr(), self.mu.data_ptr(), self.L.data_ptr(), z.data_ptr(),
+                          None, torch.cuda.current_stream(x.device).cuda_stream)
         return z
 
     def __call__(self, q64, q32, lp_out, g_out):

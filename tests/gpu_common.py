@@ -2,7 +2,7 @@
 comes from the FP64 oracle, and the parity tolerances.
 
 Tolerances (FP32 GPU path vs FP64 oracle), per vector:
-  log L:  |l_gpu - l_ref| <= 1e-4 * max(|l_ref|, 1)
+  log L:  |l_gpu - l_ref| <= 1e-4 * max(|l_ref|, 1)  [+ the conditioned term below]
   grad:   |g_gpu - g_ref|_i <= 1e-3 * (|g_ref,i| + 1e-2 * max_j |g_ref,j|)
   images: |M_gpu - M_ref| <= 1e-4 * |M_ref| + 1e-5 * max |M_ref|
 
@@ -12,7 +12,14 @@ a relative error eps in the model image M and its Jacobian J = dM/dparams
 moves component i by at most
   eps * C_i,   C_i = sum_pixels (|g| + |M dg/dM|) |J_i|,
 with g = d log L / d M. Those cases add eps * C_i to the gradient tolerance;
-the oracle supplies M and J. EPS_MODEL = 1e-5 is the FP32 accuracy of the
+the oracle supplies M and J. log L itself is a sum over pixels of terms
+l_i = -(r_i^2/v_i + log(2 pi v_i))/2 of both signs; where they nearly cancel
+(a model close to the data) |l| says nothing of the size of the terms, so
+the log L tolerance adds
+  LL_TERM * sum_i |l_i| + EPS_MODEL * sum_i |g_i M_i|,
+FP32 arithmetic and in-warp FP32 sums of the terms (a few ulp of each,
+2e-6 with margin) plus the model error carried through g = dl/dM.
+EPS_MODEL = 1e-5 is the FP32 accuracy of the
 per-pixel model: ray positions carry ~1-2e-7 arcsec of rounding (coordinates
 and deflections of ~2 arcsec at unit roundoff 6e-8), which the steepest
 Sersic profiles of the workloads (log-slope up to ~40/arcsec at R_eff = 0.05)
@@ -25,6 +32,7 @@ import oracle
 from paper_2202_07663_gb300 import inputs
 
 LL_RTOL = 1e-4
+LL_TERM = 2e-6
 G_RTOL = 1e-3
 G_FLOOR = 1e-2
 EPS_MODEL = 1e-5
@@ -63,9 +71,31 @@ def conditioned_bound(spec, image, psf, params, sigma=None, gain=None):
     return out
 
 
-def ll_err(ll, ref):
+def ll_bound(spec, image, psf, params, sigma=None, gain=None):
+    """LL_TERM * sum |l_i| + EPS_MODEL * sum |g_i M_i| per vector (see the module docstring)."""
+    sigma = np.float32(spec.sigma_bkg) if sigma is None else sigma
+    G = spec.gain_exposure if gain is None else gain
+    inv = 1.0 / G if G > 0 else 0.0
+    D = image.astype(np.float64)
+    s2 = np.asarray(sigma, np.float64) ** 2
+    Ms = oracle.simulate(np.asarray(params, np.float32).astype(np.float64), spec.H, spec.W, psf, spec.pixel_scale,
+                         spec.k)
+    out = np.empty(len(Ms))
+    for b, M in enumerate(Ms):
+        v = s2 + M * inv
+        r = D - M
+        terms = -0.5 * (r * r / v + np.log(2 * np.pi * v))
+        g = r / v + (r * r / (v * v) - 1 / v) * inv / 2
+        out[b] = LL_TERM * np.abs(terms).sum() + EPS_MODEL * np.abs(g * M).sum()
+    return out
+
+
+def ll_err(ll, ref, extra=None):
     """Per-vector error in units of the tolerance (<= 1 passes)."""
-    return np.abs(ll - ref) / (LL_RTOL * np.maximum(np.abs(ref), 1.0))
+    tol = LL_RTOL * np.maximum(np.abs(ref), 1.0)
+    if extra is not None:
+        tol = tol + extra
+    return np.abs(ll - ref) / tol
 
 
 def grad_err(g, ref, extra=None):
@@ -75,8 +105,8 @@ def grad_err(g, ref, extra=None):
     return np.abs(g - ref) / scale
 
 
-def assert_parity(ll, g, rl, rg, what="", extra=None):
-    e1 = ll_err(ll, rl)
+def assert_parity(ll, g, rl, rg, what="", extra=None, ll_extra=None):
+    e1 = ll_err(ll, rl, ll_extra)
     assert np.all(e1 <= 1.0), "%s log L: worst %.3g x tol at %d" % (what, e1.max(), int(np.argmax(e1)))
     if g is not None:
         e2 = grad_err(g, rg, extra)

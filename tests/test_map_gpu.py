@@ -113,23 +113,29 @@ def test_multistart_run_in_lockstep_with_oracle(mods):
     s.close()
 
 
-def test_map_from_the_truth_stays_in_the_mode(mods):
-    """Started at the truth, 300 iterations of the Table 1 schedule stay in
-    the mode's basin: the objective ends within the oscillation that Adam's
-    final step (1e-3 in z) allows on a sharp posterior."""
+def test_map_from_the_truth_reaches_the_mode(mods):
+    """Started at the truth, 300 iterations of the Table 1 schedule end at a
+    point at least as probable as the truth (the mode is not the truth: the
+    noise moves it) whose reduced chi^2 is within noise of the truth's, and
+    at most 1.01 + that noise (Sec. 2.3 marks runs that end at chi2_nu <= 1.01
+    as converged to the global mode)."""
     abi, gmap = mods
     spec, truth, psf, image = _paper_system(80, 202)
     s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
     tt = torch.from_numpy(truth.astype(np.float32)[None]).cuda()
     res = gmap.MultiStartMAP(s, steps=300).run(tt.repeat(4, 1))
-    ll_t = s.loglik(tt).cpu().numpy()
+    ll_t, c2_t = (x.cpu().numpy() for x in s.loglik(tt, chi2=True))
+    _, c2 = s.loglik(res.theta, chi2=True)
     s.close()
+    dof = spec.H * spec.W - 22
     zt = mo.inverse_bijector(truth[None].astype(np.float32).astype(np.float64))
     f_truth = mo.objective_grad(zt, ll_t, np.zeros((1, 22)))[0][0]
     f = res.objective.cpu().numpy()
-    assert np.all(f <= f_truth + 100.0)
-    rel = np.abs(res.theta.cpu().numpy() - truth[None]) / (np.abs(truth[None]) + 0.05)
-    assert rel.max() < 0.05
+    assert np.all(f <= f_truth + 1e-3)
+    chi2nu, chi2nu_t = c2.cpu().numpy() / dof, c2_t[0] / dof
+    noise = np.sqrt(2.0 / dof)
+    assert np.all(chi2nu <= chi2nu_t + noise)
+    assert np.all(chi2nu <= 1.01 + 2 * noise)
 
 
 def test_multistart_from_the_prior_descends(mods, golden_constants):
