@@ -137,3 +137,24 @@ def test_every_planted_vi_mistake_fails_a_pin():
             results = dict(f.result() for f in futs)
     survivors = [n for n, rc in results.items() if rc == 0]
     assert not survivors, "VI mutants not caught by any pin: %s" % survivors
+
+
+HMC_MUTANTS = {
+    "chees_drops_jitter_factor": ("grad += w[cidx] * t * a * c", "grad += w[cidx] * a * c"),
+    "chees_velocity_sign": ("c = np.sum((q_prop[cidx] - mp) * v_prop[cidx])",
+                            "c = -np.sum((q_prop[cidx] - mp) * v_prop[cidx])"),
+    "chees_previous_uncentred": ("np.sum((q_prev[cidx] - m) ** 2)", "np.sum(q_prev[cidx] ** 2)"),
+    "chees_criterion_scale": ("crit += w[cidx] * 0.25 * a * a", "crit += w[cidx] * 0.5 * a * a"),
+    "chees_unweighted": ("grad += w[cidx] * t * a * c", "grad += t * a * c"),
+    "halton_first_digit": ("out, f = 0.0, 1.0 / base", "out, f = 0.0, 0.5 / base"),
+}
+
+
+def test_every_planted_hmc_mistake_fails_a_pin():
+    with tempfile.TemporaryDirectory() as tmp:
+        with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+            futs = [ex.submit(_run_map_mutant, n, o, w, tmp, "hmc_oracle.py", "test_hmc_oracle.py")
+                    for n, (o, w) in HMC_MUTANTS.items()]
+            results = dict(f.result() for f in futs)
+    survivors = [n for n, rc in results.items() if rc == 0]
+    assert not survivors, "HMC mutants not caught by any pin: %s" % survivors
