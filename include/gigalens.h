@@ -306,6 +306,25 @@ int gl_hmc_finish(int B, int d, const double* p0, const double* logp0, double* p
                   void* stream);
 
 /*
+ * gl_hmc_chees - the trajectory-length gradient of the ChEES criterion
+ *   (Hoffman, Radul & Sountsov 2021), which Sec. 2.5 adapts during the first
+ *   80% of burn-in. For chains b with start q_prev[b], proposal q_prop[b] and
+ *   end momentum p_prop[b] after a trajectory of length t:
+ *   a_b = |q_prop[b] - m'|^2 - |q_prev[b] - m|^2, c_b = (q_prop[b] - m') .
+ *   (inv_mass * p_prop[b]), m and m' the chain means (m' over finite
+ *   proposals); out[0] = sum w t a c / sum w (gradient in log T),
+ *   out[1] = sum w a^2/4 / sum w (the criterion), out[2] = sum w, with
+ *   w = accept_prob; chains with a non-finite proposal, momentum or weight
+ *   are left out; sum w = 0 gives zeros. Device float64 arrays [B, d], [d],
+ *   [B], out [3]; 1 <= B <= GL_HMC_CHEES_MAX_B, 1 <= d <= GL_HMC_CHEES_MAX_D.
+ *   Fixed reduction order: equal inputs give equal outputs.
+ */
+#define GL_HMC_CHEES_MAX_B 16384
+#define GL_HMC_CHEES_MAX_D 1024
+int gl_hmc_chees(int B, int d, const double* q_prev, const double* q_prop, const double* p_prop,
+                 const double* inv_mass, const double* accept_prob, double t, double* out, void* stream);
+
+/*
  * Dense preconditioning (Sec. 2.5: the mass matrix set to the inverse of a
  * posterior covariance Sigma = L L^T, e.g. the variational one). HMC with
  * identity mass on whitened coordinates x is HMC with mass Sigma^-1 on

@@ -54,6 +54,7 @@ SIGNATURES = {
     "gl_map_adam_step": ([_i, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_leapfrog": ([_i, _i, _vp, _vp, _vp, _vp, _d, _d, _vp, _vp], _i),
     "gl_hmc_finish": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "gl_hmc_chees": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp], _i),
     "gl_hmc_affine": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_affine_pullback": ([_i, _i, _vp, _vp, _vp, _vp], _i),
     "gl_vi_param_count": ([_i], ctypes.c_size_t),
@@ -181,6 +182,11 @@ def gl_hmc_finish(B, d, p0, logp0, p, grad_new, logp_new, q_new, inv_mass, log_u
                   stream, accept_prob=None):
     _check(lib_handle().gl_hmc_finish(B, d, p0, logp0, p, grad_new, logp_new, q_new, inv_mass, log_u, float(eps), q,
                                       logp, grad, accepted, accept_prob, stream), "gl_hmc_finish")
+
+
+def gl_hmc_chees(B, d, q_prev, q_prop, p_prop, inv_mass, accept_prob, t, out, stream):
+    _check(lib_handle().gl_hmc_chees(B, d, q_prev, q_prop, p_prop, inv_mass, accept_prob, float(t), out, stream),
+           "gl_hmc_chees")
 
 
 def gl_hmc_affine(B, d, x, mu, L, z, z32, stream):

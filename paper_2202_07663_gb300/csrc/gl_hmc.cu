@@ -107,6 +107,86 @@ __global__ void k_affine_pullback(int B, int d, const double* __restrict__ gz, c
   }
 }
 
+// ChEES gradient of Hoffman, Radul & Sountsov (2021) for the trajectory-length
+// adaptation: per chain a = |q' - m'|^2 - |q - m|^2 and c = (q' - m') . M^-1 p',
+// out = [sum w t a c / sum w, sum w a^2/4 / sum w, sum w], w the acceptance
+// probability; a chain with a non-finite proposal, end momentum or weight
+// has no weight and is left out of the proposals' mean m'. One block; fixed
+// thread-to-chain mapping and a fixed reduction tree (reproducible).
+constexpr int kCheesThreads = 256;
+
+__global__ void __launch_bounds__(kCheesThreads) k_hmc_chees(int B, int d, const double* __restrict__ q_prev,
+                                                             const double* __restrict__ q_prop,
+                                                             const double* __restrict__ p_prop,
+                                                             const double* __restrict__ inv_mass,
+                                                             const double* __restrict__ w, double t,
+                                                             double* __restrict__ out) {
+  __shared__ unsigned char ok[GL_HMC_CHEES_MAX_B];
+  __shared__ double m[GL_HMC_CHEES_MAX_D], mp[GL_HMC_CHEES_MAX_D];
+  __shared__ double red[3][kCheesThreads];
+  __shared__ int s_nok;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_nok = 0;
+  __syncthreads();
+  int my_ok = 0;
+  for (int b = tid; b < B; b += blockDim.x) {
+    bool f = isfinite(w[b]);
+    for (int j = 0; j < d && f; ++j) {
+      const size_t i = size_t(b) * d + j;
+      f = isfinite(q_prop[i]) && isfinite(p_prop[i]);
+    }
+    ok[b] = f ? 1 : 0;
+    my_ok += f ? 1 : 0;
+  }
+  atomicAdd(&s_nok, my_ok);   // integer count: order does not matter
+  __syncthreads();
+  const int nok = s_nok;
+  for (int j = tid; j < d; j += blockDim.x) {
+    double a = 0.0, ap = 0.0;
+    for (int b = 0; b < B; ++b) {
+      a += q_prev[size_t(b) * d + j];
+      if (ok[b]) ap += q_prop[size_t(b) * d + j];
+    }
+    m[j] = a / double(B);
+    mp[j] = nok > 0 ? ap / double(nok) : 0.0;
+  }
+  __syncthreads();
+  double sg = 0.0, sc = 0.0, sw = 0.0;
+  for (int b = tid; b < B; b += blockDim.x) {
+    if (!ok[b]) continue;
+    double x2 = 0.0, y2 = 0.0, c = 0.0;
+    for (int j = 0; j < d; ++j) {
+      const size_t i = size_t(b) * d + j;
+      const double dx = q_prop[i] - mp[j], dy = q_prev[i] - m[j];
+      x2 += dx * dx;
+      y2 += dy * dy;
+      c += dx * inv_mass[j] * p_prop[i];
+    }
+    const double a = x2 - y2, wb = w[b];
+    sg += wb * t * a * c;
+    sc += wb * 0.25 * a * a;
+    sw += wb;
+  }
+  red[0][tid] = sg;
+  red[1][tid] = sc;
+  red[2][tid] = sw;
+  __syncthreads();
+  for (int o = kCheesThreads / 2; o > 0; o >>= 1) {
+    if (tid < o) {
+      red[0][tid] += red[0][tid + o];
+      red[1][tid] += red[1][tid + o];
+      red[2][tid] += red[2][tid + o];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double W = red[2][0];
+    out[0] = W > 0.0 ? red[0][0] / W : 0.0;
+    out[1] = W > 0.0 ? red[1][0] / W : 0.0;
+    out[2] = W;
+  }
+}
+
 int grid_for(long long n, int threads) {
   long long g = (n + threads - 1) / threads;
   return int(g < 4096 ? (g < 1 ? 1 : g) : 4096);
@@ -147,6 +227,21 @@ int gl_hmc_finish(int B, int d, const double* p0, const double* logp0, double* p
                                                                   accept_prob);
   cudaError_t e = h->after(GL_K_OTHER, st);
   return e == cudaSuccess ? GL_OK : gl_internal::cuda_error(e, "k_hmc_finish");
+}
+
+int gl_hmc_chees(int B, int d, const double* q_prev, const double* q_prop, const double* p_prop,
+                 const double* inv_mass, const double* accept_prob, double t, double* out, void* stream) {
+  if (B < 1 || B > GL_HMC_CHEES_MAX_B || d < 1 || d > GL_HMC_CHEES_MAX_D)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "bad B or d");
+  if (!q_prev || !q_prop || !p_prop || !inv_mass || !accept_prob || !out)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if (!std::isfinite(t)) return gl_internal::set_error(GL_ERR_INVALID_ARG, "t not finite");
+  gl::Hooks* h = gl_internal::hooks();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  h->before(GL_K_OTHER, st);
+  k_hmc_chees<<<1, kCheesThreads, 0, st>>>(B, d, q_prev, q_prop, p_prop, inv_mass, accept_prob, t, out);
+  cudaError_t e = h->after(GL_K_OTHER, st);
+  return e == cudaSuccess ? GL_OK : gl_internal::cuda_error(e, "k_hmc_chees");
 }
 
 int gl_hmc_affine(int B, int d, const double* x, const double* mu, const double* L, double* z_out, float* z32_out,

@@ -17,9 +17,11 @@ matrix is diagonal. Targets:
   ``gl_map_transform`` and ``gl_posterior_grad`` — the paper's sampler;
 - ``FunctionTarget``: any ``logp_grad(q32) -> (logp, grad)`` (tests).
 
-``run_adaptive`` adapts the step size by dual averaging (Hoffman & Gelman
-2014) during the first 80% of burn-in toward a target acceptance
-probability (0.75, Sec. 2.5), then fixes it.
+``run_adaptive`` adapts, during the first 80% of burn-in (Sec. 2.5), the
+step size by dual averaging (Hoffman & Gelman 2014) toward a target
+acceptance probability (0.75) and, optionally, the trajectory length by the
+ChEES criterion (Hoffman, Radul & Sountsov 2021; ``gl_hmc_chees``), with
+jittered leapfrog counts; then fixes both.
 """
 from __future__ import annotations
 
@@ -228,6 +230,37 @@ class DualAveraging:
         return math.exp(self.log_eps_bar)
 
 
+def van_der_corput(m: int, base: int = 2) -> float:
+    """Radical inverse of m >= 1: the jitter sequence 1/2, 1/4, 3/4, 1/8, ..."""
+    out, f = 0.0, 1.0 / base
+    while m > 0:
+        m, r = divmod(m, base)
+        out += r * f
+        f /= base
+    return out
+
+
+class TrajectoryAdam:
+    """Trajectory-length adaptation of Hoffman, Radul & Sountsov (2021):
+    Adam ascent on log T along the ChEES gradient, beta1 = 0, beta2 = 0.95,
+    rate 0.025; T capped at t_max."""
+
+    def __init__(self, T0: float, lr: float = 0.025, beta2: float = 0.95, eps: float = 1e-8,
+                 t_max: float = float("inf")):
+        self.log_t = math.log(T0)
+        self.lr, self.b2, self.eps, self.log_t_max = lr, beta2, eps, math.log(t_max)
+        self.v = 0.0
+        self.n = 0
+
+    def update(self, grad: float) -> float:
+        if math.isfinite(grad):
+            self.n += 1
+            self.v = self.b2 * self.v + (1.0 - self.b2) * grad * grad
+            vhat = self.v / (1.0 - self.b2 ** self.n)
+            self.log_t = min(self.log_t + self.lr * grad / (math.sqrt(vhat) + self.eps), self.log_t_max)
+        return math.exp(self.log_t)
+
+
 @dataclasses.dataclass
 class HMCStats:
     iterations: int
@@ -249,6 +282,8 @@ class AdaptiveRun:
     accept_samples: float
     seconds: float
     grad_evals: int
+    trajectory_length: float = float("nan")   # adapted T (jittered runs), else eps * L
+    mean_leapfrog: float = float("nan")       # leapfrog steps per iteration while sampling
 
 
 class HMC:
@@ -279,23 +314,27 @@ class HMC:
         self.accept_prob = torch.zeros(B, **f64)
         self.logp = torch.empty(B, **f64)
         self.grad = torch.empty(B, d, **f64)
+        self.q_prev = torch.empty(B, d, **f64)
+        self.chees = torch.zeros(3, **f64)
         self.q32.copy_(self.q)
         self.target(self.q, self.q32, self.logp, self.grad)
         self.n_accepted = 0
         self.n_proposed = 0
         self.grad_evals = 0
 
-    def step(self) -> None:
+    def step(self, n_leapfrog: Optional[int] = None) -> None:
         """One HMC iteration (L leapfrog steps + FP64 accept) for all chains."""
         stream = torch.cuda.current_stream(self.dev).cuda_stream
         B, d = self.B, self.d
+        L = self.L if n_leapfrog is None else int(n_leapfrog)
+        self.q_prev.copy_(self.q)
         torch.randn(B, d, generator=self.gen, dtype=torch.float64, device=self.dev, out=self.p0)
         self.p0.mul_(torch.rsqrt(self.inv_mass))
         self.p.copy_(self.p0)
         self.qp.copy_(self.q)
         self.gp.copy_(self.grad)
         q32 = self.q32.data_ptr() if self.target.needs_q32 else None
-        for l in range(self.L):
+        for l in range(L):
             abi.gl_hmc_leapfrog(B, d, self.qp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
                                 self.inv_mass.data_ptr(), self.eps, 0.5 if l == 0 else 1.0, q32, stream)
             self.target(self.qp, self.q32, self.lp_new, self.gp)
@@ -304,8 +343,15 @@ class HMC:
                           self.lp_new.data_ptr(), self.qp.data_ptr(), self.inv_mass.data_ptr(), log_u.data_ptr(),
                           self.eps, self.q.data_ptr(), self.logp.data_ptr(), self.grad.data_ptr(),
                           self.accepted.data_ptr(), stream, self.accept_prob.data_ptr())
-        self.grad_evals += B * self.L
+        self.grad_evals += B * L
         self.n_proposed += B
+
+    def chees_gradient(self, t: float):
+        """(gradient in log T, criterion, weight sum) of the last iteration (device)."""
+        abi.gl_hmc_chees(self.B, self.d, self.q_prev.data_ptr(), self.qp.data_ptr(), self.p.data_ptr(),
+                         self.inv_mass.data_ptr(), self.accept_prob.data_ptr(), t, self.chees.data_ptr(),
+                         torch.cuda.current_stream(self.dev).cuda_stream)
+        return self.chees
 
     def run(self, n_iter: int) -> HMCStats:
         torch.cuda.synchronize(self.dev)
@@ -328,34 +374,57 @@ class HMC:
             self.eps *= math.exp(1.5 * (st.acceptance - target))
         return self.eps
 
-    def run_adaptive(self, n_burn: int, n_samples: int, adapt_frac: float = 0.8,
-                     target_accept: float = 0.75) -> AdaptiveRun:
-        """Burn-in with dual-averaging step-size adaptation over its first
-        adapt_frac, then n_samples recorded iterations at the adapted step size.
-        The step size is shared by all chains and adapted on their mean
-        acceptance probability."""
+    def run_adaptive(self, n_burn: int, n_samples: int, adapt_frac: float = 0.8, target_accept: float = 0.75,
+                     adapt_trajectory: bool = False, max_leapfrog: int = 256) -> AdaptiveRun:
+        """Burn-in with adaptation over its first adapt_frac, then n_samples
+        recorded iterations. The step size (shared by all chains) follows dual
+        averaging on the chains' mean acceptance probability. With
+        adapt_trajectory, each iteration runs ceil(u_m T / eps) leapfrog steps
+        (u_m the van der Corput jitter, also while sampling) and T follows the
+        ChEES gradient (Adam on log T), starting from eps * L; both are frozen
+        when adaptation ends (eps at its dual-averaged value)."""
         torch.cuda.synchronize(self.dev)
         t0 = time.perf_counter()
         e0 = self.grad_evals
         n_adapt = int(adapt_frac * n_burn)
         da = DualAveraging(self.eps, target=target_accept)
+        T = self.eps * self.L
+        ta = TrajectoryAdam(T, t_max=max_leapfrog * self.eps) if adapt_trajectory else None
+        it = 0
+
+        def n_steps():
+            nonlocal it
+            it += 1
+            if not adapt_trajectory:
+                return self.L, self.eps * self.L
+            t = van_der_corput(it) * T
+            return min(max_leapfrog, max(1, math.ceil(t / self.eps))), t
+
         ab = torch.zeros((), dtype=torch.float64, device=self.dev)
         for i in range(n_burn):
-            self.step()
+            L, t = n_steps()
+            self.step(L)
             if i < n_adapt:
+                if adapt_trajectory:
+                    self.chees_gradient(t)
+                    g = float(self.chees[0].item())
+                    T = ta.update(g)
                 self.eps = da.update(float(self.accept_prob.mean().item()))
                 if i == n_adapt - 1:
                     self.eps = da.final()
             ab += self.accept_prob.mean()
         out = torch.empty(n_samples, self.B, self.d, dtype=torch.float64, device=self.dev)
         asum = torch.zeros((), dtype=torch.float64, device=self.dev)
+        nl = 0
         for i in range(n_samples):
-            self.step()
+            L, _ = n_steps()
+            nl += L
+            self.step(L)
             out[i].copy_(self.q)
             asum += self.accept_prob.mean()
         torch.cuda.synchronize(self.dev)
         return AdaptiveRun(out, self.eps, float(ab.item()) / max(1, n_burn), float(asum.item()) / max(1, n_samples),
-                           time.perf_counter() - t0, self.grad_evals - e0)
+                           time.perf_counter() - t0, self.grad_evals - e0, T, nl / max(1, n_samples))
 
 
 @dataclasses.dataclass
@@ -367,12 +436,15 @@ class PosteriorSamples:
 
 def sample_posterior(system, z_center: torch.Tensor, cov: torch.Tensor, chains: int = 50, n_burn: int = 250,
                      n_samples: int = 750, n_leapfrog: int = 5, seed: int = 0, prior=None,
-                     step_size: float = 0.5) -> PosteriorSamples:
+                     step_size: float = 0.3, adapt_trajectory: bool = True,
+                     max_leapfrog: int = 256) -> PosteriorSamples:
     """The sampling step of the pipeline (Sec. 2.5, Table 1): chains drawn from
     N(z_center, cov) (the variational posterior in the paper), HMC on log p~(z)
-    with mass cov^-1 (whitened coordinates), step size adapted by dual averaging
-    over the first 80% of burn-in toward acceptance 0.75, fixed trajectory
-    length n_leapfrog."""
+    with mass cov^-1 (whitened coordinates); over the first 80% of burn-in the
+    step size follows dual averaging toward acceptance 0.75 and, with
+    adapt_trajectory, the trajectory length (from step_size * n_leapfrog,
+    Table 1's 0.3 x 5) follows the ChEES gradient; otherwise n_leapfrog is
+    fixed."""
     from . import map as gmap
     dev = z_center.device
     L = torch.linalg.cholesky(cov.to(torch.float64).to(dev))
@@ -383,7 +455,7 @@ def sample_posterior(system, z_center: torch.Tensor, cov: torch.Tensor, chains: 
     x0 = torch.randn(chains, NPARAM, dtype=torch.float64, device=dev, generator=g)
     sampler = HMC(x0, torch.ones(NPARAM, dtype=torch.float64, device=dev), step_size, n_leapfrog, target=target,
                   seed=seed + 1)
-    run = sampler.run_adaptive(n_burn, n_samples)
+    run = sampler.run_adaptive(n_burn, n_samples, adapt_trajectory=adapt_trajectory, max_leapfrog=max_leapfrog)
     n = n_samples * chains
     z = target.to_z(run.samples.reshape(n, NPARAM))
     th = torch.empty(n, NPARAM, dtype=torch.float32, device=dev)

@@ -27,3 +27,24 @@ def test_dual_averaging_moves_the_right_way():
     d = hmc.DualAveraging(0.2, target=0.75)
     e1 = d.update(0.75)
     assert abs(e1 - 2.0) < 1e-12
+
+
+def test_jitter_sequence_matches_the_oracle():
+    from oracle import hmc_oracle as ho
+    assert [hmc.van_der_corput(m) for m in range(1, 200)] == [ho.van_der_corput(m) for m in range(1, 200)]
+
+
+def test_trajectory_adam_climbs_a_chees_curve():
+    # ChEES(T) = d sin^2 T (standard normal, exact flow): gradient in log T is
+    # T d sin 2T; the ascent settles at the quarter period pi/2
+    ta = hmc.TrajectoryAdam(0.3)
+    T = 0.3
+    for _ in range(3000):
+        T = ta.update(T * 22 * math.sin(2 * T))
+    assert abs(T - math.pi / 2) < 0.05
+    # capped, and a non-finite gradient leaves T alone
+    tb = hmc.TrajectoryAdam(1.0, t_max=1.2)
+    for _ in range(100):
+        Tb = tb.update(5.0)
+    assert Tb == pytest.approx(1.2)
+    assert tb.update(float("nan")) == pytest.approx(1.2)

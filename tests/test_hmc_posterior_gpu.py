@@ -5,6 +5,8 @@
 - the whitening kernels (z = mu + L x, g_x = L^T g_z) against torch FP64;
 - dual-averaging HMC through a dense preconditioner on a correlated Gaussian:
   acceptance at the 0.75 target, sample mean and covariance of the target;
+- the ChEES trajectory-length gradient kernel against its oracle, and
+  ChEES-adapted HMC on a standard normal (trajectory length, moments);
 - the paper's pipeline on a small lens system: Laplace covariance at the
   truth as the preconditioner, chains drawn from it, adapted HMC; R-hat,
   ESS, the truth's coverage and the spread against the Laplace scale.
@@ -17,6 +19,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
+from oracle import hmc_oracle as ho  # noqa: E402
 from oracle import map_oracle as mo  # noqa: E402
 from paper_2202_07663_gb300 import diagnostics as dg  # noqa: E402
 from paper_2202_07663_gb300 import inputs  # noqa: E402
@@ -151,3 +154,48 @@ def test_posterior_hmc_on_a_lens_system(mods):
     zt = (th.mean(0) - torch.from_numpy(truth)).abs() / th.std(0)
     assert zt.max().item() < 5.0, zt
     assert math.isfinite(run.step_size) and run.step_size > 0
+
+
+def test_chees_kernel_matches_oracle(mods):
+    abi, _, _ = mods
+    rng = np.random.default_rng(30)
+    st = torch.cuda.current_stream().cuda_stream
+    for B, d in ((50, 22), (1000, 7), (3, 1)):
+        q, qp, p = (rng.normal(size=(B, d)) + 0.2 for _ in range(3))
+        im = rng.uniform(0.5, 2.0, d)
+        w = rng.uniform(0, 1, B)
+        if B > 3:
+            w[1] = 0.0
+            qp[2, 0] = np.nan     # left out of the proposals' mean and the sums
+            p[3, d - 1] = np.inf
+        t = 1.37
+        ref_g, ref_c = ho.chees_grad_log_t(q, qp, im * p, w, t)
+        dv = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (q, qp, p, im, w)]
+        out = torch.empty(3, dtype=torch.float64, device="cuda")
+        abi.gl_hmc_chees(B, d, *[x.data_ptr() for x in dv], t, out.data_ptr(), st)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        assert o[0] == pytest.approx(ref_g, rel=1e-10, abs=1e-12)
+        assert o[1] == pytest.approx(ref_c, rel=1e-10, abs=1e-12)
+
+
+def test_chees_adapted_hmc_on_a_standard_normal(mods):
+    abi, hmc, _ = mods
+    d, B = 22, 128
+
+    def lg(q32):
+        q = q32.double()
+        return -0.5 * (q * q).sum(1), -q
+
+    g = torch.Generator(device="cuda").manual_seed(9)
+    x0 = torch.randn(B, d, dtype=torch.float64, device="cuda", generator=g)
+    sampler = hmc.HMC(x0, torch.ones(d, dtype=torch.float64, device="cuda"), 0.3, 5, logp_grad=lg, seed=12)
+    run = sampler.run_adaptive(n_burn=400, n_samples=300, adapt_trajectory=True)
+    assert 1.0 < run.trajectory_length < 5.0, run.trajectory_length
+    assert 0.65 < run.accept_samples < 0.85, run.accept_samples
+    X = run.samples.reshape(-1, d)
+    assert X.mean(0).abs().max().item() < 0.05
+    assert ((X.var(0) - 1).abs().max().item()) < 0.08
+    xs = run.samples.transpose(0, 1).cpu().numpy()
+    assert dg.ess(xs).min() > 0.25 * B * 300     # a large fraction of independent draws
+    assert dg.rhat(xs).max() < 1.02
