@@ -300,6 +300,11 @@ int gl_posterior_grad(int B, const double* z, const double* loglik, const double
  */
 int gl_hmc_leapfrog(int B, int d, double* q, double* p, const double* grad, const double* inv_mass, double eps,
                     double kick, float* q32_out, void* stream);
+/* gl_hmc_leapfrog_dev - gl_hmc_leapfrog with eps read from device memory
+ *   (eps_dev, one float64) when the kernel runs, so that a captured CUDA
+ *   graph of a leapfrog step can be replayed while the step size changes. */
+int gl_hmc_leapfrog_dev(int B, int d, double* q, double* p, const double* grad, const double* inv_mass,
+                        const double* eps_dev, double kick, float* q32_out, void* stream);
 int gl_hmc_finish(int B, int d, const double* p0, const double* logp0, double* p, const double* grad_new,
                   const double* logp_new, const double* q_new, const double* inv_mass, const double* log_u,
                   double eps, double* q, double* logp, double* grad, int* accepted, double* accept_prob,

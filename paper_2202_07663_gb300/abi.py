@@ -53,6 +53,7 @@ SIGNATURES = {
     "gl_map_transform": ([_i, _vp, _vp, _vp, _vp], _i),
     "gl_map_adam_step": ([_i, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_leapfrog": ([_i, _i, _vp, _vp, _vp, _vp, _d, _d, _vp, _vp], _i),
+    "gl_hmc_leapfrog_dev": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp], _i),
     "gl_hmc_finish": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_chees": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp], _i),
     "gl_hmc_affine": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp], _i),
@@ -176,6 +177,11 @@ def gl_simulate(handle, params_ptr, B, images_ptr, stream):
 def gl_hmc_leapfrog(B, d, q, p, grad, inv_mass, eps, kick, q32, stream):
     _check(lib_handle().gl_hmc_leapfrog(B, d, q, p, grad, inv_mass, float(eps), float(kick), q32, stream),
            "gl_hmc_leapfrog")
+
+
+def gl_hmc_leapfrog_dev(B, d, q, p, grad, inv_mass, eps_dev, kick, q32, stream):
+    _check(lib_handle().gl_hmc_leapfrog_dev(B, d, q, p, grad, inv_mass, eps_dev, float(kick), q32, stream),
+           "gl_hmc_leapfrog_dev")
 
 
 def gl_hmc_finish(B, d, p0, logp0, p, grad_new, logp_new, q_new, inv_mass, log_u, eps, q, logp, grad, accepted,

@@ -290,7 +290,8 @@ class HMC:
     """B chains of HMC with diagonal mass on a target (default: the lens log L of ``system``)."""
 
     def __init__(self, q0: torch.Tensor, inv_mass: torch.Tensor, step_size: float, n_leapfrog: int,
-                 system=None, logp_grad: Optional[Callable] = None, target=None, seed: int = 0):
+                 system=None, logp_grad: Optional[Callable] = None, target=None, seed: int = 0,
+                 graphs: bool = False):
         self.q = q0.to(torch.float64).contiguous().clone()
         self.B, self.d = self.q.shape
         self.dev = self.q.device
@@ -316,6 +317,13 @@ class HMC:
         self.grad = torch.empty(B, d, **f64)
         self.q_prev = torch.empty(B, d, **f64)
         self.chees = torch.zeros(3, **f64)
+        # one leapfrog update + one target evaluation, captured once per kick
+        # (0.5 opens a trajectory, 1 continues it) and replayed; eps is read
+        # from eps_dev when the graph runs
+        self.graphs = bool(graphs)
+        self.eps_dev = torch.full((1,), self.eps, **f64)
+        self._eps_dev_val = self.eps
+        self._graph = {}
         self.q32.copy_(self.q)
         self.target(self.q, self.q32, self.logp, self.grad)
         self.n_accepted = 0
@@ -334,10 +342,17 @@ class HMC:
         self.qp.copy_(self.q)
         self.gp.copy_(self.grad)
         q32 = self.q32.data_ptr() if self.target.needs_q32 else None
-        for l in range(L):
-            abi.gl_hmc_leapfrog(B, d, self.qp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
-                                self.inv_mass.data_ptr(), self.eps, 0.5 if l == 0 else 1.0, q32, stream)
-            self.target(self.qp, self.q32, self.lp_new, self.gp)
+        if self.graphs:
+            if self._eps_dev_val != self.eps:
+                self.eps_dev.fill_(self.eps)
+                self._eps_dev_val = self.eps
+            for l in range(L):
+                self._leapfrog_graph(0.5 if l == 0 else 1.0).replay()
+        else:
+            for l in range(L):
+                abi.gl_hmc_leapfrog(B, d, self.qp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
+                                    self.inv_mass.data_ptr(), self.eps, 0.5 if l == 0 else 1.0, q32, stream)
+                self.target(self.qp, self.q32, self.lp_new, self.gp)
         log_u = torch.rand(B, generator=self.gen, dtype=torch.float64, device=self.dev).log_()
         abi.gl_hmc_finish(B, d, self.p0.data_ptr(), self.logp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
                           self.lp_new.data_ptr(), self.qp.data_ptr(), self.inv_mass.data_ptr(), log_u.data_ptr(),
@@ -345,6 +360,19 @@ class HMC:
                           self.accepted.data_ptr(), stream, self.accept_prob.data_ptr())
         self.grad_evals += B * L
         self.n_proposed += B
+
+    def _leapfrog_graph(self, kick: float):
+        g = self._graph.get(kick)
+        if g is None:
+            g = torch.cuda.CUDAGraph()
+            q32 = self.q32.data_ptr() if self.target.needs_q32 else None
+            with torch.cuda.graph(g, capture_error_mode="thread_local"):
+                st = torch.cuda.current_stream(self.dev).cuda_stream
+                abi.gl_hmc_leapfrog_dev(self.B, self.d, self.qp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
+                                        self.inv_mass.data_ptr(), self.eps_dev.data_ptr(), kick, q32, st)
+                self.target(self.qp, self.q32, self.lp_new, self.gp)
+            self._graph[kick] = g
+        return g
 
     def chees_gradient(self, t: float):
         """(gradient in log T, criterion, weight sum) of the last iteration (device)."""
@@ -437,16 +465,18 @@ class PosteriorSamples:
 def sample_posterior(system, z_center: torch.Tensor, cov: torch.Tensor, chains: int = 50, n_burn: int = 250,
                      n_samples: int = 750, n_leapfrog: int = 5, seed: int = 0, prior=None,
                      step_size: float = 0.3, adapt_trajectory: bool = True,
-                     max_leapfrog: int = 256) -> PosteriorSamples:
+                     max_leapfrog: int = 256, graphs: bool = True) -> PosteriorSamples:
     """The sampling step of the pipeline (Sec. 2.5, Table 1): chains drawn from
     N(z_center, cov) (the variational posterior in the paper), HMC on log p~(z)
     with mass cov^-1 (whitened coordinates); over the first 80% of burn-in the
     step size follows dual averaging toward acceptance 0.75 and, with
     adapt_trajectory, the trajectory length (from step_size * n_leapfrog,
     Table 1's 0.3 x 5) follows the ChEES gradient; otherwise n_leapfrog is
-    fixed."""
-    from . import map as gmap
+    fixed. With graphs, each leapfrog step is a replayed CUDA graph.
+    The system's scratch is reserved for the chains first (no allocation
+    may happen inside a captured graph)."""
     dev = z_center.device
+    system.reserve(chains)
     L = torch.linalg.cholesky(cov.to(torch.float64).to(dev))
     post = PosteriorTarget(system, prior)
     target = WhitenedTarget(post, z_center.to(dev), L)
@@ -454,7 +484,7 @@ def sample_posterior(system, z_center: torch.Tensor, cov: torch.Tensor, chains: 
     g.manual_seed(seed)
     x0 = torch.randn(chains, NPARAM, dtype=torch.float64, device=dev, generator=g)
     sampler = HMC(x0, torch.ones(NPARAM, dtype=torch.float64, device=dev), step_size, n_leapfrog, target=target,
-                  seed=seed + 1)
+                  seed=seed + 1, graphs=graphs)
     run = sampler.run_adaptive(n_burn, n_samples, adapt_trajectory=adapt_trajectory, max_leapfrog=max_leapfrog)
     n = n_samples * chains
     z = target.to_z(run.samples.reshape(n, NPARAM))

@@ -7,6 +7,8 @@
   acceptance at the 0.75 target, sample mean and covariance of the target;
 - the ChEES trajectory-length gradient kernel against its oracle, and
   ChEES-adapted HMC on a standard normal (trajectory length, moments);
+- leapfrog steps replayed as CUDA graphs give the eager path's chains bit
+  for bit (same kernels, same order, step size read from device memory);
 - the paper's pipeline on a small lens system: Laplace covariance at the
   truth as the preconditioner, chains drawn from it, adapted HMC; R-hat,
   ESS, the truth's coverage and the spread against the Laplace scale.
@@ -199,3 +201,25 @@ def test_chees_adapted_hmc_on_a_standard_normal(mods):
     xs = run.samples.transpose(0, 1).cpu().numpy()
     assert dg.ess(xs).min() > 0.25 * B * 300     # a large fraction of independent draws
     assert dg.rhat(xs).max() < 1.02
+
+
+def test_graph_replay_matches_eager(mods):
+    abi, hmc, _ = mods
+    spec, truth, psf, image = _paper_system(30, 8, K=5)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    s.reserve(16)
+    post = hmc.PosteriorTarget(s)
+    z_truth = torch.from_numpy(mo.inverse_bijector(truth)[0]).cuda()
+    L = torch.linalg.cholesky(hmc.laplace_covariance(post, z_truth))
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x0 = torch.randn(16, 22, dtype=torch.float64, device="cuda", generator=g)
+    runs = []
+    for graphs in (False, True):
+        target = hmc.WhitenedTarget(hmc.PosteriorTarget(s), z_truth, L)
+        sm = hmc.HMC(x0, torch.ones(22, dtype=torch.float64, device="cuda"), 0.3, 5, target=target, seed=3,
+                     graphs=graphs)
+        runs.append(sm.run_adaptive(n_burn=8, n_samples=5, adapt_trajectory=True))
+    s.close()
+    assert runs[0].step_size == runs[1].step_size
+    assert runs[0].trajectory_length == runs[1].trajectory_length
+    assert torch.equal(runs[0].samples, runs[1].samples)
