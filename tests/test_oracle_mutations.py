@@ -158,3 +158,24 @@ def test_every_planted_hmc_mistake_fails_a_pin():
             results = dict(f.result() for f in futs)
     survivors = [n for n, rc in results.items() if rc == 0]
     assert not survivors, "HMC mutants not caught by any pin: %s" % survivors
+
+
+VARIANT_MUTANTS = {
+    "variance_not_clipped": ("np.maximum(image, 0.0) / gain_exposure", "image / gain_exposure"),
+    "solve_unweighted": ("w = 1.0 / np.asarray(var, np.float64)", "w = np.ones_like(np.asarray(var, np.float64))"),
+    "rhs_swapped": ("r = np.array([np.sum(w * A[b, i] * D) for i in range(2)])",
+                    "r = np.array([np.sum(w * A[b, 1 - i] * D) for i in range(2)])"),
+    "basis_swapped": ("pl[:, I_L], pl[:, I_S] = 1.0, 0.0", "pl[:, I_L], pl[:, I_S] = 0.0, 1.0"),
+    "amplitude_gradient_kept": ("        g[:, I_L] = 0.0\n", "        g[:, I_L] = g[:, I_L]\n"),
+    "singular_keeps_weaker": ("i = max(live, key=lambda j: G[j, j])", "i = min(range(2), key=lambda j: G[j, j])"),
+}
+
+
+def test_every_planted_variant_mistake_fails_a_pin():
+    with tempfile.TemporaryDirectory() as tmp:
+        with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+            futs = [ex.submit(_run_map_mutant, n, o, w, tmp, "variant_oracle.py", "test_variant_oracle.py")
+                    for n, (o, w) in VARIANT_MUTANTS.items()]
+            results = dict(f.result() for f in futs)
+    survivors = [n for n, rc in results.items() if rc == 0]
+    assert not survivors, "variant mutants not caught by any pin: %s" % survivors
