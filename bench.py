@@ -370,6 +370,44 @@ def run_hmc_paper_workload(device, chains: int = 50, n_burn: int = 250, n_sample
             "log_density": "posterior of the unconstrained parameters (prior Eq. sim-dist, bijectors)"}
 
 
+def run_variant_workload(device, B: int = 4096, steps: int = 10):
+    """Sec. 2.1.2 variant: observed-image variance, log L profiled over the two
+    light amplitudes (2B basis images, 2x2 solves, then log L + gradient),
+    against the plain log L + gradient on the same system and vectors
+    (80x80, k = 2, 11x11 PSF, sigma_bkg = 0.2, t_exp = 100 s)."""
+    import torch
+    from paper_2202_07663_gb300 import abi
+    spec = inputs.PAPER_SAMPLE_SPEC
+    rng = np.random.default_rng(303)
+    truth = inputs.draw_table(rng, inputs.PAPER_SIM, 1)[0]
+    psf = inputs.make_psf(spec).astype(np.float32)
+    blank = np.zeros((spec.H, spec.W), np.float32)
+    s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
+    s0.close()
+    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg,
+                     observed_variance=True)
+    s.reserve(2 * B)
+    p = torch.from_numpy(inputs.draw_perturbed(np.random.default_rng(7), truth, B, frac=0.05)
+                         .astype(np.float32)).to(device)
+    out = {"workload": "variant-obsvar-profiled-80x80-k2-psf11", "B": B}
+    for name, fn in (("plain", lambda: s.loglik_grad(p)), ("profiled", lambda: s.loglik_grad_profiled(p))):
+        fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(e) / steps
+        out[name] = {"ms_per_call": ms, "evals_per_s": B / (ms * 1e-3)}
+    out["profiled_over_plain_time"] = out["profiled"]["ms_per_call"] / out["plain"]["ms_per_call"]
+    s.close()
+    return out
+
+
 def cpu_baseline(spec, psf, image, params, budget_s: float = 12.0):
     """The FP64 oracle (log L + gradient) on a bounded sample of the same workload."""
     import oracle
@@ -549,7 +587,7 @@ def main():
     if world == 1 and not args.no_workloads:
         workloads = {"hmc": run_hmc_workload(device), "stress": run_stress_workload(device),
                      "serving": run_serving_workload(device), "map": run_map_workload(device),
-                     "hmc_paper": run_hmc_paper_workload(device)}
+                     "hmc_paper": run_hmc_paper_workload(device), "variant": run_variant_workload(device)}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",

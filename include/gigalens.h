@@ -89,6 +89,18 @@ int gl_system_create(gl_system** out, const float* image, const float* noise_map
                      int H, int W, const float* psf, int K, double pixel_scale, int supersample,
                      double gain_exposure, void* stream);
 
+/*
+ * gl_system_create_obsvar - the same system with the variance map built from
+ *   the observed image, the alternative of Sec. 2.1.2:
+ *   sigma_tot^2 = sigma_bkg^2 + max(I_obs, 0) / (G t_exp) per pixel (negative
+ *   observed pixels count as zero), fixed at creation; the model-dependent
+ *   Poisson term is off (gain_exposure only enters the map). Arguments and
+ *   errors as gl_system_create.
+ */
+int gl_system_create_obsvar(gl_system** out, const float* image, const float* noise_map, float sigma_bkg,
+                            int H, int W, const float* psf, int K, double pixel_scale, int supersample,
+                            double gain_exposure, void* stream);
+
 /* Free the system, its resident data and its scratch. Synchronises the
  * device first. NULL is accepted. */
 int gl_system_destroy(gl_system* sys);
@@ -387,6 +399,28 @@ int gl_vi_sample(int n, int d, const double* eps, const double* phi, const gl_pr
 int gl_vi_step(int n, int d, const double* eps, const double* logp, const double* grad_z, int estimator,
                double* phi, double* m, double* v, int t, double lr, double beta1, double beta2, double adam_eps,
                double* grad_out, double* loss_out, void* workspace, void* stream);
+
+/*
+ * gl_loglik_grad_profiled - log L profiled over the two light amplitudes
+ *   (Sec. 2.1.2: with a parameter-independent variance the model is linear in
+ *   I_l and I_s, so they are solved in closed form). Per vector: the model
+ *   images A_l, A_s at unit amplitudes, the 2x2 weighted least-squares solve
+ *   [<A_l,A_l> <A_l,A_s>; <A_s,A_l> <A_s,A_s>] [I_l; I_s] = [<A_l,D>; <A_s,D>]
+ *   (<a,b> = sum a b / sigma_tot^2; FP64), then log L, chi^2 and the gradient
+ *   at the solved amplitudes. Where the system is singular (a self-product
+ *   below 1e-12 of the other, or det below 1e-12 of the diagonal product) the
+ *   amplitude with the smaller self-product is 0 and the other is solved
+ *   alone. The input's I_l and I_s are ignored; grad_out entries 14 and 21
+ *   are 0 (the profiled log L does not depend on them) and the other 20 are
+ *   the profiled gradient. amps_out (may be NULL) receives [B, 2] float64
+ *   (I_l, I_s); chi2_out and grad_out may be NULL. Needs a system whose
+ *   variance does not depend on the model (gl_system_create_obsvar, or
+ *   gain_exposure <= 0), else GL_ERR_INVALID_ARG; 0 <= B <= 2^23. Device
+ *   pointers; asynchronous on stream; scratch for 2B basis images is held by
+ *   the system and grows on demand.
+ */
+int gl_loglik_grad_profiled(gl_system* sys, const float* params, int B, double* loglik_out, double* chi2_out,
+                            double* grad_out, double* amps_out, void* stream);
 
 /* Name of a status code (static string). */
 const char* gl_error_string(int code);

@@ -35,6 +35,7 @@ _f = ctypes.c_float
 # name -> (argtypes, restype), mirroring include/gigalens.h
 SIGNATURES = {
     "gl_system_create": ([ctypes.POINTER(_vp), _vp, _vp, _f, _i, _i, _vp, _i, _d, _i, _d, _vp], _i),
+    "gl_system_create_obsvar": ([ctypes.POINTER(_vp), _vp, _vp, _f, _i, _i, _vp, _i, _d, _i, _d, _vp], _i),
     "gl_system_destroy": ([_vp], _i),
     "gl_system_reserve": ([_vp, _i], _i),
     "gl_system_scratch_bytes": ([_vp, _i], ctypes.c_size_t),
@@ -52,6 +53,7 @@ SIGNATURES = {
     "gl_map_inverse": ([_i, _vp, _vp, _vp, _vp], _i),
     "gl_map_transform": ([_i, _vp, _vp, _vp, _vp], _i),
     "gl_map_adam_step": ([_i, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "gl_loglik_grad_profiled": ([_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_leapfrog": ([_i, _i, _vp, _vp, _vp, _vp, _d, _d, _vp, _vp], _i),
     "gl_hmc_leapfrog_dev": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp], _i),
     "gl_hmc_finish": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
@@ -133,8 +135,10 @@ def _dptr(t, dtype, shape=None, name="tensor") -> int:
 
 # ------------------------------------------------------------- raw calls ----
 
-def gl_system_create(image, noise_map, sigma_bkg, psf, pixel_scale, supersample, gain_exposure, stream=0):
+def gl_system_create(image, noise_map, sigma_bkg, psf, pixel_scale, supersample, gain_exposure, stream=0,
+                     observed_variance: bool = False):
     lib = lib_handle()
+    create = lib.gl_system_create_obsvar if observed_variance else lib.gl_system_create
     image = np.ascontiguousarray(image, dtype=np.float32)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
     H, W = image.shape
@@ -145,10 +149,10 @@ def gl_system_create(image, noise_map, sigma_bkg, psf, pixel_scale, supersample,
     if noise_map is not None:
         nm = np.ascontiguousarray(np.broadcast_to(np.asarray(noise_map, dtype=np.float32), image.shape))
     h = _vp()
-    code = lib.gl_system_create(ctypes.byref(h), image.ctypes.data, nm.ctypes.data if nm is not None else None,
-                                float(sigma_bkg), H, W, psf.ctypes.data, K, float(pixel_scale), int(supersample),
-                                float(gain_exposure), stream)
-    _check(code, "gl_system_create")
+    code = create(ctypes.byref(h), image.ctypes.data, nm.ctypes.data if nm is not None else None,
+                  float(sigma_bkg), H, W, psf.ctypes.data, K, float(pixel_scale), int(supersample),
+                  float(gain_exposure), stream)
+    _check(code, "gl_system_create_obsvar" if observed_variance else "gl_system_create")
     return h.value
 
 
@@ -234,7 +238,7 @@ class GLSystem:
     """
 
     def __init__(self, image, psf, pixel_scale: float, supersample: int, gain_exposure: float,
-                 noise_map=None, sigma_bkg: float = 0.0):
+                 noise_map=None, sigma_bkg: float = 0.0, observed_variance: bool = False):
         import torch
         self.H, self.W = np.asarray(image).shape
         self.K = np.asarray(psf).shape[0]
@@ -242,8 +246,9 @@ class GLSystem:
         self.pixel_scale = float(pixel_scale)
         self.gain_exposure = float(gain_exposure)
         self.device = torch.device("cuda", torch.cuda.current_device())
+        self.observed_variance = bool(observed_variance)
         self._h = gl_system_create(image, noise_map, sigma_bkg, psf, pixel_scale, supersample, gain_exposure,
-                                   _stream_ptr())
+                                   _stream_ptr(), observed_variance=observed_variance)
 
     @property
     def handle(self):
@@ -300,6 +305,22 @@ class GLSystem:
                        _dptr(c2, torch.float64, (B,), "chi2") if c2 is not None else None,
                        _dptr(g, torch.float64, (B, NPARAM), "grad"), _stream_ptr(params.device))
         return (ll, g, c2) if chi2 else (ll, g)
+
+    def loglik_grad_profiled(self, params, grad: bool = True, chi2: bool = False):
+        """log L profiled over (I_l, I_s): (loglik [B], grad [B, 22] or None,
+        amplitudes [B, 2][, chi2 [B]]); grad entries 14 and 21 are 0."""
+        import torch
+        p, B = self._params(params)
+        dev = params.device
+        ll = torch.empty(B, dtype=torch.float64, device=dev)
+        g = torch.empty(B, NPARAM, dtype=torch.float64, device=dev) if grad else None
+        amps = torch.empty(B, 2, dtype=torch.float64, device=dev)
+        c2 = torch.empty(B, dtype=torch.float64, device=dev) if chi2 else None
+        _check(lib_handle().gl_loglik_grad_profiled(self._h, p, B, ll.data_ptr(),
+                                                    c2.data_ptr() if chi2 else None,
+                                                    g.data_ptr() if grad else None, amps.data_ptr(),
+                                                    _stream_ptr(dev)), "gl_loglik_grad_profiled")
+        return (ll, g, amps, c2) if chi2 else (ll, g, amps)
 
     def loglik_grad_host(self, params: np.ndarray, loglik: np.ndarray, grad: np.ndarray, chi2=None) -> None:
         """Host-buffer path: params float32 [B,22] and outputs float64 host arrays

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "gl_device.cuh"
+#include "gl_internal.h"
 #include "gl_launch.h"
 
 using gl::Seg;
@@ -35,6 +36,13 @@ struct gl_system {
   double* d_ll = nullptr;
   double* d_c2 = nullptr;
   double* d_grad = nullptr;
+  // likelihood profiled over the light amplitudes: basis parameter rows and
+  // images (2 per vector), parameter rows with the solved amplitudes
+  long long cap_prof = 0;
+  float* d_pbasis = nullptr;
+  float* d_pimg = nullptr;
+  float* d_pfull = nullptr;
+  double* d_pamps = nullptr;
 };
 
 namespace {
@@ -228,34 +236,12 @@ void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_rel
 
 }  // namespace gl_internal
 
-extern "C" {
+namespace {
 
-int gl_system_create(gl_system** out, const float* image, const float* noise_map, float sigma_bkg, int H, int W,
-                     const float* psf, int K, double pixel_scale, int supersample, double gain_exposure,
-                     void* stream) {
-  if (!out) return fail(GL_ERR_INVALID_ARG, "null out");
-  *out = nullptr;
-  if (!image || !psf) return fail(GL_ERR_INVALID_ARG, "null image or psf");
-  if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(GL_ERR_INVALID_ARG, "image size %dx%d", H, W);
-  if (K < 1 || K > 63 || (K % 2) == 0) return fail(GL_ERR_INVALID_ARG, "PSF side K = %d must be odd in [1, 63]", K);
-  if (!(pixel_scale > 0.0) || !std::isfinite(pixel_scale))
-    return fail(GL_ERR_INVALID_ARG, "pixel_scale must be > 0");
-  if (supersample < 1 || supersample > 16) return fail(GL_ERR_INVALID_ARG, "supersample = %d", supersample);
-  if (!std::isfinite(gain_exposure)) return fail(GL_ERR_INVALID_ARG, "gain_exposure not finite");
+// Shared by the two constructors: validated sizes, the per-pixel variance s2.
+int create_impl(gl_system** out, const float* image, const std::vector<float>& s2, int H, int W, const float* psf,
+                int K, double pixel_scale, int supersample, double gain_exposure, void* stream) {
   const size_t n = size_t(H) * W;
-  if (!finite_all(image, n)) return fail(GL_ERR_INVALID_ARG, "image has non-finite values");
-  if (!finite_all(psf, size_t(K) * K)) return fail(GL_ERR_INVALID_ARG, "psf has non-finite values");
-  std::vector<float> s2(n);
-  if (noise_map) {
-    for (size_t i = 0; i < n; ++i) {
-      if (!(noise_map[i] > 0.f) || !std::isfinite(noise_map[i]))
-        return fail(GL_ERR_INVALID_ARG, "noise_map[%zu] must be finite and > 0", i);
-      s2[i] = noise_map[i] * noise_map[i];
-    }
-  } else {
-    if (!(sigma_bkg > 0.f) || !std::isfinite(sigma_bkg)) return fail(GL_ERR_INVALID_ARG, "sigma_bkg must be > 0");
-    for (size_t i = 0; i < n; ++i) s2[i] = sigma_bkg * sigma_bkg;
-  }
   int dev = 0;
   GL_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   const size_t smem = gl::conv_smem_bytes(H, W, K, false) + CONV_STATIC_SMEM;
@@ -293,6 +279,67 @@ int gl_system_create(gl_system** out, const float* image, const float* noise_map
   return GL_OK;
 }
 
+int check_create(gl_system** out, const float* image, int H, int W, const float* psf, int K, double pixel_scale,
+                 int supersample, double gain_exposure) {
+  if (!out) return fail(GL_ERR_INVALID_ARG, "null out");
+  *out = nullptr;
+  if (!image || !psf) return fail(GL_ERR_INVALID_ARG, "null image or psf");
+  if (H < 1 || W < 1 || H > 4096 || W > 4096) return fail(GL_ERR_INVALID_ARG, "image size %dx%d", H, W);
+  if (K < 1 || K > 63 || (K % 2) == 0) return fail(GL_ERR_INVALID_ARG, "PSF side K = %d must be odd in [1, 63]", K);
+  if (!(pixel_scale > 0.0) || !std::isfinite(pixel_scale))
+    return fail(GL_ERR_INVALID_ARG, "pixel_scale must be > 0");
+  if (supersample < 1 || supersample > 16) return fail(GL_ERR_INVALID_ARG, "supersample = %d", supersample);
+  if (!std::isfinite(gain_exposure)) return fail(GL_ERR_INVALID_ARG, "gain_exposure not finite");
+  if (!finite_all(image, size_t(H) * W)) return fail(GL_ERR_INVALID_ARG, "image has non-finite values");
+  if (!finite_all(psf, size_t(K) * K)) return fail(GL_ERR_INVALID_ARG, "psf has non-finite values");
+  return GL_OK;
+}
+
+// The background variance per pixel from a noise map or a scalar.
+int background_variance(const float* noise_map, float sigma_bkg, size_t n, std::vector<float>& s2) {
+  s2.resize(n);
+  if (noise_map) {
+    for (size_t i = 0; i < n; ++i) {
+      if (!(noise_map[i] > 0.f) || !std::isfinite(noise_map[i]))
+        return fail(GL_ERR_INVALID_ARG, "noise_map[%zu] must be finite and > 0", i);
+      s2[i] = noise_map[i] * noise_map[i];
+    }
+  } else {
+    if (!(sigma_bkg > 0.f) || !std::isfinite(sigma_bkg)) return fail(GL_ERR_INVALID_ARG, "sigma_bkg must be > 0");
+    for (size_t i = 0; i < n; ++i) s2[i] = sigma_bkg * sigma_bkg;
+  }
+  return GL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gl_system_create(gl_system** out, const float* image, const float* noise_map, float sigma_bkg, int H, int W,
+                     const float* psf, int K, double pixel_scale, int supersample, double gain_exposure,
+                     void* stream) {
+  int rc = check_create(out, image, H, W, psf, K, pixel_scale, supersample, gain_exposure);
+  if (rc != GL_OK) return rc;
+  std::vector<float> s2;
+  rc = background_variance(noise_map, sigma_bkg, size_t(H) * W, s2);
+  if (rc != GL_OK) return rc;
+  return create_impl(out, image, s2, H, W, psf, K, pixel_scale, supersample, gain_exposure, stream);
+}
+
+int gl_system_create_obsvar(gl_system** out, const float* image, const float* noise_map, float sigma_bkg, int H,
+                            int W, const float* psf, int K, double pixel_scale, int supersample,
+                            double gain_exposure, void* stream) {
+  int rc = check_create(out, image, H, W, psf, K, pixel_scale, supersample, gain_exposure);
+  if (rc != GL_OK) return rc;
+  std::vector<float> s2;
+  rc = background_variance(noise_map, sigma_bkg, size_t(H) * W, s2);
+  if (rc != GL_OK) return rc;
+  if (gain_exposure > 0.0)
+    for (size_t i = 0; i < s2.size(); ++i)
+      s2[i] = float(double(s2[i]) + (image[i] > 0.f ? double(image[i]) : 0.0) / gain_exposure);
+  return create_impl(out, image, s2, H, W, psf, K, pixel_scale, supersample, 0.0, stream);
+}
+
 int gl_system_destroy(gl_system* s) {
   if (!s) return GL_OK;
   cudaDeviceSynchronize();
@@ -306,6 +353,10 @@ int gl_system_destroy(gl_system* s) {
   cudaFree(s->d_ll);
   cudaFree(s->d_c2);
   cudaFree(s->d_grad);
+  cudaFree(s->d_pbasis);
+  cudaFree(s->d_pimg);
+  cudaFree(s->d_pfull);
+  cudaFree(s->d_pamps);
   delete s;
   return GL_OK;
 }
@@ -364,6 +415,50 @@ int gl_simulate(gl_system* s, const float* params, int B, float* images_out, voi
   if (!images_out) return fail(GL_ERR_INVALID_ARG, "null images_out");
   return run_one(s, params, B, nullptr, nullptr, nullptr, images_out, gl::MODE_SIM,
                  static_cast<cudaStream_t>(stream));
+}
+
+int gl_loglik_grad_profiled(gl_system* s, const float* params, int B, double* loglik_out, double* chi2_out,
+                            double* grad_out, double* amps_out, void* stream) {
+  int rc = check_call(s, params, B);
+  if (rc != GL_OK) return rc;
+  if (B == 0) return GL_OK;
+  if (!loglik_out) return fail(GL_ERR_INVALID_ARG, "null loglik_out");
+  if (s->gain_exposure > 0.0)
+    return fail(GL_ERR_INVALID_ARG, "profiling the amplitudes needs a parameter-independent variance "
+                                    "(gl_system_create_obsvar, or gain_exposure <= 0)");
+  if (B > (1 << 23)) return fail(GL_ERR_INVALID_ARG, "B = %d: the basis images take 2B vectors", B);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (B > s->cap_prof) {
+    cudaFree(s->d_pbasis);
+    cudaFree(s->d_pimg);
+    cudaFree(s->d_pfull);
+    cudaFree(s->d_pamps);
+    s->d_pbasis = s->d_pimg = s->d_pfull = nullptr;
+    s->d_pamps = nullptr;
+    s->cap_prof = 0;
+    const size_t hw = size_t(s->H) * s->W;
+    GL_CUDA(cudaMalloc(&s->d_pbasis, size_t(2) * B * GL_NPARAM * sizeof(float)), "profile scratch");
+    GL_CUDA(cudaMalloc(&s->d_pimg, size_t(2) * B * hw * sizeof(float)), "profile scratch");
+    GL_CUDA(cudaMalloc(&s->d_pfull, size_t(B) * GL_NPARAM * sizeof(float)), "profile scratch");
+    GL_CUDA(cudaMalloc(&s->d_pamps, size_t(2) * B * sizeof(double)), "profile scratch");
+    s->cap_prof = B;
+  }
+  double* amps = amps_out ? amps_out : s->d_pamps;
+  cudaError_t e = gl_internal::launch_basis_params(B, params, s->d_pbasis, st);
+  if (e != cudaSuccess) return cuda_fail(e, "k_basis_params");
+  rc = run_one(s, s->d_pbasis, 2 * B, nullptr, nullptr, nullptr, s->d_pimg, gl::MODE_SIM, st);
+  if (rc != GL_OK) return rc;
+  e = gl_internal::launch_amp_solve(B, s->H * s->W, s->d_pimg, s->d_image, s->d_sigma2, params, s->d_pfull, amps,
+                                    st);
+  if (e != cudaSuccess) return cuda_fail(e, "k_amp_solve");
+  if (grad_out) {
+    rc = run_one(s, s->d_pfull, B, loglik_out, chi2_out, grad_out, nullptr, gl::MODE_GRAD, st);
+    if (rc != GL_OK) return rc;
+    e = gl_internal::launch_zero_amp_grad(B, grad_out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "k_zero_amp_grad");
+    return GL_OK;
+  }
+  return run_one(s, s->d_pfull, B, loglik_out, chi2_out, nullptr, nullptr, gl::MODE_LOGLIK, st);
 }
 
 int gl_loglik_grad_host(gl_system* s, const float* params, int B, double* loglik_out, double* chi2_out,

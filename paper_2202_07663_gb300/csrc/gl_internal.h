@@ -23,4 +23,10 @@ gl::Hooks* hooks();
 // Add kernels launched outside the hooks (graph replays) to the launch count.
 void count_launches(long long n);
 
+// The likelihood profiled over the light amplitudes (gl_variant.cu).
+cudaError_t launch_basis_params(int B, const float* params, float* basis, cudaStream_t st);
+cudaError_t launch_amp_solve(int B, int HW, const float* images, const float* data, const float* sigma2,
+                             const float* params, float* params_out, double* amps, cudaStream_t st);
+cudaError_t launch_zero_amp_grad(int B, double* grad, cudaStream_t st);
+
 }  // namespace gl_internal
