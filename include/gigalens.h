@@ -82,8 +82,11 @@ typedef struct gl_system gl_system;
  * The library copies every input; the caller keeps its buffers. Errors:
  * GL_ERR_INVALID_ARG for bad sizes, pointers or values; GL_ERR_UNSUPPORTED
  * when the zero-padded image does not fit the shared-memory convolution
- * stage ((ceil(H/16)*16 + K - 1) * (W + K - 1) * 4 bytes + K*K*4 must stay
- * below 220 KiB); GL_ERR_OOM / GL_ERR_CUDA on device failures.
+ * stage (PSF sides 11 and 21: (H + K - 1) * P * 4 bytes + 2 K round4(K) * 4,
+ * P = ceil(W/16)*16 + K - 1 rounded up to a multiple of 4 with an odd number
+ * of 16-byte words; other sides: (ceil(H/8)*8 + K - 1) * (W + K - 1) * 4 +
+ * 2 round4(K*K) * 4; either must stay below 220 KiB); GL_ERR_OOM /
+ * GL_ERR_CUDA on device failures.
  */
 int gl_system_create(gl_system** out, const float* image, const float* noise_map, float sigma_bkg,
                      int H, int W, const float* psf, int K, double pixel_scale, int supersample,

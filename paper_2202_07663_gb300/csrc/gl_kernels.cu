@@ -550,6 +550,15 @@ __device__ __forceinline__ void corr_strip_any(const float* in, int Wp, const fl
 // lanes read 32 consecutive shared-memory words of one image row.
 __device__ __forceinline__ int conv_row_units(int W) { return (W + 31) & ~31; }
 
+// Row pitch (floats) of the row-strip convolution: room for 16-column strips
+// plus the K - 1 halo, a multiple of 4 with an odd number of float4 per row.
+__host__ __device__ inline int rowconv_pitch(int W, int K) {
+  int P = ((W + 15) / 16) * 16 + K - 1;
+  P = (P + 3) & ~3;
+  if (((P >> 2) & 1) == 0) P += 4;
+  return P;
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -675,6 +684,196 @@ __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* 
   }
 }
 
+// ---- row-strip convolution for the compile-time PSF sides (11, 21) ----
+//
+// Each thread computes S = 16 consecutive outputs of one image row; the lanes
+// of a warp take consecutive rows. Per kernel row a thread loads the input
+// span (S + K - 1 values) and the kernel row as float4 and does S*K FMAs from
+// registers. The row pitch P (floats) is a multiple of 4 with an odd number
+// of float4 per row, so the 8 lanes of each 128-bit shared-memory phase hit
+// 8 distinct bank groups.
+
+// out[r] = sum_{a,b} ker[a][b] in[(i + a) P + j0 + r + b], r < 16; ker rows of KP floats.
+template <int K>
+__device__ __forceinline__ void corr_row(const float* __restrict__ in, int P, const float* __restrict__ ker, int i,
+                                         int j0, float (&acc)[16]) {
+  constexpr int S = 16, KP = (K + 3) & ~3, NIN = (S + K - 1 + 3) & ~3;
+#pragma unroll
+  for (int r = 0; r < S; ++r) acc[r] = 0.f;
+  const float* row = in + i * P + j0;
+#pragma unroll 1
+  for (int a = 0; a < K; ++a) {
+    float x[NIN];
+    const float4* r4 = reinterpret_cast<const float4*>(row + a * P);
+#pragma unroll
+    for (int q = 0; q < NIN / 4; ++q) {
+      const float4 t = r4[q];
+      x[4 * q] = t.x;
+      x[4 * q + 1] = t.y;
+      x[4 * q + 2] = t.z;
+      x[4 * q + 3] = t.w;
+    }
+    float kr[KP];
+    const float4* k4 = reinterpret_cast<const float4*>(ker + a * KP);
+#pragma unroll
+    for (int q = 0; q < KP / 4; ++q) {
+      const float4 t = k4[q];
+      kr[4 * q] = t.x;
+      kr[4 * q + 1] = t.y;
+      kr[4 * q + 2] = t.z;
+      kr[4 * q + 3] = t.w;
+    }
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+#pragma unroll
+      for (int r = 0; r < S; ++r) acc[r] = fmaf(kr[b], x[r + b], acc[r]);
+    }
+  }
+}
+
+// 4-byte asynchronous global -> shared copy (completes at cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// One vector, PSF side K known at compile time. Shared memory: both PSF
+// orientations ([K][KP], zero padded), the zero-padded input buffer
+// [H + K - 1][P] and, when s.conv_two_buf, an unpadded staging buffer [H][P]
+// for the model values and the correlation output (else they go through the
+// vector's global work slot). After the first pass the input buffer's
+// interior is overwritten with d log L / d M (its zero halo is reused).
+template <int K>
+__device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, double* red2) {
+  constexpr int S = 16, KP = (K + 3) & ~3, c = (K - 1) / 2;
+  const int H = s.H, W = s.W, HW = H * W;
+  const int P = rowconv_pitch(W, K);
+  const int Hp = H + K - 1;
+  float* kerF = smem;
+  float* kerU = smem + K * KP;
+  float* img = smem + 2 * K * KP;
+  float* stage = img + Hp * P;
+  float* work = s.work + size_t(b) * HW;
+  const bool want_sim = (mode == MODE_SIM);
+  const bool want_grad = (mode == MODE_GRAD);
+  const bool two = s.conv_two_buf != 0;
+
+  for (int i = threadIdx.x; i < K * KP; i += blockDim.x) {
+    const int a = i / KP, bb = i - a * KP;
+    kerF[i] = bb < K ? s.psf[(K - 1 - a) * K + (K - 1 - bb)] : 0.f;
+    kerU[i] = bb < K ? s.psf[a * K + bb] : 0.f;
+  }
+  // pixel loops: rows across warps, columns across lanes (coalesced, no division)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // the binned image into the interior (asynchronous copies) while the halo is zeroed
+  for (int i = wid; i < H; i += nw)
+    for (int j = lane; j < W; j += 32) cp_async4(&img[(i + c) * P + j + c], &work[i * W + j]);
+  for (int i = threadIdx.x; i < c * P; i += blockDim.x) {
+    img[i] = 0.f;                       // top halo rows
+    img[(H + c) * P + i] = 0.f;         // bottom halo rows
+  }
+  const int side = P - W;               // left halo c columns + right halo and pitch padding
+  for (int t = threadIdx.x; t < H * side; t += blockDim.x) {
+    const int i = t / side, q = t - i * side;
+    img[(i + c) * P + (q < c ? q : W + q)] = 0.f;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // pass 1: model image M (convolution with the flipped PSF)
+  const int nstrip = (W + S - 1) / S;
+  const int units = nstrip * H;
+  float acc[S];
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int strip = u / H, i = u - strip * H, j0 = strip * S;
+    corr_row<K>(img, P, kerF, i, j0, acc);
+    if (two) {
+      float4* o4 = reinterpret_cast<float4*>(stage + i * P + j0);
+#pragma unroll
+      for (int q = 0; q < S / 4; ++q) o4[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < S; ++r)
+        if (j0 + r < W) work[i * W + j0 + r] = acc[r];
+    }
+  }
+  __syncthreads();
+
+  // pixel phase (coalesced): likelihood terms and d log L / d M into img's interior
+  float ll = 0.f, c2 = 0.f;
+  for (int i = wid; i < H; i += nw)
+#pragma unroll 2
+  for (int j = lane; j < W; j += 32) {
+    const int p = i * W + j;
+    const float M = two ? stage[i * P + j] : work[p];
+    if (want_sim) {
+      s.sim[size_t(b) * HW + p] = M;
+      continue;
+    }
+    // explicit roundings: the log-L-only and gradient calls give identical sums.
+    // 1/v and log(2 pi v) by the hardware approximations (relative error ~1e-7,
+    // far below the likelihood's FP32 summation error)
+    const float v = fmaf(M, s.inv_gain, s.sigma2[p]);
+    const float res = __fsub_rn(s.image[p], M);
+    const float iv = rcp(v);
+    const float t2 = __fmul_rn(__fmul_rn(res, res), iv);
+    c2 = __fadd_rn(c2, t2);
+    ll = __fadd_rn(ll, __fadd_rn(t2, __fmul_rn(0.69314718055994531f, lg2(__fmul_rn(6.28318530717958648f, v)))));
+    if (want_grad) {
+      // d log L / d M = res/v + (res^2/v^2 - 1/v) / (2 G t_exp)
+      img[(i + c) * P + j + c] = fmaf(0.5f * s.inv_gain, fmaf(t2, iv, -iv), res * iv);
+    }
+  }
+  if (!want_sim) {
+    // FP32 within a thread (a few tens of pixels) and a warp (pairwise), FP64 across warps
+    ll = warp_sum_f(ll);
+    c2 = warp_sum_f(c2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      red2[2 * warp] = double(ll);
+      red2[2 * warp + 1] = double(c2);
+    }
+  }
+  __syncthreads();
+  if (!want_sim && threadIdx.x == 0) {
+    double L = 0.0, C = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+      L += red2[2 * w];
+      C += red2[2 * w + 1];
+    }
+    if (s.loglik) s.loglik[b] = -0.5 * L;
+    if (s.chi2) s.chi2[b] = C;
+  }
+  if (!want_grad) return;
+
+  // pass 2: subpixel adjoint = (PSF correlated with d log L / d M) / k^2
+  const float inv_k2 = 1.0f / float(s.k * s.k);
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int strip = u / H, i = u - strip * H, j0 = strip * S;
+    corr_row<K>(img, P, kerU, i, j0, acc);
+    if (two) {
+      float4* o4 = reinterpret_cast<float4*>(stage + i * P + j0);
+#pragma unroll
+      for (int q = 0; q < S / 4; ++q)
+        o4[q] = make_float4(acc[4 * q] * inv_k2, acc[4 * q + 1] * inv_k2, acc[4 * q + 2] * inv_k2,
+                            acc[4 * q + 3] * inv_k2);
+    } else {
+#pragma unroll
+      for (int r = 0; r < S; ++r)
+        if (j0 + r < W) work[i * W + j0 + r] = acc[r] * inv_k2;
+    }
+  }
+  if (two) {
+    __syncthreads();
+    for (int i = wid; i < H; i += nw)
+      for (int j = lane; j < W; j += 32) work[i * W + j] = stage[i * P + j];
+  }
+}
+
 template <int K, int R, int NT, int MINB, class Src>
 __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src src, int mode) {
   extern __shared__ float4 smem4[];
@@ -686,7 +885,11 @@ __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src s
     const Seg* segp = src.conv_seg(item, b);
     block_copy(&ss, segp);
     __syncthreads();
-    conv_vector<K, R>(ss, b, mode, smem, red2);
+    if constexpr (K > 0) {
+      conv_vector_rows<K>(ss, b, mode, smem, red2);
+    } else {
+      conv_vector<K, R>(ss, b, mode, smem, red2);
+    }
     __syncthreads();
   }
 }
@@ -759,6 +962,10 @@ static constexpr ConvClass kConvClasses[3] = {{11, 16, 128}, {21, 16, 256}, {0, 
 int conv_class(int K) { return K == 11 ? 0 : (K == 21 ? 1 : 2); }
 
 size_t conv_smem_bytes(int H, int W, int K, bool two_buf) {
+  if (kConvClasses[conv_class(K)].K > 0) {   // row-strip layout (conv_vector_rows)
+    const size_t KP = size_t((K + 3) & ~3), P = size_t(rowconv_pitch(W, K));
+    return (2 * size_t(K) * KP + (size_t(H) + K - 1) * P + (two_buf ? size_t(H) * P : 0)) * sizeof(float);
+  }
   const int R = kConvClasses[conv_class(K)].R;
   const int nstrip = (H + R - 1) / R;
   const size_t Hp = size_t(nstrip) * R + K - 1, Wp = size_t(W) + K - 1;
