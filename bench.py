@@ -408,6 +408,44 @@ def run_variant_workload(device, B: int = 4096, steps: int = 10):
     return out
 
 
+def run_pipeline_workload(device):
+    """Sec. 2.6 / Table 1: MAP (300 prior starts x 300) -> VI (1000 x 500) ->
+    HMC (50 chains, 250 + 750, ChEES) on a system drawn from the paper's
+    simulation distribution (80x80, k = 2, 11x11 PSF, sigma_bkg = 0.2,
+    t_exp = 100 s): time per stage and in total (the paper's 105 s on
+    4 A100), the mode's reduced chi^2, and the sampler's ESS and R-hat; once
+    with HMC preconditioned by the VI covariance (the paper) and once by the
+    Laplace covariance at the MAP point."""
+    import torch
+    from paper_2202_07663_gb300 import abi, diagnostics, pipeline
+    spec = inputs.PAPER_SAMPLE_SPEC
+    rng = np.random.default_rng(202)
+    truth = inputs.draw_table(rng, inputs.PAPER_SIM, 1)[0]
+    psf = inputs.make_psf(spec).astype(np.float32)
+    blank = np.zeros((spec.H, spec.W), np.float32)
+    s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
+    s0.close()
+    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    starts = torch.from_numpy(inputs.draw_table(np.random.default_rng(13), inputs.PAPER_PRIOR_DRAW, 300)
+                              .astype(np.float32)).to(device)
+    out = {"workload": "pipeline-80x80-k2-psf11-paper-noise", "map_starts": 300, "paper_seconds_4xA100": 105.0}
+    dof = spec.H * spec.W - 22
+    for pre in ("vi", "laplace"):
+        r = pipeline.model_system(s, starts, preconditioner=pre, seed=1)
+        _, c2 = s.loglik(torch.from_numpy(r.theta_map.astype(np.float32)[None]).to(device), chi2=True)
+        th = r.samples.theta.transpose(0, 1).cpu().numpy().astype(np.float64)
+        ess, rh = diagnostics.ess(th), diagnostics.rhat(th)
+        flat = th.reshape(-1, 22)
+        out[pre] = {"seconds": {k: round(v, 4) for k, v in r.seconds.items()}, "grad_evals": r.grad_evals,
+                    "map_chi2nu": float(c2.item()) / dof, "ess_min": float(ess.min()), "rhat_max": float(rh.max()),
+                    "step_size": r.samples.run.step_size, "trajectory_length": r.samples.run.trajectory_length,
+                    "max_abs_z_truth": float(np.max(np.abs(flat.mean(0) - truth) / flat.std(0)))}
+    s.close()
+    return out
+
+
 def cpu_baseline(spec, psf, image, params, budget_s: float = 12.0):
     """The FP64 oracle (log L + gradient) on a bounded sample of the same workload."""
     import oracle
@@ -587,7 +625,8 @@ def main():
     if world == 1 and not args.no_workloads:
         workloads = {"hmc": run_hmc_workload(device), "stress": run_stress_workload(device),
                      "serving": run_serving_workload(device), "map": run_map_workload(device),
-                     "hmc_paper": run_hmc_paper_workload(device), "variant": run_variant_workload(device)}
+                     "hmc_paper": run_hmc_paper_workload(device), "variant": run_variant_workload(device),
+                     "pipeline": run_pipeline_workload(device)}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
