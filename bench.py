@@ -77,7 +77,7 @@ def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
 
 # DRAM bytes per launch of k_ray_adj from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 prefix of gl_kernels.cu + gl_device.cuh).
-TRAFFIC = {"d2790698df90f9b4": 62.089216e6}   # ncu dram read + write, one launch at B = 4096
+TRAFFIC = {"47aad26ee79304a0": 62.150656e6}   # ncu dram read + write, one launch at B = 4096
 
 
 def kernel_source_hash() -> str:
