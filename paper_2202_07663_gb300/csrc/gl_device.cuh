@@ -44,6 +44,7 @@ constexpr int NMAX = 64;             // cap on EPL series terms per vector
 constexpr int NACC = 24;             // adjoint accumulators per vector
 constexpr float RHO2_MIN = 1e-12f;   // (1e-6 arcsec)^2: EPL deflection zero / Sersic radius floor
 constexpr int RAY_THREADS = 256;     // block size of the ray kernels
+constexpr int FINAL_THREADS = 128;   // block size of k_final (vectors per block)
 
 // Accumulator slots of the adjoint (per vector, before the chain rule).
 enum Acc {

@@ -896,6 +896,35 @@ __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src s
 
 // ------------------------------------------------------------- k_final ----
 
+// The per-vector chain rule from the summed accumulators a[NACC] and the
+// parameters p (both FP64): gradient entry j. Shared by the two k_final
+// variants so that they give identical results.
+// b_n / n of a Sersic index.
+__device__ __forceinline__ double bn_over_n(float n) {
+  const double x = double(n);
+  return (1.9992 * x - 0.3271) / x;
+}
+
+// ms, ml: bn_over_n of the source (pf[16]) and of the lens light (pf[9]).
+__device__ __forceinline__ double chain_rule(int j, const double* a, const float* pf, double ms, double ml) {
+  const double ln2 = 0.69314718055994530942;
+  if (j < 8) return j == 0 ? ms * (double(pf[1]) - 1.0) / double(pf[0]) * a[A_THETAE] : ms * a[A_THETAE + j];
+  const int l = j < 15 ? 0 : 1, k = j - (l == 0 ? 8 : 15);
+  const float* q = pf + (l == 0 ? 8 : 15);
+  const double* c = a + (l == 0 ? A_L_R : A_S_R);
+  const double m = l == 0 ? ml : ms;
+  switch (k) {
+    case 0: return m / double(q[0]) * c[0];
+    case 1: return -1.9992 * c[1] + m * ln2 * c[2];
+    case 2: return -0.5 * m * c[3];
+    case 3: return -0.5 * m * c[4];
+    case 4: return m * c[5];
+    case 5: return m * c[6];
+    default: return c[7];
+  }
+}
+
+// One thread per vector (calls whose vectors have one ray tile each).
 template <class Src>
 __global__ void k_final(const __grid_constant__ Src src) {
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < src.nvec(); item += gridDim.x * blockDim.x) {
@@ -911,31 +940,40 @@ __global__ void k_final(const __grid_constant__ Src src) {
     const double* part = s->partial + size_t(b) * s->ntiles * NACC;
     for (int t = 0; t < s->ntiles; ++t)
       for (int i = 0; i < NACC; ++i) a[i] += part[t * NACC + i];
-    double p[NPARAM];
-    for (int i = 0; i < NPARAM; ++i) p[i] = double(s->params[size_t(b) * NPARAM + i]);
-    const double ln2 = 0.69314718055994530942;
-    const double bs = 1.9992 * p[16] - 0.3271, ms = bs / p[16];   // b_n / n of the source
-    g[0] = ms * (p[1] - 1.0) / p[0] * a[A_THETAE];
-    g[1] = ms * a[A_T];
-    g[2] = ms * a[A_E1];
-    g[3] = ms * a[A_E2];
-    g[4] = ms * a[A_XC];
-    g[5] = ms * a[A_YC];
-    g[6] = ms * a[A_G1];
-    g[7] = ms * a[A_G2];
-    for (int l = 0; l < 2; ++l) {
-      const double* q = p + (l == 0 ? 8 : 15);
-      const double* c = a + (l == 0 ? A_L_R : A_S_R);
-      double* o = g + (l == 0 ? 8 : 15);
-      const double bn = 1.9992 * q[1] - 0.3271, m = bn / q[1];
-      o[0] = m / q[0] * c[0];
-      o[1] = -1.9992 * c[1] + m * ln2 * c[2];
-      o[2] = -0.5 * m * c[3];
-      o[3] = -0.5 * m * c[4];
-      o[4] = m * c[5];
-      o[5] = m * c[6];
-      o[6] = c[7];
+    const float* pf = s->params + size_t(b) * NPARAM;
+    const double ms = bn_over_n(pf[16]), ml = bn_over_n(pf[9]);
+    for (int j = 0; j < NPARAM; ++j) g[j] = chain_rule(j, a, pf, ms, ml);
+  }
+}
+
+// One warp per vector (many tiles per vector, i.e. small batches): lane i <
+// NACC sums accumulator i over the tiles in tile order, lane j < NPARAM
+// applies the chain rule for entry j.
+template <class Src>
+__global__ void k_final_warp(const __grid_constant__ Src src) {
+  __shared__ double sa[FINAL_THREADS / 32][NACC];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int item = blockIdx.x * wpb + w; item < src.nvec(); item += gridDim.x * wpb) {
+    int b;
+    const Seg* s = src.vec_seg(item, b);
+    double* g = s->grad + size_t(b) * NPARAM;
+    if (s->vc[b].nterms < 0) {   // warp-uniform
+      if (lane < NPARAM) g[lane] = nan("");
+      continue;
     }
+    if (lane < NACC) {
+      const double* part = s->partial + size_t(b) * s->ntiles * NACC + lane;
+      double acc = 0.0;
+      for (int t = 0; t < s->ntiles; ++t) acc += part[size_t(t) * NACC];
+      sa[w][lane] = acc;
+    }
+    __syncwarp();
+    const float* pf = s->params + size_t(b) * NPARAM;
+    double fac = 0.0;   // lanes 0, 1 compute the two factors once; the others receive them
+    if (lane < 2) fac = bn_over_n(pf[lane == 0 ? 16 : 9]);
+    const double ms = __shfl_sync(0xffffffffu, fac, 0), ml = __shfl_sync(0xffffffffu, fac, 1);
+    if (lane < NPARAM) g[lane] = chain_rule(lane, sa[w], pf, ms, ml);
+    __syncwarp();
   }
 }
 
@@ -1015,16 +1053,18 @@ static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t
 
 template <class Src>
 static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj_final, cudaStream_t st,
-                            Hooks* hooks, bool persistent) {
+                            Hooks* hooks, bool persistent, bool one_tile = false) {
   const int sms = num_sms();
   cudaError_t e;
   const int vthreads = 128, wpb = vthreads / 32;
   int sgrid = (nvec + wpb - 1) / wpb;
-  int fgrid = (nvec + vthreads - 1) / vthreads;
+  int fgrid = (nvec + FINAL_THREADS - 1) / FINAL_THREADS;
+  int wgrid = (nvec + FINAL_THREADS / 32 - 1) / (FINAL_THREADS / 32);
   int rgrid = nray;
   if (persistent) {
     sgrid = sgrid < sms * 4 ? sgrid : sms * 4;
     fgrid = fgrid < sms ? fgrid : sms;
+    wgrid = wgrid < sms * 4 ? wgrid : sms * 4;
     rgrid = rgrid < sms * 4 ? rgrid : sms * 4;
   }
   if (fwd) {
@@ -1040,7 +1080,10 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
     k_ray_adj<Src><<<rgrid, ADJ_THREADS, 0, st>>>(src);
     if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
     hooks->before(GL_K_FINAL, st);
-    k_final<Src><<<fgrid, vthreads, 0, st>>>(src);
+    if (one_tile)
+      k_final<Src><<<fgrid, FINAL_THREADS, 0, st>>>(src);
+    else
+      k_final_warp<Src><<<wgrid, FINAL_THREADS, 0, st>>>(src);
     return hooks->after(GL_K_FINAL, st);
   }
   return cudaSuccess;
@@ -1057,7 +1100,7 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD) return cudaSuccess;
-  return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false);
+  return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false, s.ntiles == 1);
 }
 
 cudaError_t launch_table(const Seg* d_segs, int nseg, int vec_total, int ray_total, const ConvRun* conv, int nconv,
@@ -1119,7 +1162,7 @@ cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size
   k_ray_adj<DevTable><<<sms * GL_ADJ_MINB, ADJ_THREADS, 0, st>>>(src);
   if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
   hooks->before(GL_K_FINAL, st);
-  k_final<DevTable><<<sms, 128, 0, st>>>(src);
+  k_final_warp<DevTable><<<sms * 4, FINAL_THREADS, 0, st>>>(src);
   return hooks->after(GL_K_FINAL, st);
 }
 
