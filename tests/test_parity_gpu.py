@@ -232,3 +232,22 @@ def test_full_size_configs_sampled(abi, cfg, nsample):
     idx[-1] = B - 1  # include the last vector of the batch
     rl, _, rg = oracle_eval(spec, image, psf, params[idx])
     assert_parity(ll[idx], g[idx], rl, rg, "config %d sample" % cfg, ll_extra=ll_bound(spec, image, psf, params[idx]))
+
+
+def test_final_kernel_variants_agree_bitwise(abi):
+    """B large enough for one ray tile per vector: the single-system call sums
+    the tiles in one thread per vector, the grouped call in a warp per vector;
+    both must give the same bits (and match the oracle on a sample)."""
+    spec = inputs.SystemSpec(16, 16, 1, 3, "gaussian")
+    truth, image, psf = make_system(spec, 300)
+    params = inputs.draw_perturbed(np.random.default_rng(30), truth, 1400).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    p = torch.from_numpy(params).cuda()
+    ll1, g1 = (t.cpu().numpy() for t in s.loglik_grad(p))
+    lls, grads, _ = abi.loglik_grad_grouped([s], [p])
+    s.close()
+    np.testing.assert_array_equal(lls[0].cpu().numpy(), ll1)
+    np.testing.assert_array_equal(grads[0].cpu().numpy(), g1)
+    idx = np.array([0, 701, 1399])
+    rl, _, rg = oracle_eval(spec, image, psf, params[idx])
+    assert_parity(ll1[idx], g1[idx], rl, rg, "one-tile batch", ll_extra=ll_bound(spec, image, psf, params[idx]))
