@@ -77,6 +77,7 @@ def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
 
 # DRAM bytes per launch of k_ray_adj from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 prefix of gl_kernels.cu + gl_device.cuh).
+MUFU_RAY_ADJ = 12   # ex2/lg2/rcp per ray in the adjoint (EPL power, two Sersic profiles)
 TRAFFIC = {"47aad26ee79304a0": 62.150656e6}   # ncu dram read + write, one launch at B = 4096
 
 
@@ -465,8 +466,14 @@ def cpu_baseline(spec, psf, image, params, budget_s: float = 12.0):
     t = time.perf_counter()
     oracle.loglik(params[:n].astype(np.float64), *args, grad=True, nthreads=nt)
     dt = time.perf_counter() - t
+    # the same on one core, on a smaller sample
+    n1 = max(2, min(len(params), int(n * 4.0 / budget_s / max(nt, 1)) + 1))
+    t = time.perf_counter()
+    oracle.loglik(params[:n1].astype(np.float64), *args, grad=True, nthreads=1)
+    dt1 = time.perf_counter() - t
     return {"value": n / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
-            "sample": "%d of the %d vectors (log L + forward-mode gradient, FP64), %.1f s" % (n, len(params), dt)}
+            "sample": "%d of the %d vectors (log L + forward-mode gradient, FP64), %.1f s" % (n, len(params), dt),
+            "value_1core": n1 / dt1, "sample_1core": "%d vectors, %.1f s" % (n1, dt1)}
 
 
 def run_reference(args):
@@ -608,6 +615,10 @@ def main():
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = flop_adj / adj_s / 1e12
+    # special-function unit: 12 MUFU ops per ray in the adjoint; 32 per clock per SM
+    # (own ex2.approx throughput probe on this GPU)
+    mufu_peak = sms * 32 * sm_mhz * 1e6 / 1e9
+    mufu_achieved = rays * B * MUFU_RAY_ADJ / adj_s / 1e9
     th = kernel_source_hash()
     traffic = TRAFFIC.get(th)
     if traffic is not None:
@@ -647,6 +658,9 @@ def main():
                      "flops_per_launch": flop_adj, "launch_ms": adj_s * 1e3,
                      "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 x %.0f MHz (max SM clock, %s peaks file)" % (
                          sms, sm_mhz, peak_src),
+                     "mufu": {"achieved": mufu_achieved, "peak": mufu_peak, "unit": "Gop/s",
+                              "frac": mufu_achieved / mufu_peak, "ops_per_ray": MUFU_RAY_ADJ,
+                              "peak_basis": "%d SMs x 32 MUFU/clk (measured ex2 probe) x %.0f MHz" % (sms, sm_mhz)},
                      "mean_series_terms": float(N.mean())},
         "kernels": kern,
         "cpu_baseline": cpu,
