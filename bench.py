@@ -61,14 +61,22 @@ NMAX = 64
 
 def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
     """Per-vector EPL series length, the rules the setup kernel applies:
-    forward  smallest N >= 0 with f^(N+1)/(1-f) <= tol,
+    forward  smallest N >= 0 with |a_(N+1)| f^(N+1) / (1 - f max(1, c_(N+2))) <= tol,
+             a_n = c_1 ... c_n, c_k = (2k - 2 + t) / (2k + 2 - t), t = gamma - 1,
     adjoint  the same N, at least 1."""
-    f = np.hypot(params[:, 2].astype(np.float64), params[:, 3].astype(np.float64))
-    N = np.arange(0, NMAX + 1)[None, :]
+    p = params.astype(np.float64)
+    f = np.hypot(p[:, 2], p[:, 3])[:, None]
+    t = (p[:, 1] - 1.0)[:, None]
+    k = np.arange(1, NMAX + 2)[None, :]
+    c = (2 * k - 2 + t) / (2 * k + 2 - t)                    # c_1 .. c_(NMAX+1)
     with np.errstate(divide="ignore"):
-        lf = np.where(f > 0, np.log(np.maximum(f, 1e-300)), -1e300)[:, None]
-    l1f = np.log1p(-np.minimum(f, 0.999999))[:, None]
-    good = (N + 1) * lf - l1f <= np.log(SERIES_TOL)
+        la = np.cumsum(np.log(np.abs(c)), axis=1)             # log|a_1| .. log|a_(NMAX+1)|
+        lf = np.where(f > 0, np.log(np.maximum(f, 1e-300)), -1e300)
+    N = np.arange(0, NMAX + 1)[None, :]
+    kk = N + 2
+    cnext = (2 * kk - 2 + t) / (2 * kk + 2 - t)
+    r = np.minimum(f * np.maximum(1.0, cnext), 0.999999)
+    good = la[:, :NMAX + 1] + (N + 1) * lf - np.log1p(-r) <= np.log(SERIES_TOL)
     first = np.where(good.any(axis=1), good.argmax(axis=1), NMAX)
     if adjoint:
         first = np.maximum(first, 1)

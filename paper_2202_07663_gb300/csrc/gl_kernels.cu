@@ -144,10 +144,13 @@ __device__ void setup_light(const float* p, LightC& L, bool& ok) {
   L.C2 = 4.f * e2 * (1.f + e1) * iD2;
 }
 
-// Truncation target of the EPL series: the smallest N with
-// |F - F_N| <= f^(N+1)/(1-f) <= SERIES_TOL. The adjoint uses the same N (at
-// least 1): its dF/du comes from F and h_1 in closed form, and the tail of
-// dF/dt exceeds that of F only by a logarithmic factor.
+// Truncation target of the EPL series F = sum a_n u^n, |u| = f, a_n = c_1 ... c_n:
+// the smallest N with |a_{N+1}| f^(N+1) / (1 - f max(1, c_{N+2})) <= SERIES_TOL,
+// a bound on |F - F_N| (|c_k| decreases toward 1 for k >= 2, so the tail after
+// a_{N+1} is at most a geometric series of ratio f max(1, c_{N+2})). The
+// adjoint uses the same N (at least 1): its dF/du comes from F and h_1 in
+// closed form, and the tail of dF/dt exceeds that of F only by a logarithmic
+// factor.
 constexpr double SERIES_TOL = 2e-8;
 
 // One warp per vector: lanes 0..21 check one parameter each, lane 0 derives
@@ -193,14 +196,28 @@ __global__ void k_setup(const __grid_constant__ Src src) {
       V->light[lane - 1] = L;
     }
     ok = __all_sync(0xffffffffu, ok);
-    // term count: lane tests N = lane and N = lane + 32
+    // term count: lane tests N = lane and N = lane + 32, with log|a_{N+1}| from
+    // a warp prefix sum of log|c_k| (k = lane + 1 and lane + 33)
     const float f = sqrtf(e2s);
     const float lf = f > 0.f ? logf(f) : -1e30f;
-    const float l1f = log1pf(-fminf(f, 0.999999f));
     const float ltol = logf(float(SERIES_TOL));
-    auto fwd_ok = [&](int N) { return (N + 1) * lf - l1f <= ltol; };
-    const unsigned f_lo = __ballot_sync(0xffffffffu, fwd_ok(lane));
-    const unsigned f_hi = __ballot_sync(0xffffffffu, fwd_ok(lane + 32));
+    auto coef = [&](int k) { return (2.f * k - 2.f + t) / (2.f * k + 2.f - t); };
+    float la_lo = logf(fabsf(coef(lane + 1))), la_hi = logf(fabsf(coef(lane + 33)));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float ylo = __shfl_up_sync(0xffffffffu, la_lo, o), yhi = __shfl_up_sync(0xffffffffu, la_hi, o);
+      if (lane >= o) {
+        la_lo += ylo;
+        la_hi += yhi;
+      }
+    }
+    la_hi += __shfl_sync(0xffffffffu, la_lo, 31);
+    auto fwd_ok = [&](int N, float la) {
+      const float r = fminf(f * fmaxf(1.f, coef(N + 2)), 0.999999f);
+      return la + (N + 1) * lf - log1pf(-r) <= ltol;
+    };
+    const unsigned f_lo = __ballot_sync(0xffffffffu, fwd_ok(lane, la_lo));
+    const unsigned f_hi = __ballot_sync(0xffffffffu, fwd_ok(lane + 32, la_hi));
     const int n_fwd = f_lo ? __ffs(f_lo) - 1 : (f_hi ? 32 + __ffs(f_hi) - 1 : NMAX);
     for (int n = lane + 1; n <= NMAX; n += 32) {
       const float den = 2.f * n + 2.f - t;
