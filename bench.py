@@ -42,13 +42,13 @@ UNIT = "evals/s"
 WORKLOAD = "multistart-60x60-k2-psf11-B4096"
 
 # FP32 flop counts per ray of the two ray kernels (FMA = 2), N = EPL series
-# terms of the vector; per pixel of the convolution kernel (see DESIGN.md).
+# terms of the vector; per pixel of the convolution kernel.
 def flops_ray_fwd(N):
-    return 83 + 9 * N
+    return 90 + 7 * N
 
 
 def flops_ray_adj(N):
-    return 318 + 21 * N
+    return 331 + 14 * N
 
 
 def flops_conv_pixel(K, grad):

@@ -17,6 +17,7 @@
 //   u   = -conj(eps) w / conj(w)          (= -f e^{2 i phi_ell}, Tessore & Metcalf)
 //   F(u) = sum_n a_n u^n,  a_0 = 1,  a_n = a_{n-1} c_n,
 //          c_n = (2n - 2 + t) / (2n + 2 - t),  t = gamma - 1
+//        = 1 + u G(u),  G(u) = sum_{n>=0} a_{n+1} u^n
 //   alpha = (thetaE / rho)^t  w  F(u)     (image frame, complex)
 //
 // This is the Tessore & Metcalf (2015) deflection that the paper cites,
@@ -24,9 +25,9 @@
 //   2b/(1+q) (b/R)^(t-1) e^{i phi} e^{i phi_ell} = (thetaE/rho)^t w
 // (b = thetaE sqrt(q), R = sqrt(q) rho) have been applied. It is smooth in
 // (e1, e2) through e = 0, needs no atan2 and no rotation, and gives the
-// gradient with respect to e1, e2 in closed form. F is evaluated by Horner's
-// rule with a per-vector term count N, so all rays of a vector run the same
-// loop.
+// gradient with respect to e1, e2 in closed form. G is evaluated by Horner's
+// rule on the coefficients a_1..a_N (per-vector term count N, so all rays of
+// a vector run the same loop): one complex multiply-add per term.
 //
 // The Sersic profile (Eq. Sersic) uses the same quadratic form for its
 // elliptical radius: q x_l^2 + y_l^2 / q = A dx^2 + 2 B dx dy + C dy^2 with
@@ -74,14 +75,14 @@ struct __align__(16) VecConst {
   int nterms;              // series terms of F (0 <= N <= NMAX); < 0 marks an invalid vector
   int nterms_adj;          // series terms in the adjoint, max(N, 1)
   float th;                // t / 2
-  float kc;                // (1 - t/2) c_1, for dF/du = [(t/2) F - (1 - t/2) c_1 h_1] / (1 - u)
+  float kc;                // 1 - t/2, for dF/du = [(t/2) F - (1 - t/2) G] / (1 - u)
   float kap_c;             // (2 - t) / 2: kappa = kap_c (thetaE/rho)^t
   float omt;               // 1 - t
   float e1i, e2i;          // e1, e2 times 1 / (1 - |eps|^2)
   float pad_[3];
   LightC light[2];         // [0] lens light at theta, [1] source at beta
-  float cn[NMAX];          // c_n, n = 1..N at index n-1
-  float cnt[NMAX];         // d c_n / d t
+  float an[NMAX];          // a_n = c_1 ... c_n, n = 1..NMAX at index n-1
+  float ant[NMAX];         // d a_n / d t
 };
 static_assert(sizeof(VecConst) % 16 == 0, "VecConst must be a whole number of 16-byte words");
 
@@ -190,7 +191,7 @@ __device__ __forceinline__ T sersic_fwd_T(const LightC& L, T px, T py) {
 // EPL deflection, generic in the ray type. A ray inside rho < 1e-6 arcsec gets
 // zero deflection (mask), computed without a branch so pairs stay in lockstep.
 template <class T>
-__device__ __forceinline__ void epl_fwd_T(const VecConst& V, const float* cn, T x, T y, T& ax, T& ay) {
+__device__ __forceinline__ void epl_fwd_T(const VecConst& V, const float* an, T x, T y, T& ax, T& ay) {
   const T dx = x - sp<T>(V.xc), dy = y - sp<T>(V.yc);
   const T wr = fmaT(sp<T>(V.om1), dx, sp<T>(-V.e2) * dy);
   const T wi = fmaT(sp<T>(V.op1), dy, sp<T>(-V.e2) * dx);
@@ -206,77 +207,27 @@ __device__ __forceinline__ void epl_fwd_T(const VecConst& V, const float* cn, T 
   const T ur = fmaT(sp<T>(-V.e1), vr, sp<T>(-V.e2) * vi);
   const T ui = fmaT(sp<T>(V.e2), vr, sp<T>(-V.e1) * vi);
   const T nui = fmaT(sp<T>(-V.e2), vr, sp<T>(V.e1) * vi);   // -ui: packed FMAs take no negated operands
-  T hr = sp<T>(1.f), hi = sp<T>(0.f);
+  // G = sum_{n<N} a_{n+1} u^n by Horner (g = a_n + u g), then F = 1 + u G
+  T gr = sp<T>(0.f), gi = sp<T>(0.f);
 #pragma unroll 2
   for (int n = V.nterms; n >= 1; --n) {
-    const T c = sp<T>(cn[n - 1]);
-    const T tr = fmaT(ur, hr, nui * hi);
-    const T ti = fmaT(ur, hi, ui * hr);
-    hr = fmaT(c, tr, sp<T>(1.f));
-    hi = c * ti;
+    const T ngr = fmaT(ur, gr, fmaT(nui, gi, sp<T>(an[n - 1])));
+    gi = fmaT(ur, gi, ui * gr);
+    gr = ngr;
   }
+  const T hr = fmaT(ur, gr, fmaT(nui, gi, sp<T>(1.f)));
+  const T hi = fmaT(ur, gi, ui * gr);
   ax = S * fmaT(wr, hr, nwi * hi);
   ay = S * fmaT(wr, hi, wi * hr);
 }
 
 template <class T>
-__device__ __forceinline__ T ray_intensity_T(const VecConst& V, const float* cn, T x, T y) {
+__device__ __forceinline__ T ray_intensity_T(const VecConst& V, const float* an, T x, T y) {
   T ax, ay;
-  epl_fwd_T(V, cn, x, y, ax, ay);
+  epl_fwd_T(V, an, x, y, ax, ay);
   const T bx = x - ax - fmaT(sp<T>(V.g1), x, sp<T>(V.g2) * y);
   const T by = y - ay - fmaT(sp<T>(V.g2), x, sp<T>(-V.g1) * y);
   return sersic_fwd_T(V.light[1], bx, by) + sersic_fwd_T(V.light[0], x, y);
-}
-
-// ------------------------------------------------------------ forward -----
-
-// Elliptical Sersic at (px, py).
-__device__ __forceinline__ float sersic_fwd(const LightC& L, float px, float py) {
-  const float dx = px - L.x, dy = py - L.y;
-  float r2 = fmaf(L.A * dx, dx, fmaf(L.B2 * dx, dy, L.C * dy * dy));
-  r2 = fmaxf(r2, RHO2_MIN);
-  const float s = ex2(fmaf(L.c1, lg2(r2), L.c0));
-  return L.I0 * ex2(fmaf(-L.k1, s, L.k1));
-}
-
-// EPL deflection (complex, image frame) at (x, y); cn in shared memory.
-__device__ __forceinline__ void epl_fwd(const VecConst& V, const float* cn, float x, float y,
-                                        float& ax, float& ay) {
-  const float dx = x - V.xc, dy = y - V.yc;
-  const float wr = fmaf(V.om1, dx, -V.e2 * dy);
-  const float wi = fmaf(V.op1, dy, -V.e2 * dx);
-  const float w2 = fmaf(wr, wr, wi * wi);
-  const float r2 = w2 * V.inv_1me2;
-  if (r2 < RHO2_MIN) {
-    ax = 0.f;
-    ay = 0.f;
-    return;
-  }
-  const float S = ex2(V.t * fmaf(-0.5f, lg2(r2), V.log2_thetaE));
-  const float iw2 = rcp(w2);
-  const float vr = (wr * wr - wi * wi) * iw2;
-  const float vi = 2.f * wr * wi * iw2;
-  const float ur = -fmaf(V.e1, vr, V.e2 * vi);
-  const float ui = fmaf(V.e2, vr, -V.e1 * vi);
-  float hr = 1.f, hi = 0.f;
-  for (int n = V.nterms; n >= 1; --n) {
-    const float c = cn[n - 1];
-    const float tr = fmaf(ur, hr, -ui * hi);
-    const float ti = fmaf(ur, hi, ui * hr);
-    hr = fmaf(c, tr, 1.f);
-    hi = c * ti;
-  }
-  ax = S * fmaf(wr, hr, -wi * hi);
-  ay = S * fmaf(wr, hi, wi * hr);
-}
-
-// Surface brightness of one ray (lensed source + lens light).
-__device__ __forceinline__ float ray_intensity(const VecConst& V, const float* cn, float x, float y) {
-  float ax, ay;
-  epl_fwd(V, cn, x, y, ax, ay);
-  const float bx = x - ax - fmaf(V.g1, x, V.g2 * y);
-  const float by = y - ay - fmaf(V.g2, x, -V.g1 * y);
-  return sersic_fwd(V.light[1], bx, by) + sersic_fwd(V.light[0], x, y);
 }
 
 }  // namespace gl

@@ -185,7 +185,7 @@ __global__ void k_setup(const __grid_constant__ Src src) {
       V->g1 = pp[6];
       V->g2 = pp[7];
       V->th = 0.5f * t;
-      V->kc = (1.f - 0.5f * t) * t / (4.f - t);
+      V->kc = 1.f - 0.5f * t;
       V->kap_c = 0.5f * (2.f - t);
       V->omt = 1.f - t;
       V->e1i = e1 * i1me2;
@@ -219,12 +219,30 @@ __global__ void k_setup(const __grid_constant__ Src src) {
     const unsigned f_lo = __ballot_sync(0xffffffffu, fwd_ok(lane, la_lo));
     const unsigned f_hi = __ballot_sync(0xffffffffu, fwd_ok(lane + 32, la_hi));
     const int n_fwd = f_lo ? __ffs(f_lo) - 1 : (f_hi ? 32 + __ffs(f_hi) - 1 : NMAX);
-    for (int n = lane + 1; n <= NMAX; n += 32) {
-      const float den = 2.f * n + 2.f - t;
-      const float iden = 1.0f / den;
-      V->cn[n - 1] = (2.f * n - 2.f + t) * iden;
-      V->cnt[n - 1] = 4.f * n * iden * iden;
+    // a_n = c_1 ... c_n and d a_n / d t by a warp scan of the pairs (c_k, d c_k / d t)
+    // under (x1, y1) (x2, y2) = (x1 x2, x1 y2 + x2 y1) (the product rule), k = lane + 1
+    // and lane + 33; d c_k / d t = 4k / (2k + 2 - t)^2
+    auto dcoef = [&](int k) {
+      const float iden = 1.0f / (2.f * k + 2.f - t);
+      return 4.f * k * iden * iden;
+    };
+    float xl = coef(lane + 1), yl = dcoef(lane + 1), xh = coef(lane + 33), yh = dcoef(lane + 33);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float pxl = __shfl_up_sync(0xffffffffu, xl, o), pyl = __shfl_up_sync(0xffffffffu, yl, o);
+      const float pxh = __shfl_up_sync(0xffffffffu, xh, o), pyh = __shfl_up_sync(0xffffffffu, yh, o);
+      if (lane >= o) {
+        yl = fmaf(pxl, yl, xl * pyl);
+        xl = pxl * xl;
+        yh = fmaf(pxh, yh, xh * pyh);
+        xh = pxh * xh;
+      }
     }
+    const float tx = __shfl_sync(0xffffffffu, xl, 31), ty = __shfl_sync(0xffffffffu, yl, 31);
+    V->an[lane] = xl;
+    V->ant[lane] = yl;
+    V->an[lane + 32] = tx * xh;
+    V->ant[lane + 32] = fmaf(tx, yh, xh * ty);
     if (lane == 0) {
       V->nterms = ok ? min(n_fwd, NMAX) : -1;
       V->nterms_adj = max(min(n_fwd, NMAX), 1);
@@ -274,7 +292,7 @@ __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd(const __gr
           const F2 y = {make_float2(fmaf(float(ip * k + a), ss.sub, ss.y0), fmaf(float(iq * k + a), ss.sub, ss.y0))};
           for (int c = 0; c < k; ++c) {
             const F2 x = {make_float2(fmaf(float(jp * k + c), ss.sub, ss.x0), fmaf(float(jq * k + c), ss.sub, ss.x0))};
-            acc = acc + ray_intensity_T(sv, sv.cn, x, y);
+            acc = acc + ray_intensity_T(sv, sv.an, x, y);
           }
         }
         acc = acc * sp<F2>(inv_k2);
@@ -326,7 +344,7 @@ __device__ __forceinline__ void light_adj(const LightC& L, T px, T py, T g, T* a
 // 24 accumulators. Branch-free: a ray inside rho < 1e-6 arcsec has S = 0,
 // which zeroes its deflection and every EPL derivative (all carry S).
 template <class T>
-__device__ __forceinline__ void ray_adj(const VecConst& V, const float* cn, const float* cnt, T x, T y, T g, T* acc) {
+__device__ __forceinline__ void ray_adj(const VecConst& V, const float* an, const float* ant, T x, T y, T g, T* acc) {
   T Gx, Gy;
   light_adj(V.light[0], x, y, g, acc + A_L_R, Gx, Gy);
 
@@ -347,30 +365,22 @@ __device__ __forceinline__ void ray_adj(const VecConst& V, const float* cn, cons
   const T ur = fmaT(sp<T>(-V.e1), vr, sp<T>(-V.e2) * vi);
   const T ui = fmaT(sp<T>(V.e2), vr, sp<T>(-V.e1) * vi);
   const T nui = fmaT(sp<T>(-V.e2), vr, sp<T>(V.e1) * vi);   // -ui: packed FMAs take no negated operands
-  // Horner for F and dF/dt down to h_1, then the last step (n = 1)
-  T hr = sp<T>(1.f), hi = sp<T>(0.f), tr = sp<T>(0.f), ti = sp<T>(0.f);
+  // G = sum_{n<N} a_{n+1} u^n and dG/dt by Horner; F = 1 + u G, dF/dt = u dG/dt
+  T Gr = sp<T>(0.f), Gi = sp<T>(0.f), Gtr = sp<T>(0.f), Gti = sp<T>(0.f);
 #pragma unroll 2
-  for (int n = V.nterms_adj; n >= 2; --n) {
-    const T c = sp<T>(cn[n - 1]), ct = sp<T>(cnt[n - 1]);
-    const T uhr = fmaT(ur, hr, nui * hi), uhi = fmaT(ur, hi, ui * hr);
-    const T utr = fmaT(ur, tr, nui * ti), uti = fmaT(ur, ti, ui * tr);
-    tr = fmaT(ct, uhr, c * utr);
-    ti = fmaT(ct, uhi, c * uti);
-    hr = fmaT(c, uhr, sp<T>(1.f));
-    hi = c * uhi;
+  for (int n = V.nterms_adj; n >= 1; --n) {
+    const T nGr = fmaT(ur, Gr, fmaT(nui, Gi, sp<T>(an[n - 1])));
+    Gi = fmaT(ur, Gi, ui * Gr);
+    Gr = nGr;
+    const T nGtr = fmaT(ur, Gtr, fmaT(nui, Gti, sp<T>(ant[n - 1])));
+    Gti = fmaT(ur, Gti, ui * Gtr);
+    Gtr = nGtr;
   }
-  const T h1r = hr, h1i = hi;
-  {
-    const T c = sp<T>(cn[0]), ct = sp<T>(cnt[0]);
-    const T uhr = fmaT(ur, hr, nui * hi), uhi = fmaT(ur, hi, ui * hr);
-    const T utr = fmaT(ur, tr, nui * ti), uti = fmaT(ur, ti, ui * tr);
-    tr = fmaT(ct, uhr, c * utr);
-    ti = fmaT(ct, uhi, c * uti);
-    hr = fmaT(c, uhr, sp<T>(1.f));
-    hi = c * uhi;
-  }
-  // dF/du = [(t/2) F - (1 - t/2) c_1 h_1] / (1 - u)   (Gauss contiguous relation)
-  const T nr = fmaT(sp<T>(V.th), hr, sp<T>(-V.kc) * h1r), ni = fmaT(sp<T>(V.th), hi, sp<T>(-V.kc) * h1i);
+  const T hr = fmaT(ur, Gr, fmaT(nui, Gi, sp<T>(1.f))), hi = fmaT(ur, Gi, ui * Gr);     // F
+  const T tr = fmaT(ur, Gtr, nui * Gti), ti = fmaT(ur, Gti, ui * Gtr);                 // dF/dt
+  // dF/du = [(t/2) F - (1 - t/2) G] / (1 - u)   (Gauss contiguous relation; G = (F - 1)/u
+  // without the cancellation)
+  const T nr = fmaT(sp<T>(V.th), hr, sp<T>(-V.kc) * Gr), ni = fmaT(sp<T>(V.th), hi, sp<T>(-V.kc) * Gi);
   const T dr = sp<T>(1.f) - ur;                 // 1 - u = (dr, -ui) = (dr, nui)
   const T idd = rcpT(fmaT(dr, dr, ui * ui));
   const T pr = fmaT(nr, dr, ni * nui) * idd, pi = fmaT(ni, dr, nr * ui) * idd;
@@ -477,7 +487,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, GL_ADJ_MINB) k_ray_adj(const __gr
             const F2 y = {make_float2(fmaf(float(ip * k + a), ss.sub, ss.y0), fmaf(float(iq * k + a), ss.sub, ss.y0))};
             for (int c = 0; c < k; ++c) {
               const F2 x = {make_float2(fmaf(float(jp * k + c), ss.sub, ss.x0), fmaf(float(jq * k + c), ss.sub, ss.x0))};
-              ray_adj(sv, sv.cn, sv.cnt, x, y, g, acc);
+              ray_adj(sv, sv.an, sv.ant, x, y, g, acc);
             }
           }
         }
@@ -491,7 +501,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, GL_ADJ_MINB) k_ray_adj(const __gr
             const float y = fmaf(float(i * k + a), ss.sub, ss.y0);
             for (int c = 0; c < k; ++c) {
               const float x = fmaf(float(j * k + c), ss.sub, ss.x0);
-              ray_adj(sv, sv.cn, sv.cnt, x, y, g, acc);
+              ray_adj(sv, sv.an, sv.ant, x, y, g, acc);
             }
           }
         }
