@@ -856,19 +856,19 @@ __device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, dou
     }
   }
   if (!want_sim) {
-    // FP32 within a thread (a few tens of pixels) and a warp (pairwise), FP64 across warps
+    // FP32 within a thread (a few tens of pixels) and a warp (pairwise), FP64 across
+    // warps: the block size sets the summation order (the last bits of log L)
     ll = warp_sum_f(ll);
     c2 = warp_sum_f(c2);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-      red2[2 * warp] = double(ll);
-      red2[2 * warp + 1] = double(c2);
+      red2[2 * wid] = double(ll);
+      red2[2 * wid + 1] = double(c2);
     }
   }
   __syncthreads();
   if (!want_sim && threadIdx.x == 0) {
     double L = 0.0, C = 0.0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+    for (int w = 0; w < nw; ++w) {
       L += red2[2 * w];
       C += red2[2 * w + 1];
     }
@@ -1068,12 +1068,20 @@ static cudaError_t launch_conv(const Src& src, int nitems, size_t smem, int mode
   return cudaSuccess;
 }
 
+// wide: 512-thread blocks for calls with fewer vectors than SMs (one vector's
+// work spread over 16 warps). Every pixel's model value and d log L / d M is
+// computed by one thread whatever the width, so gradients are the same bits;
+// log L and chi^2 are summed in a width-dependent order (last FP32 bits).
 template <class Src>
 static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t smem, int mode, cudaStream_t st,
-                                     bool persistent) {
+                                     bool persistent, bool wide = false) {
   switch (cls) {
-    case 0: return launch_conv<11, 16, 128, 5>(src, nitems, smem, mode, st, persistent);
-    case 1: return launch_conv<21, 16, 256, 1>(src, nitems, smem, mode, st, persistent);
+    case 0:
+      return wide ? launch_conv<11, 16, 512, 1>(src, nitems, smem, mode, st, persistent)
+                  : launch_conv<11, 16, 128, 5>(src, nitems, smem, mode, st, persistent);
+    case 1:
+      return wide ? launch_conv<21, 16, 512, 1>(src, nitems, smem, mode, st, persistent)
+                  : launch_conv<21, 16, 256, 1>(src, nitems, smem, mode, st, persistent);
     default: return launch_conv<0, 8, 128, 4>(src, nitems, smem, mode, st, persistent);
   }
 }
@@ -1123,7 +1131,7 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_CONV, st);
   e = launch_conv_class(conv_class(s.K), src, s.B, conv_smem_bytes(s.H, s.W, s.K, s.conv_two_buf != 0), mode, st,
-                        false);
+                        false, s.B < num_sms());
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD) return cudaSuccess;

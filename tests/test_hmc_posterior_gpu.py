@@ -9,8 +9,9 @@
   ChEES-adapted HMC on a standard normal (trajectory length, moments);
 - leapfrog steps replayed as CUDA graphs give the eager path's chains bit
   for bit (same kernels, same order, step size read from device memory);
-- the paper's pipeline on a small lens system: Laplace covariance at the
-  truth as the preconditioner, chains drawn from it, adapted HMC; R-hat,
+- the paper's sampler on a small lens system: Laplace covariance at the
+  truth as the preconditioner, chains drawn from it, HMC with dual-averaged
+  step size and ChEES trajectory length; R-hat,
   ESS, the truth's coverage and the spread against the Laplace scale.
 """
 import math
@@ -134,9 +135,10 @@ def test_posterior_hmc_on_a_lens_system(mods):
     B, d = 32, 22
     g = torch.Generator(device="cuda").manual_seed(4)
     x0 = torch.randn(B, d, dtype=torch.float64, device="cuda", generator=g)
-    sampler = hmc.HMC(x0, torch.ones(d, dtype=torch.float64, device="cuda"), 0.3, 5, target=target, seed=6)
+    sampler = hmc.HMC(x0, torch.ones(d, dtype=torch.float64, device="cuda"), 0.3, 5, target=target, seed=6,
+                      graphs=True)
     assert torch.isfinite(sampler.logp).all()
-    run = sampler.run_adaptive(n_burn=100, n_samples=200)
+    run = sampler.run_adaptive(n_burn=150, n_samples=200, adapt_trajectory=True, max_leapfrog=64)
     s.close()
     assert torch.isfinite(sampler.logp).all()
     assert 0.55 < run.accept_samples < 0.92, run

@@ -204,12 +204,15 @@ def test_grouped_launch_equals_single_calls(abi):
         params.append(p)
         singles.append([t.cpu().numpy() for t in s.loglik_grad(p)])
     lls, grads, _ = abi.loglik_grad_grouped(systems, params)
+    # gradients are the same bits; a single call this small runs the
+    # convolution in wider blocks, which sums log L in another order
     for (sl, sg), ll, g in zip(singles, lls, grads):
-        np.testing.assert_array_equal(ll.cpu().numpy(), sl)
+        np.testing.assert_allclose(ll.cpu().numpy(), sl, rtol=1e-6, atol=0)
         np.testing.assert_array_equal(g.cpu().numpy(), sg)
     lls2, grads2, _ = abi.loglik_grad_grouped(systems, params, grad=False)
-    for (sl, _), ll in zip(singles, lls2):
-        np.testing.assert_array_equal(ll.cpu().numpy(), sl)
+    for (sl, _), ll, l1 in zip(singles, lls2, lls):
+        np.testing.assert_allclose(ll.cpu().numpy(), sl, rtol=1e-6, atol=0)
+        np.testing.assert_array_equal(ll.cpu().numpy(), l1.cpu().numpy())
     for s in systems:
         s.close()
 
