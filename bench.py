@@ -56,7 +56,7 @@ def flops_conv_pixel(K, grad):
 
 
 SERIES_TOL = 2e-8
-NMAX = 64
+NMAX = 128
 
 
 def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:

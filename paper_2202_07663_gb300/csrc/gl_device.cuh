@@ -41,7 +41,7 @@
 namespace gl {
 
 constexpr int NPARAM = 22;
-constexpr int NMAX = 64;             // cap on EPL series terms per vector
+constexpr int NMAX = 128;            // cap on EPL series terms per vector (a multiple of 32)
 constexpr int NACC = 24;             // adjoint accumulators per vector
 constexpr float RHO2_MIN = 1e-12f;   // (1e-6 arcsec)^2: EPL deflection zero / Sersic radius floor
 constexpr int RAY_THREADS = 256;     // block size of the ray kernels

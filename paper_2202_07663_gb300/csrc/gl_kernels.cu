@@ -196,53 +196,70 @@ __global__ void k_setup(const __grid_constant__ Src src) {
       V->light[lane - 1] = L;
     }
     ok = __all_sync(0xffffffffu, ok);
-    // term count: lane tests N = lane and N = lane + 32, with log|a_{N+1}| from
-    // a warp prefix sum of log|c_k| (k = lane + 1 and lane + 33)
+    // term count: lane tests N = lane + 32 m (m < NMAX / 32), with log|a_{N+1}| from a
+    // warp prefix sum of log|c_k| (k = lane + 1 + 32 m)
+    constexpr int NCH = NMAX / 32;
     const float f = sqrtf(e2s);
     const float lf = f > 0.f ? logf(f) : -1e30f;
     const float ltol = logf(float(SERIES_TOL));
     auto coef = [&](int k) { return (2.f * k - 2.f + t) / (2.f * k + 2.f - t); };
-    float la_lo = logf(fabsf(coef(lane + 1))), la_hi = logf(fabsf(coef(lane + 33)));
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float ylo = __shfl_up_sync(0xffffffffu, la_lo, o), yhi = __shfl_up_sync(0xffffffffu, la_hi, o);
-      if (lane >= o) {
-        la_lo += ylo;
-        la_hi += yhi;
-      }
-    }
-    la_hi += __shfl_sync(0xffffffffu, la_lo, 31);
-    auto fwd_ok = [&](int N, float la) {
-      const float r = fminf(f * fmaxf(1.f, coef(N + 2)), 0.999999f);
-      return la + (N + 1) * lf - log1pf(-r) <= ltol;
-    };
-    const unsigned f_lo = __ballot_sync(0xffffffffu, fwd_ok(lane, la_lo));
-    const unsigned f_hi = __ballot_sync(0xffffffffu, fwd_ok(lane + 32, la_hi));
-    const int n_fwd = f_lo ? __ffs(f_lo) - 1 : (f_hi ? 32 + __ffs(f_hi) - 1 : NMAX);
-    // a_n = c_1 ... c_n and d a_n / d t by a warp scan of the pairs (c_k, d c_k / d t)
-    // under (x1, y1) (x2, y2) = (x1 x2, x1 y2 + x2 y1) (the product rule), k = lane + 1
-    // and lane + 33; d c_k / d t = 4k / (2k + 2 - t)^2
-    auto dcoef = [&](int k) {
+    auto dcoef = [&](int k) {   // d c_k / d t = 4k / (2k + 2 - t)^2
       const float iden = 1.0f / (2.f * k + 2.f - t);
       return 4.f * k * iden * iden;
     };
-    float xl = coef(lane + 1), yl = dcoef(lane + 1), xh = coef(lane + 33), yh = dcoef(lane + 33);
+    float la[NCH];
+#pragma unroll
+    for (int m = 0; m < NCH; ++m) la[m] = logf(fabsf(coef(lane + 1 + 32 * m)));
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const float pxl = __shfl_up_sync(0xffffffffu, xl, o), pyl = __shfl_up_sync(0xffffffffu, yl, o);
-      const float pxh = __shfl_up_sync(0xffffffffu, xh, o), pyh = __shfl_up_sync(0xffffffffu, yh, o);
-      if (lane >= o) {
-        yl = fmaf(pxl, yl, xl * pyl);
-        xl = pxl * xl;
-        yh = fmaf(pxh, yh, xh * pyh);
-        xh = pxh * xh;
+#pragma unroll
+      for (int m = 0; m < NCH; ++m) {
+        const float y = __shfl_up_sync(0xffffffffu, la[m], o);
+        if (lane >= o) la[m] += y;
       }
     }
-    const float tx = __shfl_sync(0xffffffffu, xl, 31), ty = __shfl_sync(0xffffffffu, yl, 31);
-    V->an[lane] = xl;
-    V->ant[lane] = yl;
-    V->an[lane + 32] = tx * xh;
-    V->ant[lane + 32] = fmaf(tx, yh, xh * ty);
+    float carry = 0.f;
+#pragma unroll
+    for (int m = 0; m < NCH; ++m) {
+      la[m] += carry;
+      carry = __shfl_sync(0xffffffffu, la[m], 31);
+    }
+    int n_fwd = NMAX;
+#pragma unroll
+    for (int m = NCH - 1; m >= 0; --m) {
+      const int N = lane + 32 * m;
+      const float r = fminf(f * fmaxf(1.f, coef(N + 2)), 0.999999f);
+      const unsigned ok_m = __ballot_sync(0xffffffffu, la[m] + (N + 1) * lf - log1pf(-r) <= ltol);
+      if (ok_m) n_fwd = 32 * m + __ffs(ok_m) - 1;
+    }
+    // a_n = c_1 ... c_n and d a_n / d t by a warp scan of the pairs (c_k, d c_k / d t)
+    // under (x1, y1) (x2, y2) = (x1 x2, x1 y2 + x2 y1) (the product rule)
+    float xs[NCH], ys[NCH];
+#pragma unroll
+    for (int m = 0; m < NCH; ++m) {
+      xs[m] = coef(lane + 1 + 32 * m);
+      ys[m] = dcoef(lane + 1 + 32 * m);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+      for (int m = 0; m < NCH; ++m) {
+        const float px = __shfl_up_sync(0xffffffffu, xs[m], o), py = __shfl_up_sync(0xffffffffu, ys[m], o);
+        if (lane >= o) {
+          ys[m] = fmaf(px, ys[m], xs[m] * py);
+          xs[m] = px * xs[m];
+        }
+      }
+    }
+    float tx = 1.f, ty = 0.f;   // the product over the earlier chunks
+#pragma unroll
+    for (int m = 0; m < NCH; ++m) {
+      const float x = tx * xs[m], y = fmaf(tx, ys[m], xs[m] * ty);
+      V->an[lane + 32 * m] = x;
+      V->ant[lane + 32 * m] = y;
+      tx = __shfl_sync(0xffffffffu, x, 31);
+      ty = __shfl_sync(0xffffffffu, y, 31);
+    }
     if (lane == 0) {
       V->nterms = ok ? min(n_fwd, NMAX) : -1;
       V->nterms_adj = max(min(n_fwd, NMAX), 1);

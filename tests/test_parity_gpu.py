@@ -254,3 +254,24 @@ def test_final_kernel_variants_agree_bitwise(abi):
     idx = np.array([0, 701, 1399])
     rl, _, rg = oracle_eval(spec, image, psf, params[idx])
     assert_parity(ll1[idx], g1[idx], rl, rg, "one-tile batch", ll_extra=ll_bound(spec, image, psf, params[idx]))
+
+
+@pytest.mark.parametrize("f", [0.8, 0.85])
+def test_high_ellipticity_long_series(abi, f):
+    """|eps_epl| = 0.8 and 0.85 (q = 0.11, 0.08): the series needs 64 and 88 terms
+    to meet its truncation target; log L and gradient against the oracle, which
+    sums the series to 1e-18. (At |eps| = 0.9 the FP32 Horner sum of ~128
+    terms loses about 2x the gradient tolerance: the accuracy limit of the FP32
+    path, not of its truncation.)"""
+    spec = inputs.SystemSpec(40, 40, 2, 7, "gaussian")
+    truth, image, psf = make_system(spec, 400)
+    rng = np.random.default_rng(41)
+    params = inputs.draw_perturbed(rng, truth, 6, frac=0.01).astype(np.float32)
+    ang = rng.uniform(0, 2 * np.pi, 6)
+    params[:, 2] = f * np.cos(ang)
+    params[:, 3] = f * np.sin(ang)
+    params[:, 1] = np.linspace(1.6, 2.6, 6)     # gamma across the prior's range
+    ll, g = _gpu(abi, spec, image, psf, params)
+    rl, _, rg = oracle_eval(spec, image, psf, params)
+    assert_parity(ll, g, rl, rg, "|e| = %.2f" % f, extra=conditioned_bound(spec, image, psf, params),
+                  ll_extra=ll_bound(spec, image, psf, params))
