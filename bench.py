@@ -288,7 +288,7 @@ def run_serving_workload(device, n_latency: int = 200, n_capacity: int = 1000):
             "speedup_lenses_per_s": cap.lenses_per_s / base_cap.lenses_per_s}
 
 
-def run_map_workload(device, n_starts: int = 300, steps=(300, 1000)):
+def run_map_workload(device, n_starts: int = 300, steps=(300, 1000, 3000)):
     """Sec. 2.3 / Table 1: multi-start MAP, 300 starts drawn from the prior, on
     a system drawn from the paper's simulation distribution (80x80, k = 2,
     sigma_bkg = 0.2, t_exp = 100 s, G = 1). Reports time, the fraction of
