@@ -404,6 +404,24 @@ int gl_vi_step(int n, int d, const double* eps, const double* logp, const double
                double* grad_out, double* loss_out, void* workspace, void* stream);
 
 /*
+ * The two halves of gl_vi_step, for draws spread over several processes:
+ * gl_vi_moments - the estimator's moment sums over this call's n draws
+ *   (sums_out: device float64 [1 + gl_vi_param_count(d)], not divided by n);
+ *   the caller gathers the processes' sums, one row each, and passes them to
+ * gl_vi_apply - the loss, gradient and (with m, v) Adam step from sums
+ *   [nparts, 1 + gl_vi_param_count(d)] over n_total draws in all; the rows are
+ *   added in row order, so every process that passes the same rows gets the
+ *   same bits. Other arguments mean what they mean for gl_vi_step.
+ * One process: gl_vi_moments then gl_vi_apply(n, d, 1, ...) gives gl_vi_step's
+ * bits. Errors: GL_ERR_INVALID_ARG for a size out of range or a null pointer.
+ */
+int gl_vi_moments(int n, int d, const double* eps, const double* logp, const double* grad_z, int estimator,
+                  const double* phi, void* workspace, double* sums_out, void* stream);
+int gl_vi_apply(int n_total, int d, int nparts, const double* sums, int estimator, double* phi, double* m, double* v, int t,
+                double lr, double beta1, double beta2, double adam_eps, double* grad_out, double* loss_out,
+                void* stream);
+
+/*
  * gl_loglik_grad_profiled - log L profiled over the two light amplitudes
  *   (Sec. 2.1.2: with a parameter-independent variance the model is linear in
  *   I_l and I_s, so they are solved in closed form). Per vector: the model

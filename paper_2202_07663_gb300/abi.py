@@ -64,6 +64,8 @@ SIGNATURES = {
     "gl_vi_workspace_bytes": ([_i, _i], ctypes.c_size_t),
     "gl_vi_sample": ([_i, _i, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_vi_step": ([_i, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp], _i),
+    "gl_vi_moments": ([_i, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp], _i),
+    "gl_vi_apply": ([_i, _i, _i, _vp, _i, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp, _vp, _vp], _i),
     "gl_posterior_grad": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_error_string": ([_i], ctypes.c_char_p),
     "gl_last_error_message": ([], ctypes.c_char_p),

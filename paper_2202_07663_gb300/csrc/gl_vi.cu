@@ -255,6 +255,16 @@ __global__ void __launch_bounds__(kThreads) k_vi_finish(int n, int d, int nblk, 
   }
 }
 
+// Sum the blocks' partial moments in block order: the moment sums of this
+// call's draws (other processes' draws are added by the caller).
+__global__ void k_vi_sum(int Q, int nblk, const double* __restrict__ partial, double* __restrict__ sums) {
+  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < nblk; ++b) t += partial[size_t(b) * Q + q];
+    sums[q] = t;
+  }
+}
+
 int finish(cudaStream_t st, const char* what) {
   cudaError_t e = gl_internal::hooks()->after(GL_K_OTHER, st);
   return e == cudaSuccess ? GL_OK : gl_internal::cuda_error(e, what);
@@ -314,6 +324,44 @@ int gl_vi_step(int n, int d, const double* eps, const double* logp, const double
   h->before(GL_K_OTHER, st);
   k_vi_finish<<<1, kThreads, 0, st>>>(n, d, nb, part, pw, phi, m, v, c1, c2, lr, beta1, beta2, adam_eps, grad_out,
                                       loss_out);
+  return finish(st, "k_vi_finish");
+}
+
+int gl_vi_moments(int n, int d, const double* eps, const double* logp, const double* grad_z, int estimator,
+                  const double* phi, void* workspace, double* sums_out, void* stream) {
+  if (n < 1 || d < 1 || d > GL_VI_MAX_D) return gl_internal::set_error(GL_ERR_INVALID_ARG, "bad n or d");
+  if (estimator != GL_VI_SCORE && estimator != GL_VI_PATHWISE)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "unknown estimator");
+  if (!eps || !logp || !phi || !workspace || !sums_out || (estimator == GL_VI_PATHWISE && !grad_z))
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  const int nb = n_blocks(n);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gl::Hooks* h = gl_internal::hooks();
+  double* part = static_cast<double*>(workspace);
+  h->before(GL_K_OTHER, st);
+  k_vi_moments<<<nb, kThreads, 0, st>>>(n, d, eps, logp, grad_z, phi, estimator == GL_VI_PATHWISE ? 1 : 0, part);
+  int rc = finish(st, "k_vi_moments");
+  if (rc != GL_OK) return rc;
+  h->before(GL_K_OTHER, st);
+  k_vi_sum<<<1, kThreads, 0, st>>>(1 + d + tri(d), nb, part, sums_out);
+  return finish(st, "k_vi_sum");
+}
+
+int gl_vi_apply(int n_total, int d, int nparts, const double* sums, int estimator, double* phi, double* m, double* v, int t,
+                double lr, double beta1, double beta2, double adam_eps, double* grad_out, double* loss_out,
+                void* stream) {
+  if (n_total < 1 || d < 1 || d > GL_VI_MAX_D || nparts < 1)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "bad n, d or nparts");
+  if (estimator != GL_VI_SCORE && estimator != GL_VI_PATHWISE)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "unknown estimator");
+  if (!sums || !phi || !grad_out || !loss_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if ((m == nullptr) != (v == nullptr)) return gl_internal::set_error(GL_ERR_INVALID_ARG, "m and v: both or neither");
+  if (m && (t < 1 || !std::isfinite(lr))) return gl_internal::set_error(GL_ERR_INVALID_ARG, "t < 1 or lr");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double c1 = m ? 1.0 - std::pow(beta1, t) : 1.0, c2 = m ? 1.0 - std::pow(beta2, t) : 1.0;
+  gl_internal::hooks()->before(GL_K_OTHER, st);
+  k_vi_finish<<<1, kThreads, 0, st>>>(n_total, d, nparts, sums, estimator == GL_VI_PATHWISE ? 1 : 0, phi, m, v, c1, c2,
+                                      lr, beta1, beta2, adam_eps, grad_out, loss_out);
   return finish(st, "k_vi_finish");
 }
 

@@ -11,7 +11,7 @@ library's CUDA kernels (``gl_hmc_*``); the random numbers (momenta, accept
 uniforms) come from a seeded torch generator and are passed in. The mass
 matrix is diagonal. Targets:
 
-- ``LensTarget``: log L in the physical parameters (the config-3 workload);
+- ``LensTarget``: log L in the physical parameters (the HMC throughput workload);
 - ``PosteriorTarget``: the posterior of the unconstrained parameters,
   log p~(z) = log L(g(z)) + log p(g(z)) + log|J| (Eq. reparam-post), through
   ``gl_map_transform`` and ``gl_posterior_grad`` — the paper's sampler;
@@ -34,7 +34,7 @@ from typing import Callable, Optional
 import numpy as np
 import torch
 
-from . import abi
+from . import abi, distributed
 
 NPARAM = abi.NPARAM
 
@@ -291,8 +291,18 @@ class HMC:
 
     def __init__(self, q0: torch.Tensor, inv_mass: torch.Tensor, step_size: float, n_leapfrog: int,
                  system=None, logp_grad: Optional[Callable] = None, target=None, seed: int = 0,
-                 graphs: bool = False):
-        self.q = q0.to(torch.float64).contiguous().clone()
+                 graphs: bool = False, group=None):
+        # with a process group, q0 holds every chain and this process runs its
+        # shard of them; random draws are made for all chains and sliced
+        self.group = group
+        rank, size = distributed.world(group)
+        self.B_total = q0.shape[0]
+        if self.B_total < size:
+            raise ValueError("fewer chains than processes")
+        self.rows = distributed.shard(self.B_total, rank, size)
+        self.row_counts = distributed.counts(self.B_total, size)
+        self.size = size
+        self.q = q0[self.rows[0]:self.rows[1]].to(torch.float64).contiguous().clone()
         self.B, self.d = self.q.shape
         self.dev = self.q.device
         self.inv_mass = inv_mass.to(torch.float64).to(self.dev).contiguous()
@@ -306,7 +316,9 @@ class HMC:
         B, d = self.B, self.d
         f64 = dict(dtype=torch.float64, device=self.dev)
         self.p = torch.empty(B, d, **f64)
-        self.p0 = torch.empty(B, d, **f64)
+        self.p0_all = torch.empty(self.B_total, d, **f64)
+        self.p0 = self.p0_all[self.rows[0]:self.rows[1]]
+        self.u_all = torch.empty(self.B_total, **f64)
         self.qp = torch.empty(B, d, **f64)
         self.gp = torch.empty(B, d, **f64)
         self.lp_new = torch.empty(B, **f64)
@@ -336,7 +348,7 @@ class HMC:
         B, d = self.B, self.d
         L = self.L if n_leapfrog is None else int(n_leapfrog)
         self.q_prev.copy_(self.q)
-        torch.randn(B, d, generator=self.gen, dtype=torch.float64, device=self.dev, out=self.p0)
+        torch.randn(self.B_total, d, generator=self.gen, dtype=torch.float64, device=self.dev, out=self.p0_all)
         self.p0.mul_(torch.rsqrt(self.inv_mass))
         self.p.copy_(self.p0)
         self.qp.copy_(self.q)
@@ -353,7 +365,8 @@ class HMC:
                 abi.gl_hmc_leapfrog(B, d, self.qp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
                                     self.inv_mass.data_ptr(), self.eps, 0.5 if l == 0 else 1.0, q32, stream)
                 self.target(self.qp, self.q32, self.lp_new, self.gp)
-        log_u = torch.rand(B, generator=self.gen, dtype=torch.float64, device=self.dev).log_()
+        torch.rand(self.B_total, generator=self.gen, dtype=torch.float64, device=self.dev, out=self.u_all)
+        log_u = self.u_all[self.rows[0]:self.rows[1]].log_()
         abi.gl_hmc_finish(B, d, self.p0.data_ptr(), self.logp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
                           self.lp_new.data_ptr(), self.qp.data_ptr(), self.inv_mass.data_ptr(), log_u.data_ptr(),
                           self.eps, self.q.data_ptr(), self.logp.data_ptr(), self.grad.data_ptr(),
@@ -375,11 +388,20 @@ class HMC:
         return g
 
     def chees_gradient(self, t: float):
-        """(gradient in log T, criterion, weight sum) of the last iteration (device)."""
-        abi.gl_hmc_chees(self.B, self.d, self.q_prev.data_ptr(), self.qp.data_ptr(), self.p.data_ptr(),
-                         self.inv_mass.data_ptr(), self.accept_prob.data_ptr(), t, self.chees.data_ptr(),
+        """(gradient in log T, criterion, weight sum) of the last iteration
+        over all chains (device); with a process group the chains' rows are
+        gathered first and every process evaluates the same criterion."""
+        rows = (self.q_prev, self.qp, self.p, self.accept_prob)
+        if self.size > 1:
+            rows = tuple(distributed.gather_rows(x, self.group, self.row_counts).contiguous() for x in rows)
+        abi.gl_hmc_chees(self.B_total, self.d, rows[0].data_ptr(), rows[1].data_ptr(), rows[2].data_ptr(),
+                         self.inv_mass.data_ptr(), rows[3].data_ptr(), t, self.chees.data_ptr(),
                          torch.cuda.current_stream(self.dev).cuda_stream)
         return self.chees
+
+    def mean_accept_prob(self) -> torch.Tensor:
+        """The last iteration's acceptance probability averaged over all chains (device scalar)."""
+        return distributed.mean(self.accept_prob, self.group, self.row_counts)
 
     def run(self, n_iter: int) -> HMCStats:
         torch.cuda.synchronize(self.dev)
@@ -437,10 +459,10 @@ class HMC:
                     self.chees_gradient(t)
                     g = float(self.chees[0].item())
                     T = ta.update(g)
-                self.eps = da.update(float(self.accept_prob.mean().item()))
+                self.eps = da.update(float(self.mean_accept_prob().item()))
                 if i == n_adapt - 1:
                     self.eps = da.final()
-            ab += self.accept_prob.mean()
+            ab += self.mean_accept_prob()
         out = torch.empty(n_samples, self.B, self.d, dtype=torch.float64, device=self.dev)
         asum = torch.zeros((), dtype=torch.float64, device=self.dev)
         nl = 0
@@ -449,7 +471,7 @@ class HMC:
             nl += L
             self.step(L)
             out[i].copy_(self.q)
-            asum += self.accept_prob.mean()
+            asum += self.mean_accept_prob()
         torch.cuda.synchronize(self.dev)
         return AdaptiveRun(out, self.eps, float(ab.item()) / max(1, n_burn), float(asum.item()) / max(1, n_samples),
                            time.perf_counter() - t0, self.grad_evals - e0, T, nl / max(1, n_samples))
@@ -465,7 +487,7 @@ class PosteriorSamples:
 def sample_posterior(system, z_center: torch.Tensor, cov: torch.Tensor, chains: int = 50, n_burn: int = 250,
                      n_samples: int = 750, n_leapfrog: int = 5, seed: int = 0, prior=None,
                      step_size: float = 0.3, adapt_trajectory: bool = True,
-                     max_leapfrog: int = 256, graphs: bool = True) -> PosteriorSamples:
+                     max_leapfrog: int = 256, graphs: bool = True, group=None) -> PosteriorSamples:
     """The sampling step of the pipeline (Sec. 2.5, Table 1): chains drawn from
     N(z_center, cov) (the variational posterior in the paper), HMC on log p~(z)
     with mass cov^-1 (whitened coordinates); over the first 80% of burn-in the
@@ -474,9 +496,13 @@ def sample_posterior(system, z_center: torch.Tensor, cov: torch.Tensor, chains: 
     Table 1's 0.3 x 5) follows the ChEES gradient; otherwise n_leapfrog is
     fixed. With graphs, each leapfrog step is a replayed CUDA graph.
     The system's scratch is reserved for the chains first (no allocation
-    may happen inside a captured graph)."""
+    may happen inside a captured graph). With a process group the chains are
+    split over the processes and every process returns all chains' samples
+    (``run.grad_evals`` counts this process's evaluations)."""
     dev = z_center.device
-    system.reserve(chains)
+    rank, size = distributed.world(group)
+    lo, hi = distributed.shard(chains, rank, size)
+    system.reserve(max(1, hi - lo))
     L = torch.linalg.cholesky(cov.to(torch.float64).to(dev))
     post = PosteriorTarget(system, prior)
     target = WhitenedTarget(post, z_center.to(dev), L)
@@ -484,8 +510,11 @@ def sample_posterior(system, z_center: torch.Tensor, cov: torch.Tensor, chains: 
     g.manual_seed(seed)
     x0 = torch.randn(chains, NPARAM, dtype=torch.float64, device=dev, generator=g)
     sampler = HMC(x0, torch.ones(NPARAM, dtype=torch.float64, device=dev), step_size, n_leapfrog, target=target,
-                  seed=seed + 1, graphs=graphs)
+                  seed=seed + 1, graphs=graphs, group=group)
     run = sampler.run_adaptive(n_burn, n_samples, adapt_trajectory=adapt_trajectory, max_leapfrog=max_leapfrog)
+    if size > 1:
+        chains_first = run.samples.transpose(0, 1).contiguous()
+        run.samples = distributed.gather_rows(chains_first, group, sampler.row_counts).transpose(0, 1).contiguous()
     n = n_samples * chains
     z = target.to_z(run.samples.reshape(n, NPARAM))
     th = torch.empty(n, NPARAM, dtype=torch.float32, device=dev)

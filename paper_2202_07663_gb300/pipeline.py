@@ -12,6 +12,10 @@
 the chains' start) by the Laplace covariance of log p~(z) at the MAP point
 (see ``hmc.laplace_covariance``); VI still runs and is timed.
 Every stage runs in the library's kernels; this module only sequences them.
+
+With a process group (one GPU per process, ``distributed``) the starts, the
+VI draws and the chains are split over the processes; every process ends
+with the same MAP point, variational posterior and all chains' samples.
 """
 from __future__ import annotations
 
@@ -22,7 +26,7 @@ from typing import Optional
 import numpy as np
 import torch
 
-from . import abi, hmc, map as gmap, vi
+from . import abi, distributed, hmc, map as gmap, vi
 
 NPARAM = abi.NPARAM
 
@@ -41,27 +45,33 @@ class PipelineResult:
 def model_system(system: abi.GLSystem, theta_starts: torch.Tensor, prior=None, map_steps: int = 300,
                  vi_steps: int = 1000, vi_draws: int = 500, chains: int = 50, n_burn: int = 250,
                  n_samples: int = 750, preconditioner: str = "vi", seed: int = 0,
-                 vi_estimator: str = "pathwise") -> PipelineResult:
+                 vi_estimator: str = "pathwise", group=None) -> PipelineResult:
     """Run MAP -> VI -> HMC on ``system`` from the given multi-start points
-    (physical, [n_MAP, 22]; the paper draws them from the prior)."""
+    (physical, [n_MAP, 22]; the paper draws them from the prior; with a
+    process group every process passes all of them)."""
     if preconditioner not in ("vi", "laplace"):
         raise ValueError("preconditioner must be 'vi' or 'laplace'")
     dev = theta_starts.device
     prior = gmap.PAPER_PRIOR if prior is None else prior
-    system.reserve(max(theta_starts.shape[0], vi_draws, chains, 2 * NPARAM))
+    rank, size = distributed.world(group)
+    n_map = theta_starts.shape[0]
+    if min(n_map, vi_draws, chains) < size:
+        raise ValueError("fewer starts, draws or chains than processes")
+    lo, hi = distributed.shard(n_map, rank, size)
+    local = [hi - lo] + [b - a for a, b in (distributed.shard(n, rank, size) for n in (vi_draws, chains))]
+    system.reserve(max(local + [2 * NPARAM]))
     sec, evals = {}, {}
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
 
-    m = gmap.MultiStartMAP(system, prior=prior, steps=map_steps).run(theta_starts)
-    best = m.best
-    z_map = m.z[best].clone()
+    m = gmap.MultiStartMAP(system, prior=prior, steps=map_steps).run(theta_starts[lo:hi])
+    _, map_objective, (theta_map, z_map) = distributed.best_row(m.objective, [m.theta, m.z], group)
     torch.cuda.synchronize(dev)
     t1 = time.perf_counter()
     sec["map"], evals["map"] = t1 - t0, m.grad_evals
 
     post = hmc.PosteriorTarget(system, prior)
-    r = vi.FullRankVI(post, n=vi_draws, steps=vi_steps, estimator=vi_estimator, seed=seed).run(z_map)
+    r = vi.FullRankVI(post, n=vi_draws, steps=vi_steps, estimator=vi_estimator, seed=seed, group=group).run(z_map)
     torch.cuda.synchronize(dev)
     t2 = time.perf_counter()
     sec["vi"], evals["vi"] = t2 - t1, r.evals
@@ -75,10 +85,9 @@ def model_system(system: abi.GLSystem, theta_starts: torch.Tensor, prior=None, m
     t3 = time.perf_counter()
     sec["preconditioner"] = t3 - t2
     ps = hmc.sample_posterior(system, mu, cov, chains=chains, n_burn=n_burn, n_samples=n_samples, seed=seed + 7,
-                              prior=prior)
+                              prior=prior, group=group)
     torch.cuda.synchronize(dev)
     t4 = time.perf_counter()
     sec["hmc"], evals["hmc"] = t4 - t3, ps.run.grad_evals
     sec["total"] = t4 - t0
-    return PipelineResult(m.theta[best].cpu().numpy().astype(np.float64), float(m.objective[best].item()), r.mu,
-                          r.cov, ps, sec, evals)
+    return PipelineResult(theta_map.cpu().numpy().astype(np.float64), map_objective, r.mu, r.cov, ps, sec, evals)

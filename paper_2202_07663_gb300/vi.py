@@ -10,6 +10,12 @@ mu = the MAP point, Sigma = 1e-6 I at the start.
 
 Targets are the ones ``hmc`` defines (``PosteriorTarget`` for a lens system,
 ``FunctionTarget`` for tests): ``target(z64, z32, logp_out, grad_out_or_None)``.
+
+With a process group the n draws of each iteration are split over the
+processes (``distributed``): each evaluates its rows, reduces them to moment
+sums (``gl_vi_moments``), and every process applies the same step from all
+processes' sums (``gl_vi_apply``); ``VIResult.evals`` counts this process's
+evaluations.
 """
 from __future__ import annotations
 
@@ -20,7 +26,7 @@ from typing import Optional
 
 import torch
 
-from . import abi
+from . import abi, distributed
 
 SCORE, PATHWISE = 0, 1
 ADAM = (0.9, 0.999, 1e-8)
@@ -77,7 +83,7 @@ class FullRankVI:
     """Stochastic VI with Adam; ``estimator`` 'pathwise' (reparameterised) or 'score' (Eq. elbo-grad)."""
 
     def __init__(self, target, d: int = abi.NPARAM, n: int = 500, steps: int = 1000, lr_peak: float = 1e-3,
-                 warmup: int = 500, estimator: str = "pathwise", seed: int = 0, lr_fn=None):
+                 warmup: int = 500, estimator: str = "pathwise", seed: int = 0, lr_fn=None, group=None):
         if estimator not in ("pathwise", "score"):
             raise ValueError("estimator must be 'pathwise' or 'score'")
         self.target = target
@@ -85,11 +91,15 @@ class FullRankVI:
         self.lr_fn = lr_fn if lr_fn is not None else (lambda t: quadratic_warmup(t, lr_peak, warmup))
         self.est = PATHWISE if estimator == "pathwise" else SCORE
         self.seed = seed
+        self.group = group
 
     def run(self, mu0: torch.Tensor, sigma0: float = 1e-6, phi0: Optional[torch.Tensor] = None) -> VIResult:
         dev = mu0.device
         d, n = self.d, self.n
         P = n_params(d)
+        rank, size = distributed.world(self.group)
+        lo, hi = distributed.shard(n, rank, size)
+        nl = hi - lo                                  # this process's draws
         lib = abi.lib_handle()
         st = torch.cuda.current_stream(dev).cuda_stream
         f64 = dict(dtype=torch.float64, device=dev)
@@ -101,12 +111,14 @@ class FullRankVI:
         v = torch.zeros(P, **f64)
         g = torch.empty(P, **f64)
         loss = torch.empty(self.steps, **f64)
-        eps = torch.empty(n, d, **f64)
-        z = torch.empty(n, d, **f64)
-        z32 = torch.empty(n, d, dtype=torch.float32, device=dev)
-        logp = torch.empty(n, **f64)
-        gz = torch.empty(n, d, **f64) if self.est == PATHWISE else None
-        ws = torch.empty(max(1, lib.gl_vi_workspace_bytes(n, d)), dtype=torch.uint8, device=dev)
+        eps_all = torch.empty(n, d, **f64)
+        eps = eps_all[lo:hi]
+        z = torch.empty(nl, d, **f64)
+        z32 = torch.empty(nl, d, dtype=torch.float32, device=dev)
+        logp = torch.empty(nl, **f64)
+        gz = torch.empty(nl, d, **f64) if self.est == PATHWISE else None
+        ws = torch.empty(max(1, lib.gl_vi_workspace_bytes(max(1, nl), d)), dtype=torch.uint8, device=dev)
+        sums = torch.zeros(1 + P, **f64)
         gen = torch.Generator(device=dev)
         gen.manual_seed(self.seed)
         need32 = getattr(self.target, "needs_q32", True)
@@ -114,15 +126,25 @@ class FullRankVI:
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for t in range(self.steps):
-            torch.randn(n, d, generator=gen, out=eps)
-            abi._check(lib.gl_vi_sample(n, d, eps.data_ptr(), phi.data_ptr(), None, z.data_ptr(),
-                                        z32.data_ptr() if need32 else None, st), "gl_vi_sample")
-            self.target(z, z32, logp, gz)
-            abi._check(lib.gl_vi_step(n, d, eps.data_ptr(), logp.data_ptr(), gz.data_ptr() if gz is not None else None,
-                                      self.est, phi.data_ptr(), m.data_ptr(), v.data_ptr(), t + 1, self.lr_fn(t),
-                                      b1, b2, ae, g.data_ptr(), loss[t:].data_ptr(), ws.data_ptr(), st),
-                       "gl_vi_step")
+            torch.randn(n, d, generator=gen, out=eps_all)   # every process draws all n, keeps its rows
+            gzp = gz.data_ptr() if gz is not None else None
+            if nl:
+                abi._check(lib.gl_vi_sample(nl, d, eps.data_ptr(), phi.data_ptr(), None, z.data_ptr(),
+                                            z32.data_ptr() if need32 else None, st), "gl_vi_sample")
+                self.target(z, z32, logp, gz)
+            if size == 1:
+                abi._check(lib.gl_vi_step(n, d, eps.data_ptr(), logp.data_ptr(), gzp, self.est, phi.data_ptr(),
+                                          m.data_ptr(), v.data_ptr(), t + 1, self.lr_fn(t), b1, b2, ae, g.data_ptr(),
+                                          loss[t:].data_ptr(), ws.data_ptr(), st), "gl_vi_step")
+                continue
+            if nl:
+                abi._check(lib.gl_vi_moments(nl, d, eps.data_ptr(), logp.data_ptr(), gzp, self.est, phi.data_ptr(),
+                                             ws.data_ptr(), sums.data_ptr(), st), "gl_vi_moments")
+            parts = distributed.gather_parts(sums, self.group)
+            abi._check(lib.gl_vi_apply(n, d, size, parts.data_ptr(), self.est, phi.data_ptr(), m.data_ptr(),
+                                       v.data_ptr(), t + 1, self.lr_fn(t), b1, b2, ae, g.data_ptr(),
+                                       loss[t:].data_ptr(), st), "gl_vi_apply")
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
         mu, L = unpack(phi, d)
-        return VIResult(phi, mu, L, loss, dt, n * self.steps)
+        return VIResult(phi, mu, L, loss, dt, nl * self.steps)

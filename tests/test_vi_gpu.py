@@ -205,3 +205,72 @@ def test_vi_lockstep_with_oracle_on_a_lens_posterior(mods, estimator):
         assert loss.item() == pytest.approx(lo, rel=1e-11)
         np.testing.assert_allclose(phid.cpu().numpy(), phi, rtol=1e-10, atol=1e-12)
     s.close()
+
+
+@pytest.mark.parametrize("estimator", ["score", "pathwise"])
+def test_moments_then_apply(mods, estimator):
+    """The step split in two: one part gives gl_vi_step's bits; draws spread
+    over uneven parts (as over processes) give the oracle's step on all draws."""
+    abi, _, _, vi = mods
+    lib = abi.lib_handle()
+    st = torch.cuda.current_stream().cuda_stream
+    d, n = 22, 500
+    rng = np.random.default_rng(97)
+    phi = _rand_phi(rng, d)
+    eps = rng.normal(size=(n, d))
+    logp = -1e3 + rng.normal(size=n) * 30
+    gz = rng.normal(size=(n, d)) * 50
+    P = vo.n_params(d)
+    Q = 1 + P
+    m = rng.normal(size=P) * 0.1
+    v = rng.uniform(0.5, 2.0, P)
+    t, lr = 5, 4e-4
+    est = vi.SCORE if estimator == "score" else vi.PATHWISE
+    ed, lpd, gzd = _cuda(eps), _cuda(logp), _cuda(gz)
+    ws = torch.empty(lib.gl_vi_workspace_bytes(n, d), dtype=torch.uint8, device="cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def gz_ptr(lo):
+        return gzd[lo:].data_ptr() if estimator == "pathwise" else None
+
+    def apply(nparts, sums):
+        phid, md, vd = _cuda(phi), _cuda(m), _cuda(v)
+        g = torch.empty(P, dtype=torch.float64, device="cuda")
+        abi._check(lib.gl_vi_apply(n, d, nparts, sums.data_ptr(), est, phid.data_ptr(), md.data_ptr(), vd.data_ptr(),
+                                   t, lr, *vi.ADAM, g.data_ptr(), loss.data_ptr(), st), "apply")
+        torch.cuda.synchronize()
+        return phid.cpu().numpy(), md.cpu().numpy(), g.cpu().numpy(), loss.item()
+
+    # one part: bitwise gl_vi_step
+    phid, md, vd = _cuda(phi), _cuda(m), _cuda(v)
+    g = torch.empty(P, dtype=torch.float64, device="cuda")
+    abi._check(lib.gl_vi_step(n, d, ed.data_ptr(), lpd.data_ptr(), gz_ptr(0), est, phid.data_ptr(), md.data_ptr(),
+                              vd.data_ptr(), t, lr, *vi.ADAM, g.data_ptr(), loss.data_ptr(), ws.data_ptr(), st), "step")
+    torch.cuda.synchronize()
+    ref = (phid.cpu().numpy(), md.cpu().numpy(), g.cpu().numpy(), loss.item())
+    sums = torch.empty(1, Q, dtype=torch.float64, device="cuda")
+    abi._check(lib.gl_vi_moments(n, d, ed.data_ptr(), lpd.data_ptr(), gz_ptr(0), est, _cuda(phi).data_ptr(),
+                                 ws.data_ptr(), sums.data_ptr(), st), "moments")
+    one = apply(1, sums)
+    for a, b in zip(one[:3], ref[:3]):
+        np.testing.assert_array_equal(a, b)
+    assert one[3] == ref[3]
+    # three uneven parts against the oracle on all draws
+    cuts = [0, 1, 320, n]
+    sums = torch.empty(3, Q, dtype=torch.float64, device="cuda")
+    pd = _cuda(phi)
+    for k in range(3):
+        lo, hi = cuts[k], cuts[k + 1]
+        abi._check(lib.gl_vi_moments(hi - lo, d, ed[lo:].data_ptr(), lpd[lo:].data_ptr(), gz_ptr(lo), est,
+                                     pd.data_ptr(), ws.data_ptr(), sums[k].data_ptr(), st), "moments")
+    pn, mn, gn, ln = apply(3, sums)
+    po, mo_, vo_, lo_, go = vo.vi_step(phi, m, v, t, eps, logp, gz, estimator=estimator, lr=lr)
+    np.testing.assert_allclose(gn, go, rtol=1e-9, atol=1e-9 * np.max(np.abs(go)))
+    assert ln == pytest.approx(lo_, rel=1e-12)
+    np.testing.assert_allclose(mn, mo_, rtol=1e-9, atol=1e-9 * np.max(np.abs(mo_)))
+    np.testing.assert_allclose(pn, po, rtol=1e-12, atol=1e-12)
+    # invalid arguments are refused before any launch
+    assert lib.gl_vi_apply(n, d, 0, sums.data_ptr(), est, pd.data_ptr(), None, None, 0, 0.0, *vi.ADAM,
+                           g.data_ptr(), loss.data_ptr(), st) != 0
+    assert lib.gl_vi_moments(0, d, ed.data_ptr(), lpd.data_ptr(), gz_ptr(0), est, pd.data_ptr(), ws.data_ptr(),
+                             sums.data_ptr(), st) != 0
