@@ -86,7 +86,7 @@ def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
 # DRAM bytes per launch of k_ray_adj from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 prefix of gl_kernels.cu + gl_device.cuh).
 MUFU_RAY_ADJ = 12   # ex2/lg2/rcp per ray in the adjoint (EPL power, two Sersic profiles)
-TRAFFIC = {"cc4acd42356035c7": 62.1952e6}   # ncu dram read + write, one launch at B = 4096
+TRAFFIC = {"db8e85f83db1ce2f": 64.400896e6}   # ncu dram read + write, one launch at B = 4096
 
 
 def kernel_source_hash() -> str:
@@ -106,7 +106,7 @@ def read_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+    """nvidia-smi sampling of SM clocks and throttle reasons (every 50 ms)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -119,7 +119,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -528,7 +528,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
