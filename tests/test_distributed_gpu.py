@@ -81,7 +81,7 @@ def test_two_processes_match_one():
     build.build()
     oracle.build()
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of this (threaded, CUDA) process
         out = m.dict()
         mp.spawn(_single, args=(out,), nprocs=1, join=True)
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
