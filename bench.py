@@ -36,10 +36,9 @@ sys.path.insert(0, ROOT)
 
 from paper_2202_07663_gb300 import inputs  # noqa: E402
 
-CONFIG = 2
 METRIC = "log-lik+grad evals/s"
 UNIT = "evals/s"
-WORKLOAD = "multistart-60x60-k2-psf11-B4096"
+WORKLOAD = inputs.MULTISTART
 
 # FP32 flop counts per ray of the two ray kernels (FMA = 2), N = EPL series
 # terms of the vector; per pixel of the convolution kernel.
@@ -158,7 +157,7 @@ class Clocks:
 
 def rank_param_seed(rank: int) -> int:
     """Seed of rank r's parameter batch: every rank evaluates its own B vectors."""
-    return CONFIG * 1000 + 17 + rank
+    return inputs.WORKLOADS[WORKLOAD]["seed"] + 17 + rank
 
 
 def max_over_ranks(value: float, device, world: int) -> float:
@@ -180,9 +179,9 @@ def make_workload(device, rank: int):
     """Synthetic lens system (observed image from the GPU model + seeded noise) and B vectors."""
     import torch
     from paper_2202_07663_gb300 import abi
-    c = inputs.CONFIGS[CONFIG]
+    c = inputs.WORKLOADS[WORKLOAD]
     spec, B = c["spec"], c["B"]
-    rng = inputs.rng_for(CONFIG, 0)
+    rng = inputs.rng_for(WORKLOAD, 0)
     truth = inputs.draw_truth(rng)
     psf = inputs.make_psf(spec).astype(np.float32)
     blank = np.zeros((spec.H, spec.W), np.float32)
@@ -194,12 +193,12 @@ def make_workload(device, rank: int):
     return spec, B, truth, psf, image, params
 
 
-def synthetic_system(cfg: int, device):
-    """(spec, truth, psf, image) of a config: GPU model of a seeded truth + seeded noise."""
+def synthetic_system(workload: str, device):
+    """(spec, truth, psf, image) of a workload: GPU model of a seeded truth + seeded noise."""
     import torch
     from paper_2202_07663_gb300 import abi
-    spec = inputs.CONFIGS[cfg]["spec"]
-    rng = inputs.rng_for(cfg, 0)
+    spec = inputs.WORKLOADS[workload]["spec"]
+    rng = inputs.rng_for(workload, 0)
     truth = inputs.draw_truth(rng)
     psf = inputs.make_psf(spec).astype(np.float32)
     blank = np.zeros((spec.H, spec.W), np.float32)
@@ -211,10 +210,10 @@ def synthetic_system(cfg: int, device):
 
 
 def run_hmc_workload(device, iterations: int = 200, chains: int = 512, leapfrog: int = 8):
-    """Config 3: HMC through the adjoint, 100x100 pixels, k = 4, 21x21 Moffat PSF."""
+    """HMC through the adjoint, 100x100 pixels, k = 4, 21x21 Moffat PSF."""
     import torch
     from paper_2202_07663_gb300 import abi, hmc
-    spec, truth, psf, image = synthetic_system(3, device)
+    spec, truth, psf, image = synthetic_system(inputs.HMC, device)
     s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
     s.reserve(chains)
     q0 = torch.from_numpy(inputs.draw_perturbed(np.random.default_rng(3017), truth, chains, frac=0.002)).to(device)
@@ -231,11 +230,11 @@ def run_hmc_workload(device, iterations: int = 200, chains: int = 512, leapfrog:
 
 
 def run_stress_workload(device, steps: int = 3):
-    """Config 5: 200x200 pixels, k = 4, 21x21 PSF, B = 16384 vectors per call."""
+    """The stress workload: 200x200 pixels, k = 4, 21x21 PSF, B = 16384 vectors per call."""
     import torch
     from paper_2202_07663_gb300 import abi
-    spec, truth, psf, image = synthetic_system(5, device)
-    B = inputs.CONFIGS[5]["B"]
+    spec, truth, psf, image = synthetic_system(inputs.STRESS, device)
+    B = inputs.WORKLOADS[inputs.STRESS]["B"]
     s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
     s.reserve(B)
     params = inputs.draw_box(np.random.default_rng(5017), B).astype(np.float32)
@@ -267,7 +266,7 @@ def run_stress_workload(device, steps: int = 3):
 
 
 def run_serving_workload(device, n_latency: int = 200, n_capacity: int = 1000):
-    """Config 4: the seeded stream of heterogeneous lenses (Poisson 20/s; sizes
+    """The serving workload: the seeded stream of heterogeneous lenses (Poisson 20/s; sizes
     40..120 px, k in {2, 4}, PSF 11 or 21, 256..2048 vectors per request).
     Latency: the first n_latency requests at their arrival times through the
     continuous-batching server. Capacity: n_capacity requests all at t = 0,
@@ -490,9 +489,9 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    c = inputs.CONFIGS[CONFIG]
+    c = inputs.WORKLOADS[WORKLOAD]
     spec, B = c["spec"], c["B"]
-    rng = inputs.rng_for(CONFIG, 0)
+    rng = inputs.rng_for(WORKLOAD, 0)
     truth = inputs.draw_truth(rng)
     psf = inputs.make_psf(spec).astype(np.float32)
     model = oracle.simulate(truth, spec.H, spec.W, psf, spec.pixel_scale, spec.k)[0]

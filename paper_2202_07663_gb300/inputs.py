@@ -75,18 +75,23 @@ class SystemSpec:
     gain_exposure: float = 1000.0   # G * t_exp, seconds (G = 1)
 
 
-# The five workloads: shapes, PSFs and batch sizes.
-CONFIGS = {
-    1: dict(spec=SystemSpec(60, 60, 2, 11, "gaussian"), B=64, draw="perturbed"),
-    2: dict(spec=SystemSpec(60, 60, 2, 11, "gaussian"), B=4096, draw="box"),
-    3: dict(spec=SystemSpec(100, 100, 4, 21, "moffat"), B=512, draw="perturbed"),
-    5: dict(spec=SystemSpec(200, 200, 4, 21, "gaussian"), B=16384, draw="box"),
+# The fixed-shape workloads: shapes, PSFs, batch sizes and the base of their
+# seeds (system s of a workload draws from PCG64 seeded with seed + s).
+PLAIN = "plain-60x60-k2-psf11-B64"
+MULTISTART = "multistart-60x60-k2-psf11-B4096"
+HMC = "hmc-100x100-k4-moffat21-B512"
+STRESS = "stress-200x200-k4-psf21-B16384"
+WORKLOADS = {
+    PLAIN: dict(spec=SystemSpec(60, 60, 2, 11, "gaussian"), B=64, draw="perturbed", seed=1000),
+    MULTISTART: dict(spec=SystemSpec(60, 60, 2, 11, "gaussian"), B=4096, draw="box", seed=2000),
+    HMC: dict(spec=SystemSpec(100, 100, 4, 21, "moffat"), B=512, draw="perturbed", seed=3000),
+    STRESS: dict(spec=SystemSpec(200, 200, 4, 21, "gaussian"), B=16384, draw="box", seed=5000),
 }
 
 
-def rng_for(config: int, system: int = 0) -> np.random.Generator:
-    """PCG64 stream for (config, system): seed = config * 1000 + system."""
-    return np.random.default_rng(config * 1000 + system)
+def rng_for(workload: str, system: int = 0) -> np.random.Generator:
+    """PCG64 stream of system ``system`` of a workload: seed = its base + system."""
+    return np.random.default_rng(WORKLOADS[workload]["seed"] + system)
 
 
 def draw_truth(rng: np.random.Generator) -> np.ndarray:

@@ -1,4 +1,4 @@
-"""Config-3 path: the adjoint behind torch.autograd.Function, and HMC kernels.
+"""The HMC path (100x100, k=4, 21x21 Moffat PSF): the adjoint behind torch.autograd.Function, and HMC kernels.
 
 - autograd gradient of LogLik vs the FP64 oracle and vs central finite
   differences (h = 1e-4) of the oracle's log L, on the 100x100, k=4, 21x21
@@ -35,7 +35,7 @@ def mods():
 
 def test_autograd_gradient_vs_oracle_and_central_differences(mods):
     abi, hmc = mods
-    spec = inputs.CONFIGS[3]["spec"]
+    spec = inputs.WORKLOADS[inputs.HMC]["spec"]
     truth, image, psf = make_system(spec, 3000)
     params = inputs.draw_perturbed(np.random.default_rng(31), truth, 3).astype(np.float32)
     s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)

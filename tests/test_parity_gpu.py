@@ -40,16 +40,16 @@ def _gpu(abi, spec, image, psf, params, grad=True):
     return out
 
 
-def test_config1_plain_b64(abi):
+def test_plain_60x60_b64(abi):
     """60x60, k=2, 11x11 Gaussian PSF; 64 perturbed vectors; all compared.
     Light-centre gradients are sums that cancel around the Sersic cusp, so the
     FP32 model error bound eps * C_i is part of the gradient tolerance."""
-    spec = inputs.CONFIGS[1]["spec"]
+    spec = inputs.WORKLOADS[inputs.PLAIN]["spec"]
     truth, image, psf = make_system(spec, 1000)
     params = inputs.draw_perturbed(np.random.default_rng(1), truth, 64).astype(np.float32)
     ll, g = _gpu(abi, spec, image, psf, params)
     rl, _, rg = oracle_eval(spec, image, psf, params)
-    assert_parity(ll, g, rl, rg, "config 1", extra=conditioned_bound(spec, image, psf, params),
+    assert_parity(ll, g, rl, rg, "plain 60x60 B=64", extra=conditioned_bound(spec, image, psf, params),
                   ll_extra=ll_bound(spec, image, psf, params))
 
 
@@ -57,7 +57,7 @@ def test_near_truth_gradient(abi):
     """Vectors 0.1% of the box from the truth: residuals are noise and the
     gradient is a near-cancelling pixel sum, so the FP32 model error bound
     eps * C_i is added to the gradient tolerance."""
-    spec = inputs.CONFIGS[1]["spec"]
+    spec = inputs.WORKLOADS[inputs.PLAIN]["spec"]
     truth, image, psf = make_system(spec, 1001)
     params = inputs.draw_perturbed(np.random.default_rng(2), truth, 8, frac=0.001).astype(np.float32)
     params[0] = truth.astype(np.float32)
@@ -174,7 +174,7 @@ def test_batch_zero_and_argument_errors(abi):
 
 
 def test_deterministic_and_host_path(abi):
-    spec = inputs.CONFIGS[1]["spec"]
+    spec = inputs.WORKLOADS[inputs.PLAIN]["spec"]
     truth, image, psf = make_system(spec, 16)
     params = inputs.draw_perturbed(np.random.default_rng(10), truth, 40).astype(np.float32)
     s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
@@ -217,14 +217,14 @@ def test_grouped_launch_equals_single_calls(abi):
         s.close()
 
 
-@pytest.mark.parametrize("cfg,nsample", [(2, 24), (3, 3), (5, 2)])
-def test_full_size_configs_sampled(abi, cfg, nsample):
+@pytest.mark.parametrize("workload,nsample", [(inputs.MULTISTART, 24), (inputs.HMC, 3), (inputs.STRESS, 2)])
+def test_full_size_workloads_sampled(abi, workload, nsample):
     """Full batch sizes in the launch configuration of the benchmark; the oracle
     checks a seeded sample of the vectors one by one."""
-    c = inputs.CONFIGS[cfg]
+    c = inputs.WORKLOADS[workload]
     spec, B = c["spec"], c["B"]
-    truth, image, psf = make_system(spec, cfg * 1000)
-    rng = np.random.default_rng(cfg)
+    truth, image, psf = make_system(spec, c["seed"])
+    rng = np.random.default_rng(c["seed"] // 1000)
     if c["draw"] == "box":
         params = inputs.draw_box(rng, B).astype(np.float32)
     else:
@@ -234,7 +234,7 @@ def test_full_size_configs_sampled(abi, cfg, nsample):
     idx = np.sort(rng.choice(B, nsample, replace=False))
     idx[-1] = B - 1  # include the last vector of the batch
     rl, _, rg = oracle_eval(spec, image, psf, params[idx])
-    assert_parity(ll[idx], g[idx], rl, rg, "config %d sample" % cfg, ll_extra=ll_bound(spec, image, psf, params[idx]))
+    assert_parity(ll[idx], g[idx], rl, rg, "%s sample" % workload, ll_extra=ll_bound(spec, image, psf, params[idx]))
 
 
 def test_final_kernel_variants_agree_bitwise(abi):

@@ -49,7 +49,7 @@ def _noalloc(lib, sysm, params):
 
 def test_noalloc_matches_allocating_entry_point_twice(abi):
     lib = abi.lib_handle()
-    spec = inputs.CONFIGS[1]["spec"]
+    spec = inputs.WORKLOADS[inputs.PLAIN]["spec"]
     truth, image, psf = make_system(spec, 4242)
     sysm = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
     rng = np.random.default_rng(77)
@@ -65,7 +65,7 @@ def test_noalloc_matches_allocating_entry_point_twice(abi):
 
 def test_noalloc_rejects_batches_beyond_the_static_scratch(abi):
     lib = abi.lib_handle()
-    spec = inputs.CONFIGS[1]["spec"]
+    spec = inputs.WORKLOADS[inputs.PLAIN]["spec"]
     _, image, psf = make_system(spec, 4243)
     sysm = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
     B = SCRATCH_BYTES // (4 * spec.H * spec.W) + 1   # the image work buffer alone overflows
