@@ -491,15 +491,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, GL_ADJ_MINB) k_ray_adj(const __gr
       const int stride = blockDim.x;
 #if GL_ADJ_PAIRED
       {
-        // two pixels per thread and step (p and p + blockDim), their rays paired in f32x2;
-        // a missing second pixel repeats the first with zero weight
-        for (int p = p0 + threadIdx.x; p < p1; p += 2 * stride) {
-          const int q = p + stride;
-          const bool has_q = q < p1;
-          const int qq = has_q ? q : p;
+        // whole steps: two pixels per thread (p and p + blockDim), their rays paired in f32x2
+        const int nfull = (p1 - p0) / (2 * stride);
+        for (int it = 0; it < nfull; ++it) {
+          const int p = p0 + 2 * stride * it + threadIdx.x, q = p + stride;
           const int ip = p / W, jp = p - ip * W;
-          const int iq = qq / W, jq = qq - iq * W;
-          const F2 g = {make_float2(gpre[p], has_q ? gpre[q] : 0.f)};
+          const int iq = q / W, jq = q - iq * W;
+          const F2 g = {make_float2(gpre[p], gpre[q])};
           for (int a = 0; a < k; ++a) {
             const F2 y = {make_float2(fmaf(float(ip * k + a), ss.sub, ss.y0), fmaf(float(iq * k + a), ss.sub, ss.y0))};
             for (int c = 0; c < k; ++c) {
@@ -507,6 +505,22 @@ __global__ void __launch_bounds__(ADJ_THREADS, GL_ADJ_MINB) k_ray_adj(const __gr
               ray_adj(sv, sv.an, sv.ant, x, y, g, acc);
             }
           }
+        }
+        // the ragged end (fewer than 2 blockDim pixels): its rays two per thread and step,
+        // so that every thread takes a share; an odd last ray is paired with itself at zero weight
+        const int base = p0 + 2 * stride * nfull, kk = k * k;
+        const int nr = (p1 - base) * kk;
+        for (int r = 2 * int(threadIdx.x); r < nr; r += 2 * stride) {
+          const bool has2 = r + 1 < nr;
+          const int r2 = has2 ? r + 1 : r;
+          const int pa = base + r / kk, sa = r - (pa - base) * kk;
+          const int pb = base + r2 / kk, sb = r2 - (pb - base) * kk;
+          const int ia = pa / W, ja = pa - ia * W, ib = pb / W, jb = pb - ib * W;
+          const int aa = sa / k, ca = sa - aa * k, ab = sb / k, cb = sb - ab * k;
+          const F2 y = {make_float2(fmaf(float(ia * k + aa), ss.sub, ss.y0), fmaf(float(ib * k + ab), ss.sub, ss.y0))};
+          const F2 x = {make_float2(fmaf(float(ja * k + ca), ss.sub, ss.x0), fmaf(float(jb * k + cb), ss.sub, ss.x0))};
+          const F2 g = {make_float2(gpre[pa], has2 ? gpre[pb] : 0.f)};
+          ray_adj(sv, sv.an, sv.ant, x, y, g, acc);
         }
       }
 #else
