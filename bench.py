@@ -380,7 +380,9 @@ def run_hmc_paper_workload(device, chains: int = 50, n_burn: int = 250, n_sample
 
 def run_variant_workload(device, B: int = 4096, steps: int = 10):
     """Sec. 2.1.2 variant: observed-image variance, log L profiled over the two
-    light amplitudes (2B basis images, 2x2 solves, then log L + gradient),
+    light amplitudes (both basis images from one ray pass, 2B convolutions,
+    2x2 solves and log L of the profiled model, then the gradient by the PSF
+    correlation and the ray adjoint),
     against the plain log L + gradient on the same system and vectors
     (80x80, k = 2, 11x11 PSF, sigma_bkg = 0.2, t_exp = 100 s)."""
     import torch

@@ -427,8 +427,11 @@ int gl_vi_apply(int n_total, int d, int nparts, const double* sums, int estimato
  *   I_l and I_s, so they are solved in closed form). Per vector: the model
  *   images A_l, A_s at unit amplitudes, the 2x2 weighted least-squares solve
  *   [<A_l,A_l> <A_l,A_s>; <A_s,A_l> <A_s,A_s>] [I_l; I_s] = [<A_l,D>; <A_s,D>]
- *   (<a,b> = sum a b / sigma_tot^2; FP64), then log L, chi^2 and the gradient
- *   at the solved amplitudes. Where the system is singular (a self-product
+ *   (<a,b> = sum a b / sigma_tot^2; FP64), then log L and chi^2 of
+ *   M = I_l A_l + I_s A_s (the PSF convolution is linear, so the convolved
+ *   basis images give the convolved model; no second forward pass) and the
+ *   gradient at the solved amplitudes from d log L / d M by the PSF
+ *   correlation and the ray adjoint. Where the system is singular (a self-product
  *   below 1e-12 of the other, or det below 1e-12 of the diagonal product) the
  *   amplitude with the smaller self-product is 0 and the other is solved
  *   alone. The input's I_l and I_s are ignored; grad_out entries 14 and 21

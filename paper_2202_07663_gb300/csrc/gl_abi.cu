@@ -39,7 +39,6 @@ struct gl_system {
   // likelihood profiled over the light amplitudes: basis parameter rows and
   // images (2 per vector), parameter rows with the solved amplitudes
   long long cap_prof = 0;
-  float* d_pbasis = nullptr;
   float* d_pimg = nullptr;
   float* d_pfull = nullptr;
   double* d_pamps = nullptr;
@@ -353,7 +352,6 @@ int gl_system_destroy(gl_system* s) {
   cudaFree(s->d_ll);
   cudaFree(s->d_c2);
   cudaFree(s->d_grad);
-  cudaFree(s->d_pbasis);
   cudaFree(s->d_pimg);
   cudaFree(s->d_pfull);
   cudaFree(s->d_pamps);
@@ -429,36 +427,43 @@ int gl_loglik_grad_profiled(gl_system* s, const float* params, int B, double* lo
   if (B > (1 << 23)) return fail(GL_ERR_INVALID_ARG, "B = %d: the basis images take 2B vectors", B);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (B > s->cap_prof) {
-    cudaFree(s->d_pbasis);
     cudaFree(s->d_pimg);
     cudaFree(s->d_pfull);
     cudaFree(s->d_pamps);
-    s->d_pbasis = s->d_pimg = s->d_pfull = nullptr;
+    s->d_pimg = s->d_pfull = nullptr;
     s->d_pamps = nullptr;
     s->cap_prof = 0;
     const size_t hw = size_t(s->H) * s->W;
-    GL_CUDA(cudaMalloc(&s->d_pbasis, size_t(2) * B * GL_NPARAM * sizeof(float)), "profile scratch");
     GL_CUDA(cudaMalloc(&s->d_pimg, size_t(2) * B * hw * sizeof(float)), "profile scratch");
     GL_CUDA(cudaMalloc(&s->d_pfull, size_t(B) * GL_NPARAM * sizeof(float)), "profile scratch");
     GL_CUDA(cudaMalloc(&s->d_pamps, size_t(2) * B * sizeof(double)), "profile scratch");
     s->cap_prof = B;
   }
   double* amps = amps_out ? amps_out : s->d_pamps;
-  cudaError_t e = gl_internal::launch_basis_params(B, params, s->d_pbasis, st);
-  if (e != cudaSuccess) return cuda_fail(e, "k_basis_params");
-  rc = run_one(s, s->d_pbasis, 2 * B, nullptr, nullptr, nullptr, s->d_pimg, gl::MODE_SIM, st);
+  // the two convolved unit-amplitude basis images of every vector (one ray
+  // pass, 2B convolutions); the image scratch gets 2B slots, so the B-vector
+  // pass below keeps it
+  int ntiles, tile_pix;
+  long long partial;
+  partial_need(s, B, &ntiles, &tile_pix, &partial);
+  rc = ensure_scratch(s, 2LL * B, partial);
   if (rc != GL_OK) return rc;
+  Seg g = make_seg(s, params, B);
+  g.sim = s->d_pimg;
+  cudaError_t e = gl::launch_basis(g, st, &g_prof);
+  if (e != cudaSuccess) return cuda_fail(e, "basis images");
+  // amplitudes, then log L of M = I_l A_l + I_s A_s and d log L / d M into the
+  // image scratch, which the correlation-only pass turns into the gradient
+  const float inv_gain = s->gain_exposure > 0.0 ? float(1.0 / s->gain_exposure) : 0.f;
   e = gl_internal::launch_amp_solve(B, s->H * s->W, s->d_pimg, s->d_image, s->d_sigma2, params, s->d_pfull, amps,
-                                    st);
+                                    inv_gain, loglik_out, chi2_out, grad_out ? s->d_work : nullptr, st);
   if (e != cudaSuccess) return cuda_fail(e, "k_amp_solve");
-  if (grad_out) {
-    rc = run_one(s, s->d_pfull, B, loglik_out, chi2_out, grad_out, nullptr, gl::MODE_GRAD, st);
-    if (rc != GL_OK) return rc;
-    e = gl_internal::launch_zero_amp_grad(B, grad_out, st);
-    if (e != cudaSuccess) return cuda_fail(e, "k_zero_amp_grad");
-    return GL_OK;
-  }
-  return run_one(s, s->d_pfull, B, loglik_out, chi2_out, nullptr, nullptr, gl::MODE_LOGLIK, st);
+  if (!grad_out) return GL_OK;
+  rc = run_one(s, s->d_pfull, B, nullptr, nullptr, grad_out, nullptr, gl::MODE_CORR, st);
+  if (rc != GL_OK) return rc;
+  e = gl_internal::launch_zero_amp_grad(B, grad_out, st);
+  if (e != cudaSuccess) return cuda_fail(e, "k_zero_amp_grad");
+  return GL_OK;
 }
 
 int gl_loglik_grad_host(gl_system* s, const float* params, int B, double* loglik_out, double* chi2_out,

@@ -24,9 +24,11 @@ gl::Hooks* hooks();
 void count_launches(long long n);
 
 // The likelihood profiled over the light amplitudes (gl_variant.cu).
-cudaError_t launch_basis_params(int B, const float* params, float* basis, cudaStream_t st);
+// With loglik set also log L and chi^2 of the profiled model and, with dldm
+// set, d log L / d M per pixel ([B, H, W]).
 cudaError_t launch_amp_solve(int B, int HW, const float* images, const float* data, const float* sigma2,
-                             const float* params, float* params_out, double* amps, cudaStream_t st);
+                             const float* params, float* params_out, double* amps, float inv_gain, double* loglik,
+                             double* chi2, float* dldm, cudaStream_t st);
 cudaError_t launch_zero_amp_grad(int B, double* grad, cudaStream_t st);
 
 }  // namespace gl_internal

@@ -323,6 +323,72 @@ __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd(const __gr
   }
 }
 
+// Unit-amplitude basis images of the likelihood profiled over the light
+// amplitudes: per vector the binned lens light with I_l = 1 into work slot 2b
+// and the binned, lensed source light with I_s = 1 into slot 2b + 1, from one
+// ray pass (both share the rays, the source the deflection); the vector's own
+// amplitudes are not used. Invalid vectors get NaN in both slots.
+template <class Src>
+__global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd_basis(const __grid_constant__ Src src) {
+  __shared__ VecConst sv;
+  __shared__ Seg ss;
+  for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
+    int local;
+    const Seg* segp = src.ray_seg(item, local);
+    block_copy(&ss, segp);
+    __syncthreads();
+    const int b = local / ss.ntiles, tile = local - b * ss.ntiles;
+    block_copy(&sv, ss.vc + b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sv.light[0].I0 = 1.f;
+      sv.light[1].I0 = 1.f;
+    }
+    __syncthreads();
+    const int HW = ss.H * ss.W, W = ss.W, k = ss.k;
+    const int p0 = tile * ss.tile_pix;
+    const int p1 = min(HW, p0 + ss.tile_pix);
+    const float inv_k2 = 1.0f / float(k * k);
+    const bool valid = sv.nterms >= 0;
+    float* out_l = ss.work + size_t(2 * b) * HW;
+    float* out_s = out_l + HW;
+    const int stride = blockDim.x;
+    for (int p = p0 + threadIdx.x; p < p1; p += 2 * stride) {
+      const int q = p + stride;
+      const bool has_q = q < p1;
+      const int qq = has_q ? q : p;
+      const int ip = p / W, jp = p - ip * W;
+      const int iq = qq / W, jq = qq - iq * W;
+      F2 acc_l = sp<F2>(0.f), acc_s = sp<F2>(0.f);
+      if (valid) {
+        for (int a = 0; a < k; ++a) {
+          const F2 y = {make_float2(fmaf(float(ip * k + a), ss.sub, ss.y0), fmaf(float(iq * k + a), ss.sub, ss.y0))};
+          for (int c = 0; c < k; ++c) {
+            const F2 x = {make_float2(fmaf(float(jp * k + c), ss.sub, ss.x0), fmaf(float(jq * k + c), ss.sub, ss.x0))};
+            F2 ax, ay;
+            epl_fwd_T(sv, sv.an, x, y, ax, ay);
+            const F2 bx = x - ax - fmaT(sp<F2>(sv.g1), x, sp<F2>(sv.g2) * y);
+            const F2 by = y - ay - fmaT(sp<F2>(sv.g2), x, sp<F2>(-sv.g1) * y);
+            acc_s = acc_s + sersic_fwd_T(sv.light[1], bx, by);
+            acc_l = acc_l + sersic_fwd_T(sv.light[0], x, y);
+          }
+        }
+        acc_l = acc_l * sp<F2>(inv_k2);
+        acc_s = acc_s * sp<F2>(inv_k2);
+      } else {
+        acc_l = acc_s = sp<F2>(__int_as_float(0x7fc00000));
+      }
+      out_l[p] = acc_l.v.x;
+      out_s[p] = acc_s.v.x;
+      if (has_q) {
+        out_l[q] = acc_l.v.y;
+        out_s[q] = acc_s.v.y;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------- k_ray_adj -----
 
 // Lens or source light: accumulates R, n (two terms), e1, e2, x, y, I0 slots
@@ -642,8 +708,9 @@ __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* 
   float* img2 = img + Hp * Wp;
   float* work = s.work + size_t(b) * HW;
   const bool want_sim = (mode == MODE_SIM);
-  const bool want_grad = (mode == MODE_GRAD);
-  const bool two = want_grad && s.conv_two_buf;
+  const bool corr_only = (mode == MODE_CORR);   // the work slot holds d log L / d M already
+  const bool want_grad = (mode == MODE_GRAD) || corr_only;
+  const bool two = (mode == MODE_GRAD) && s.conv_two_buf;
 
   for (int i = threadIdx.x; i < Kk * Kk; i += blockDim.x) {
     kerF[i] = s.psf[Kk * Kk - 1 - i];
@@ -663,6 +730,7 @@ __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* 
   const int Wr = conv_row_units(W);
   const int units = nstrip * Wr;
   float acc[R];
+  if (!corr_only) {
   for (int u = threadIdx.x; u < units; u += blockDim.x) {
     const int strip = u / Wr, j = u - strip * Wr;
     if (j >= W) continue;
@@ -715,10 +783,13 @@ __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* 
     if (s.chi2) s.chi2[b] = C;
   }
   if (!want_grad) return;
+  }   // !corr_only
 
   // adjoint: gpre = (PSF correlated with dlogL/dM) / k^2
   float* gsrc = img2;
-  if (!two) {
+  if (corr_only) {
+    gsrc = img;   // loaded from the work slot above
+  } else if (!two) {
 #pragma unroll 4
     for (int p = threadIdx.x; p < HW; p += blockDim.x) {
       const int i = p / W, j = p - i * W;
@@ -817,7 +888,8 @@ __device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, dou
   float* stage = img + Hp * P;
   float* work = s.work + size_t(b) * HW;
   const bool want_sim = (mode == MODE_SIM);
-  const bool want_grad = (mode == MODE_GRAD);
+  const bool corr_only = (mode == MODE_CORR);   // the work slot holds d log L / d M already
+  const bool want_grad = (mode == MODE_GRAD) || corr_only;
   const bool two = s.conv_two_buf != 0;
 
   for (int i = threadIdx.x; i < K * KP; i += blockDim.x) {
@@ -842,10 +914,11 @@ __device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, dou
   cp_async_wait_all();
   __syncthreads();
 
-  // pass 1: model image M (convolution with the flipped PSF)
   const int nstrip = (W + S - 1) / S;
   const int units = nstrip * H;
   float acc[S];
+  if (!corr_only) {
+  // pass 1: model image M (convolution with the flipped PSF)
   for (int u = threadIdx.x; u < units; u += blockDim.x) {
     const int strip = u / H, i = u - strip * H, j0 = strip * S;
     corr_row<K>(img, P, kerF, i, j0, acc);
@@ -907,6 +980,7 @@ __device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, dou
     if (s.chi2) s.chi2[b] = C;
   }
   if (!want_grad) return;
+  }   // !corr_only
 
   // pass 2: subpixel adjoint = (PSF correlated with d log L / d M) / k^2
   const float inv_k2 = 1.0f / float(s.k * s.k);
@@ -1119,7 +1193,7 @@ static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t
 
 template <class Src>
 static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj_final, cudaStream_t st,
-                            Hooks* hooks, bool persistent, bool one_tile = false) {
+                            Hooks* hooks, bool persistent, bool one_tile = false, bool fwd_rays = true) {
   const int sms = num_sms();
   cudaError_t e;
   const int vthreads = 128, wpb = vthreads / 32;
@@ -1137,6 +1211,7 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
     hooks->before(GL_K_SETUP, st);
     k_setup<Src><<<sgrid, vthreads, 0, st>>>(src);
     if ((e = hooks->after(GL_K_SETUP, st)) != cudaSuccess) return e;
+    if (!fwd_rays) return cudaSuccess;   // setup only (the correlation-only gradient)
     hooks->before(GL_K_RAY_FWD, st);
     k_ray_fwd<Src><<<rgrid, FWD_THREADS, 0, st>>>(src);
     return hooks->after(GL_K_RAY_FWD, st);
@@ -1158,15 +1233,33 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
 cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   if (s.B <= 0) return cudaSuccess;
   OneSeg src{s};
-  cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false);
+  cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false, mode != MODE_CORR);
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_CONV, st);
   e = launch_conv_class(conv_class(s.K), src, s.B, conv_smem_bytes(s.H, s.W, s.K, s.conv_two_buf != 0), mode, st,
                         false, s.B < num_sms());
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
-  if (mode != MODE_GRAD) return cudaSuccess;
+  if (mode != MODE_GRAD && mode != MODE_CORR) return cudaSuccess;
   return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false, s.ntiles == 1);
+}
+
+cudaError_t launch_basis(const Seg& s, cudaStream_t st, Hooks* hooks) {
+  if (s.B <= 0) return cudaSuccess;
+  OneSeg src{s};
+  cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false, false);   // setup
+  if (e != cudaSuccess) return e;
+  hooks->before(GL_K_RAY_FWD, st);
+  k_ray_fwd_basis<OneSeg><<<s.B * s.ntiles, FWD_THREADS, 0, st>>>(src);
+  if ((e = hooks->after(GL_K_RAY_FWD, st)) != cudaSuccess) return e;
+  Seg c = s;
+  c.B = 2 * s.B;   // the convolution takes the two images of every vector as vectors of their own
+  OneSeg csrc{c};
+  hooks->before(GL_K_CONV, st);
+  e = launch_conv_class(conv_class(c.K), csrc, c.B, conv_smem_bytes(c.H, c.W, c.K, c.conv_two_buf != 0), MODE_SIM,
+                        st, false, c.B < num_sms());
+  if (e != cudaSuccess) return e;
+  return hooks->after(GL_K_CONV, st);
 }
 
 cudaError_t launch_table(const Seg* d_segs, int nseg, int vec_total, int ray_total, const ConvRun* conv, int nconv,

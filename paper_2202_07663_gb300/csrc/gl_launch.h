@@ -11,7 +11,10 @@ namespace gl {
 
 struct Seg;
 
-enum Mode { MODE_SIM = 0, MODE_LOGLIK = 1, MODE_GRAD = 2 };
+// MODE_CORR: the vectors' d log L / d M is already in their work slots (set by
+// the caller); the launch runs the per-vector setup, the PSF correlation and
+// the ray adjoint only (gradient without a forward pass).
+enum Mode { MODE_SIM = 0, MODE_LOGLIK = 1, MODE_GRAD = 2, MODE_CORR = 3 };
 
 // Called around every kernel launch: instrumentation and error checks.
 struct Hooks {
@@ -46,6 +49,12 @@ void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix);
 
 // One segment, passed by value.
 cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks);
+
+// Basis images of the likelihood profiled over the light amplitudes: for the
+// s.B vectors, the PSF-convolved lens light at I_l = 1 into s.sim[2b] and the
+// lensed source light at I_s = 1 into s.sim[2b + 1] (one ray pass; s.work
+// needs 2 s.B image slots).
+cudaError_t launch_basis(const Seg& s, cudaStream_t st, Hooks* hooks);
 
 // Segments in device memory, sorted by convolution class (grouped launch;
 // persistent grids); one convolution launch per ConvRun.

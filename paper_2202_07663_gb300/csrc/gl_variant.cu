@@ -5,9 +5,10 @@
 // (I_l, I_s), M = I_l A_l + I_s A_s, and the amplitudes maximising log L solve
 //   [<A_l,A_l> <A_l,A_s>; <A_s,A_l> <A_s,A_s>] [I_l; I_s] = [<A_l,D>; <A_s,D>],
 // <a,b> = sum_pixels a b / sigma_tot^2. The basis images A come from the
-// simulation path at unit amplitudes; these kernels build those parameter
-// rows, reduce and solve the 2x2 systems (FP64), and zero the amplitude
-// entries of the profiled gradient.
+// simulation path at unit amplitudes (one ray pass for both, k_ray_fwd_basis);
+// these kernels reduce and solve the 2x2 systems (FP64), evaluate log L and
+// d log L / d M of the profiled model, and zero the amplitude entries of the
+// profiled gradient.
 #include <cuda_runtime.h>
 
 #include "gl_internal.h"
@@ -17,17 +18,6 @@ namespace {
 constexpr int kIL = 14, kIS = 21;
 constexpr double kSingular = 1e-12;   // relative size below which a self-product or det counts as zero
 constexpr int kSolveThreads = 256;
-
-// rows 2b and 2b+1 of basis: params[b] with (I_l, I_s) = (1, 0) and (0, 1)
-__global__ void k_basis_params(int B, const float* __restrict__ params, float* __restrict__ basis) {
-  const int n = B * gl::NPARAM;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int b = i / gl::NPARAM, j = i % gl::NPARAM;
-    const float v = params[i];
-    basis[size_t(2 * b) * gl::NPARAM + j] = j == kIL ? 1.f : (j == kIS ? 0.f : v);
-    basis[size_t(2 * b + 1) * gl::NPARAM + j] = j == kIL ? 0.f : (j == kIS ? 1.f : v);
-  }
-}
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
 #pragma unroll
@@ -43,14 +33,22 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // One block per vector: the five weighted inner products, the 2x2 solve, the
-// amplitudes (FP64) and the parameter row with the amplitudes substituted.
+// amplitudes (FP64) and the parameter row with the amplitudes substituted;
+// then, with loglik set, the model M = I_l A_l + I_s A_s (the PSF convolution
+// is linear, so the convolved basis images give the convolved model), log L
+// and chi^2 (FP32 per pixel and thread, FP64 across threads) and, with dldm
+// set, d log L / d M per pixel into dldm[b] (the next pass correlates it with
+// the PSF for the gradient).
 __global__ void __launch_bounds__(kSolveThreads) k_amp_solve(int B, int HW, const float* __restrict__ images,
                                                              const float* __restrict__ data,
                                                              const float* __restrict__ sigma2,
                                                              const float* __restrict__ params,
                                                              float* __restrict__ params_out,
-                                                             double* __restrict__ amps) {
+                                                             double* __restrict__ amps, float inv_gain,
+                                                             double* __restrict__ loglik,
+                                                             double* __restrict__ chi2, float* __restrict__ dldm) {
   __shared__ double sh[kSolveThreads / 32];
+  __shared__ double s_amp[2];
   const int b = blockIdx.x;
   if (b >= B) return;
   const float* Al = images + size_t(2 * b) * HW;
@@ -87,6 +85,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_amp_solve(int B, int HW, cons
     }
     amps[2 * b] = il;
     amps[2 * b + 1] = is;
+    s_amp[0] = il;
+    s_amp[1] = is;
   }
   for (int j = threadIdx.x; j < gl::NPARAM; j += blockDim.x) {
     // thread 0 wrote amps above; the other rows are copies of the input
@@ -94,8 +94,29 @@ __global__ void __launch_bounds__(kSolveThreads) k_amp_solve(int B, int HW, cons
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    params_out[size_t(b) * gl::NPARAM + kIL] = float(amps[2 * b]);
-    params_out[size_t(b) * gl::NPARAM + kIS] = float(amps[2 * b + 1]);
+    params_out[size_t(b) * gl::NPARAM + kIL] = float(s_amp[0]);
+    params_out[size_t(b) * gl::NPARAM + kIS] = float(s_amp[1]);
+  }
+  if (!loglik) return;
+  // the amplitudes as the model evaluation uses them (the substituted FP32 row)
+  const float il = float(s_amp[0]), is = float(s_amp[1]);
+  float ll = 0.f, c2 = 0.f;
+  for (int i = threadIdx.x; i < HW; i += blockDim.x) {
+    const float M = fmaf(il, Al[i], is * As[i]);
+    const float v = fmaf(M, inv_gain, sigma2[i]);
+    const float res = data[i] - M;
+    const float iv = 1.0f / v;
+    const float t2 = res * res * iv;
+    c2 += t2;
+    ll += t2 + logf(6.28318530717958648f * v);
+    // d log L / d M = res/v + (res^2/v^2 - 1/v) / (2 G t_exp)
+    if (dldm) dldm[size_t(b) * HW + i] = fmaf(0.5f * inv_gain, fmaf(t2, iv, -iv), res * iv);
+  }
+  const double L = block_sum(double(ll), sh);
+  const double C = block_sum(double(c2), sh);
+  if (threadIdx.x == 0) {
+    loglik[b] = -0.5 * L;
+    if (chi2) chi2[b] = C;
   }
 }
 
@@ -115,16 +136,12 @@ int grid_for(long long n, int threads) {
 
 namespace gl_internal {
 
-cudaError_t launch_basis_params(int B, const float* params, float* basis, cudaStream_t st) {
-  hooks()->before(GL_K_OTHER, st);
-  k_basis_params<<<grid_for((long long)B * gl::NPARAM, 256), 256, 0, st>>>(B, params, basis);
-  return hooks()->after(GL_K_OTHER, st);
-}
-
 cudaError_t launch_amp_solve(int B, int HW, const float* images, const float* data, const float* sigma2,
-                             const float* params, float* params_out, double* amps, cudaStream_t st) {
+                             const float* params, float* params_out, double* amps, float inv_gain, double* loglik,
+                             double* chi2, float* dldm, cudaStream_t st) {
   hooks()->before(GL_K_OTHER, st);
-  k_amp_solve<<<B, kSolveThreads, 0, st>>>(B, HW, images, data, sigma2, params, params_out, amps);
+  k_amp_solve<<<B, kSolveThreads, 0, st>>>(B, HW, images, data, sigma2, params, params_out, amps, inv_gain, loglik,
+                                           chi2, dldm);
   return hooks()->after(GL_K_OTHER, st);
 }
 
