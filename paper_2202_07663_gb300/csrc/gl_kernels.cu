@@ -1174,7 +1174,8 @@ static cudaError_t launch_conv(const Src& src, int nitems, size_t smem, int mode
 }
 
 // wide: 512-thread blocks for calls with fewer vectors than SMs (one vector's
-// work spread over 16 warps). Every pixel's model value and d log L / d M is
+// work spread over 16 warps) and for blocks that hold an SM's shared memory
+// alone (CONV_WIDE_MIN_SMEM). Every pixel's model value and d log L / d M is
 // computed by one thread whatever the width, so gradients are the same bits;
 // log L and chi^2 are summed in a width-dependent order (last FP32 bits).
 template <class Src>
@@ -1236,8 +1237,9 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false, mode != MODE_CORR);
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_CONV, st);
-  e = launch_conv_class(conv_class(s.K), src, s.B, conv_smem_bytes(s.H, s.W, s.K, s.conv_two_buf != 0), mode, st,
-                        false, s.B < num_sms());
+  const size_t csmem = conv_smem_bytes(s.H, s.W, s.K, s.conv_two_buf != 0);
+  e = launch_conv_class(conv_class(s.K), src, s.B, csmem, mode, st, false,
+                        s.B < num_sms() || csmem > CONV_WIDE_MIN_SMEM);
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD && mode != MODE_CORR) return cudaSuccess;
@@ -1274,7 +1276,8 @@ cudaError_t launch_table(const Seg* d_segs, int nseg, int vec_total, int ray_tot
     cs.conv_nseg = conv[i].nseg;
     cs.conv_total = conv[i].nitems;
     hooks->before(GL_K_CONV, st);
-    e = launch_conv_class(conv[i].cls, cs, conv[i].nitems, conv[i].smem, mode, st, true);
+    e = launch_conv_class(conv[i].cls, cs, conv[i].nitems, conv[i].smem, mode, st, true,
+                          conv[i].smem > CONV_WIDE_MIN_SMEM);
     if (e != cudaSuccess) return e;
     if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   }
@@ -1294,8 +1297,12 @@ static cudaError_t set_devtable_attr(size_t smem) {
 
 cudaError_t prepare_devtable(const size_t* conv_smem) {
   cudaError_t e;
-  if ((e = set_devtable_attr<11, 16, 128, 5>(conv_smem[0])) != cudaSuccess) return e;
-  if ((e = set_devtable_attr<21, 16, 256, 1>(conv_smem[1])) != cudaSuccess) return e;
+  e = conv_smem[0] > CONV_WIDE_MIN_SMEM ? set_devtable_attr<11, 16, 512, 1>(conv_smem[0])
+                                        : set_devtable_attr<11, 16, 128, 5>(conv_smem[0]);
+  if (e != cudaSuccess) return e;
+  e = conv_smem[1] > CONV_WIDE_MIN_SMEM ? set_devtable_attr<21, 16, 512, 1>(conv_smem[1])
+                                        : set_devtable_attr<21, 16, 256, 1>(conv_smem[1]);
+  if (e != cudaSuccess) return e;
   return set_devtable_attr<0, 8, 128, 4>(conv_smem[2]);
 }
 
@@ -1313,7 +1320,7 @@ cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size
   for (int c = 0; c < N_CONV_CLASSES; ++c) {
     DevTable cs{d_hdr, d_segs, c};
     hooks->before(GL_K_CONV, st);
-    e = launch_conv_class(c, cs, 1 << 30, conv_smem[c], MODE_GRAD, st, true);
+    e = launch_conv_class(c, cs, 1 << 30, conv_smem[c], MODE_GRAD, st, true, conv_smem[c] > CONV_WIDE_MIN_SMEM);
     if (e != cudaSuccess) return e;
     if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   }

@@ -30,6 +30,11 @@ size_t conv_smem_bytes(int H, int W, int K, bool two_buf);
 // Largest dynamic shared memory for which the second buffer is used.
 constexpr size_t CONV_TWO_BUF_MAX_SMEM = 200 * 1024;
 
+// Above this dynamic shared memory a convolution block has an SM's shared
+// memory (228 KB) to itself, so the PSF classes with a compile-time side run
+// it with 512 threads (16 warps) instead of 128 or 256.
+constexpr size_t CONV_WIDE_MIN_SMEM = 100 * 1024;
+
 // Whether the convolution of an H x W image, K x K PSF uses the second buffer.
 bool conv_two_buf(int H, int W, int K);
 
