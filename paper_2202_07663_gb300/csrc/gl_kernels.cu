@@ -153,6 +153,79 @@ __device__ void setup_light(const float* p, LightC& L, bool& ok) {
 // factor.
 constexpr double SERIES_TOL = 2e-8;
 
+__device__ __forceinline__ float series_coef(int k, float t) { return (2.f * k - 2.f + t) / (2.f * k + 2.f - t); }
+__device__ __forceinline__ float series_dcoef(int k, float t) {   // d c_k / d t = 4k / (2k + 2 - t)^2
+  const float iden = 1.0f / (2.f * k + 2.f - t);
+  return 4.f * k * iden * iden;
+}
+
+// Term count over the first NC chunks of 32 candidates (NMAX if none of them
+// qualifies): lane tests N = lane + 32 m, with log|a_{N+1}| from a warp prefix
+// sum of log|c_k| (k = lane + 1 + 32 m). The first chunk's result does not
+// depend on NC.
+template <int NC>
+__device__ __forceinline__ int term_count(int lane, float t, float f, float lf, float ltol) {
+  float la[NC];
+#pragma unroll
+  for (int m = 0; m < NC; ++m) la[m] = logf(fabsf(series_coef(lane + 1 + 32 * m, t)));
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const float y = __shfl_up_sync(0xffffffffu, la[m], o);
+      if (lane >= o) la[m] += y;
+    }
+  }
+  float carry = 0.f;
+#pragma unroll
+  for (int m = 0; m < NC; ++m) {
+    la[m] += carry;
+    carry = __shfl_sync(0xffffffffu, la[m], 31);
+  }
+  int n = NMAX;
+#pragma unroll
+  for (int m = NC - 1; m >= 0; --m) {
+    const int N = lane + 32 * m;
+    const float r = fminf(f * fmaxf(1.f, series_coef(N + 2, t)), 0.999999f);
+    const unsigned ok_m = __ballot_sync(0xffffffffu, la[m] + (N + 1) * lf - log1pf(-r) <= ltol);
+    if (ok_m) n = 32 * m + __ffs(ok_m) - 1;
+  }
+  return n;
+}
+
+// a_n = c_1 ... c_n and d a_n / d t for n <= 32 NC by a warp scan of the pairs
+// (c_k, d c_k / d t) under (x1, y1) (x2, y2) = (x1 x2, x1 y2 + x2 y1) (the
+// product rule); the first chunk's values do not depend on NC.
+template <int NC>
+__device__ __forceinline__ void series_coeffs(int lane, float t, VecConst* V) {
+  float xs[NC], ys[NC];
+#pragma unroll
+  for (int m = 0; m < NC; ++m) {
+    xs[m] = series_coef(lane + 1 + 32 * m, t);
+    ys[m] = series_dcoef(lane + 1 + 32 * m, t);
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+      const float px = __shfl_up_sync(0xffffffffu, xs[m], o), py = __shfl_up_sync(0xffffffffu, ys[m], o);
+      if (lane >= o) {
+        ys[m] = fmaf(px, ys[m], xs[m] * py);
+        xs[m] = px * xs[m];
+      }
+    }
+  }
+  float tx = 1.f, ty = 0.f;   // the product over the earlier chunks
+#pragma unroll
+  for (int m = 0; m < NC; ++m) {
+    const float x = tx * xs[m], y = fmaf(tx, ys[m], xs[m] * ty);
+    V->an[lane + 32 * m] = x;
+    V->ant[lane + 32 * m] = y;
+    tx = __shfl_sync(0xffffffffu, x, 31);
+    ty = __shfl_sync(0xffffffffu, y, 31);
+  }
+}
+
 // One warp per vector: lanes 0..21 check one parameter each, lane 0 derives
 // the EPL constants, lanes 1 and 2 the two light profiles; all lanes compute
 // series coefficients and, by ballot, the term count. FP32 throughout: every
@@ -196,69 +269,17 @@ __global__ void k_setup(const __grid_constant__ Src src) {
       V->light[lane - 1] = L;
     }
     ok = __all_sync(0xffffffffu, ok);
-    // term count: lane tests N = lane + 32 m (m < NMAX / 32), with log|a_{N+1}| from a
-    // warp prefix sum of log|c_k| (k = lane + 1 + 32 m)
-    constexpr int NCH = NMAX / 32;
+    // term count and coefficients over the first 32 candidates; the other
+    // chunks only for the vectors (large |eps|) whose series is longer
     const float f = sqrtf(e2s);
     const float lf = f > 0.f ? logf(f) : -1e30f;
     const float ltol = logf(float(SERIES_TOL));
-    auto coef = [&](int k) { return (2.f * k - 2.f + t) / (2.f * k + 2.f - t); };
-    auto dcoef = [&](int k) {   // d c_k / d t = 4k / (2k + 2 - t)^2
-      const float iden = 1.0f / (2.f * k + 2.f - t);
-      return 4.f * k * iden * iden;
-    };
-    float la[NCH];
-#pragma unroll
-    for (int m = 0; m < NCH; ++m) la[m] = logf(fabsf(coef(lane + 1 + 32 * m)));
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-      for (int m = 0; m < NCH; ++m) {
-        const float y = __shfl_up_sync(0xffffffffu, la[m], o);
-        if (lane >= o) la[m] += y;
-      }
-    }
-    float carry = 0.f;
-#pragma unroll
-    for (int m = 0; m < NCH; ++m) {
-      la[m] += carry;
-      carry = __shfl_sync(0xffffffffu, la[m], 31);
-    }
-    int n_fwd = NMAX;
-#pragma unroll
-    for (int m = NCH - 1; m >= 0; --m) {
-      const int N = lane + 32 * m;
-      const float r = fminf(f * fmaxf(1.f, coef(N + 2)), 0.999999f);
-      const unsigned ok_m = __ballot_sync(0xffffffffu, la[m] + (N + 1) * lf - log1pf(-r) <= ltol);
-      if (ok_m) n_fwd = 32 * m + __ffs(ok_m) - 1;
-    }
-    // a_n = c_1 ... c_n and d a_n / d t by a warp scan of the pairs (c_k, d c_k / d t)
-    // under (x1, y1) (x2, y2) = (x1 x2, x1 y2 + x2 y1) (the product rule)
-    float xs[NCH], ys[NCH];
-#pragma unroll
-    for (int m = 0; m < NCH; ++m) {
-      xs[m] = coef(lane + 1 + 32 * m);
-      ys[m] = dcoef(lane + 1 + 32 * m);
-    }
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-      for (int m = 0; m < NCH; ++m) {
-        const float px = __shfl_up_sync(0xffffffffu, xs[m], o), py = __shfl_up_sync(0xffffffffu, ys[m], o);
-        if (lane >= o) {
-          ys[m] = fmaf(px, ys[m], xs[m] * py);
-          xs[m] = px * xs[m];
-        }
-      }
-    }
-    float tx = 1.f, ty = 0.f;   // the product over the earlier chunks
-#pragma unroll
-    for (int m = 0; m < NCH; ++m) {
-      const float x = tx * xs[m], y = fmaf(tx, ys[m], xs[m] * ty);
-      V->an[lane + 32 * m] = x;
-      V->ant[lane + 32 * m] = y;
-      tx = __shfl_sync(0xffffffffu, x, 31);
-      ty = __shfl_sync(0xffffffffu, y, 31);
+    int n_fwd = term_count<1>(lane, t, f, lf, ltol);
+    if (n_fwd < 32) {   // warp-uniform
+      series_coeffs<1>(lane, t, V);
+    } else {
+      n_fwd = term_count<NMAX / 32>(lane, t, f, lf, ltol);
+      series_coeffs<NMAX / 32>(lane, t, V);
     }
     if (lane == 0) {
       V->nterms = ok ? min(n_fwd, NMAX) : -1;
@@ -1094,9 +1115,19 @@ __global__ void k_final_warp(const __grid_constant__ Src src) {
       continue;
     }
     if (lane < NACC) {
+      // eight loads in flight, then added in tile order (the same sum as k_final)
       const double* part = s->partial + size_t(b) * s->ntiles * NACC + lane;
+      const int nt = s->ntiles;
       double acc = 0.0;
-      for (int t = 0; t < s->ntiles; ++t) acc += part[size_t(t) * NACC];
+      int t = 0;
+      for (; t + 8 <= nt; t += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = part[size_t(t + u) * NACC];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+      }
+      for (; t < nt; ++t) acc += part[size_t(t) * NACC];
       sa[w][lane] = acc;
     }
     __syncwarp();
