@@ -238,9 +238,10 @@ def test_full_size_workloads_sampled(abi, workload, nsample):
 
 
 def test_final_kernel_variants_agree_bitwise(abi):
-    """B large enough for one ray tile per vector: the single-system call sums
-    the tiles in one thread per vector, the grouped call in a warp per vector;
-    both must give the same bits (and match the oracle on a sample)."""
+    """B large enough for one ray tile per vector: the single-system call takes
+    each vector's sums straight from its only tile, the grouped (persistent)
+    call through the same end of the adjoint kernel; both must give the same
+    bits (and match the oracle on a sample)."""
     spec = inputs.SystemSpec(16, 16, 1, 3, "gaussian")
     truth, image, psf = make_system(spec, 300)
     params = inputs.draw_perturbed(np.random.default_rng(30), truth, 1400).astype(np.float32)
@@ -275,3 +276,45 @@ def test_high_ellipticity_long_series(abi, f):
     rl, _, rg = oracle_eval(spec, image, psf, params)
     assert_parity(ll, g, rl, rg, "|e| = %.2f" % f, extra=conditioned_bound(spec, image, psf, params),
                   ll_extra=ll_bound(spec, image, psf, params))
+
+
+def test_tile_counters_reset_between_calls(abi):
+    """Small batches split every vector into many ray tiles; the last tile of a
+    vector to finish applies the chain rule, found by a per-vector counter
+    that the setup kernel zeroes in every call. Calls of other sizes in
+    between (single, no-allocation and grouped paths over the same scratch)
+    leave no trace: the same input gives the same bits."""
+    spec = inputs.SystemSpec(40, 40, 2, 11, "gaussian")
+    truth, image, psf = make_system(spec, 310)
+    params = inputs.draw_perturbed(np.random.default_rng(31), truth, 9).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    s2 = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    p = torch.from_numpy(params).cuda()
+    pa, pb = p[:2].contiguous(), p[5:].contiguous()
+
+    def run(sys_, q):
+        return [t.cpu().numpy() for t in sys_.loglik_grad(q)]
+
+    ref = run(s, p)
+    ref_a, ref_b = run(s, pa), run(s2, pb)
+    lls, grads, _ = abi.loglik_grad_grouped([s, s2], [pa, pb])
+    ll_n = torch.empty(5, dtype=torch.float64, device="cuda")
+    g_n = torch.empty(5, 22, dtype=torch.float64, device="cuda")
+    q = p[3:8].contiguous()
+    abi._check(abi.lib_handle().gl_loglik_grad_noalloc(s.handle, q.data_ptr(), 5, ll_n.data_ptr(), None, g_n.data_ptr(),
+                                                      torch.cuda.current_stream().cuda_stream), "noalloc")
+    again = run(s, p)
+    again_a = run(s, pa)
+    ref_q = run(s2, q)
+    np.testing.assert_array_equal(grads[0].cpu().numpy(), ref_a[1])
+    np.testing.assert_array_equal(grads[1].cpu().numpy(), ref_b[1])
+    np.testing.assert_array_equal(again[1], ref[1])
+    np.testing.assert_array_equal(again[0], ref[0])
+    np.testing.assert_array_equal(again_a[1], ref_a[1])
+    np.testing.assert_array_equal(g_n.cpu().numpy(), ref_q[1])
+    s.close()
+    s2.close()
+    idx = np.array([0, 8])
+    rl, _, rg = oracle_eval(spec, image, psf, params[idx])
+    assert_parity(ref[0][idx], ref[1][idx], rl, rg, "many tiles per vector",
+                  ll_extra=ll_bound(spec, image, psf, params[idx]))
