@@ -465,9 +465,8 @@ enum gl_kernel_kind {
   GL_K_SETUP = 0,    /* per-vector constants */
   GL_K_RAY_FWD = 1,  /* ray shooting + lights + k x k binning */
   GL_K_CONV = 2,     /* PSF convolution + likelihood (+ pixel adjoint) */
-  GL_K_RAY_ADJ = 3,  /* recomputed rays + forward-mode derivatives, ending in the
-                        per-vector gradient reduction and chain rule */
-  GL_K_FINAL = 4,    /* reserved (no kernel of its own: the reduction ends GL_K_RAY_ADJ) */
+  GL_K_RAY_ADJ = 3,  /* recomputed rays + forward-mode derivatives */
+  GL_K_FINAL = 4,    /* per-vector gradient reduction */
   GL_K_OTHER = 5
 };
 int gl_profile_enable(int on);

@@ -30,7 +30,6 @@ struct gl_system {
   VecConst* d_vc = nullptr;
   float* d_work = nullptr;
   double* d_partial = nullptr;
-  int* d_done = nullptr;      // [cap_B] ray tiles finished per vector
   // device staging of the host-buffer entry point
   long long cap_host = 0;
   float* d_params = nullptr;
@@ -141,14 +140,11 @@ int ensure_scratch(gl_system* s, long long B, long long partial) {
   if (B > s->cap_B) {
     cudaFree(s->d_vc);
     cudaFree(s->d_work);
-    cudaFree(s->d_done);
     s->d_vc = nullptr;
     s->d_work = nullptr;
-    s->d_done = nullptr;
     s->cap_B = 0;
     GL_CUDA(cudaMalloc(&s->d_vc, sizeof(VecConst) * size_t(B)), "scratch (vector constants)");
     GL_CUDA(cudaMalloc(&s->d_work, sizeof(float) * size_t(B) * s->H * s->W), "scratch (image work)");
-    GL_CUDA(cudaMalloc(&s->d_done, sizeof(int) * size_t(B)), "scratch (tile counters)");
     s->cap_B = B;
   }
   if (partial > s->cap_partial) {
@@ -187,7 +183,6 @@ Seg make_seg(const gl_system* s, const float* params, int B) {
   g.vc = s->d_vc;
   g.work = s->d_work;
   g.partial = s->d_partial;
-  g.tiles_done = s->d_done;
   g.conv_two_buf = gl::conv_two_buf(s->H, s->W, s->K) ? 1 : 0;
   return g;
 }
@@ -227,7 +222,6 @@ gl::Seg seg_without_scratch(const gl_system* s, const float* params, int B) {
   g.vc = nullptr;
   g.work = nullptr;
   g.partial = nullptr;
-  g.tiles_done = nullptr;
   return g;
 }
 
@@ -354,7 +348,6 @@ int gl_system_destroy(gl_system* s) {
   cudaFree(s->d_vc);
   cudaFree(s->d_work);
   cudaFree(s->d_partial);
-  cudaFree(s->d_done);
   cudaFree(s->d_params);
   cudaFree(s->d_ll);
   cudaFree(s->d_c2);

@@ -32,7 +32,7 @@ struct CaptureHooks final : gl::Hooks {
 
 size_t segment_scratch(const gl::Seg& g) {
   return align256(sizeof(gl::VecConst) * size_t(g.B)) + align256(sizeof(float) * size_t(g.B) * g.H * g.W) +
-         align256(sizeof(double) * size_t(g.B) * g.ntiles * gl::NACC) + align256(sizeof(int) * size_t(g.B));
+         align256(sizeof(double) * size_t(g.B) * g.ntiles * gl::NACC);
 }
 
 }  // namespace
@@ -178,8 +178,6 @@ int gl_batcher_run(gl_batcher* b, gl_system* const* systems, const float* const*
     g.work = reinterpret_cast<float*>(base + align256(sizeof(gl::VecConst) * size_t(g.B)));
     g.partial = reinterpret_cast<double*>(base + align256(sizeof(gl::VecConst) * size_t(g.B)) +
                                           align256(sizeof(float) * size_t(g.B) * g.H * g.W));
-    g.tiles_done = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(g.partial) +
-                                          align256(sizeof(double) * size_t(g.B) * g.ntiles * gl::NACC));
     used += need;
     g.loglik = loglik_out[i];
     g.chi2 = chi2_out ? chi2_out[i] : nullptr;

@@ -45,6 +45,7 @@ constexpr int NMAX = 128;            // cap on EPL series terms per vector (a mu
 constexpr int NACC = 24;             // adjoint accumulators per vector
 constexpr float RHO2_MIN = 1e-12f;   // (1e-6 arcsec)^2: EPL deflection zero / Sersic radius floor
 constexpr int RAY_THREADS = 256;     // block size of the ray kernels
+constexpr int FINAL_THREADS = 128;   // block size of k_final (vectors per block)
 
 // Accumulator slots of the adjoint (per vector, before the chain rule).
 enum Acc {
@@ -108,7 +109,6 @@ struct Seg {
   VecConst* vc;            // [B]
   float* work;             // [B, H, W]: binned pre-PSF image, then the subpixel adjoint
   double* partial;         // [B, ntiles, NACC]
-  int* tiles_done;         // [B] ray tiles of the vector finished (k_setup zeroes it)
   // first item of this segment in the launch's item spaces
   int vec_begin;           // per-vector kernels
   int ray_begin;           // ray kernels (B * ntiles items)

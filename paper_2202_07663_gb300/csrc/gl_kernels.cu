@@ -10,9 +10,9 @@
 //              for the gradient also the pixel adjoint d log L / d I_model,
 //              correlated with the PSF and divided by k^2 -> work
 //   k_ray_adj  per (vector, pixel tile): rays recomputed, forward-mode
-//              derivatives contracted with the subpixel adjoint -> partial;
-//              the vector's last tile to finish adds the tile partials in
-//              tile order (FP64) and applies the chain rule -> grad
+//              derivatives contracted with the subpixel adjoint -> partial
+//   k_final    per vector: fixed-order FP64 sum of the tile partials and the
+//              per-vector chain rule -> grad
 // Every kernel loops over its items with a grid stride, so the same code
 // serves one-system launches (one segment passed by value) and grouped
 // launches over many systems (segment table in device memory).
@@ -284,7 +284,6 @@ __global__ void k_setup(const __grid_constant__ Src src) {
     if (lane == 0) {
       V->nterms = ok ? min(n_fwd, NMAX) : -1;
       V->nterms_adj = max(min(n_fwd, NMAX), 1);
-      if (s->tiles_done) s->tiles_done[b] = 0;
     }
   }
 }
@@ -536,33 +535,6 @@ __device__ __forceinline__ void ray_adj(const VecConst& V, const float* an, cons
   acc[A_G2] = fmaT(gx, y, fmaT(gy, x, acc[A_G2]));
 }
 
-// b_n / n of a Sersic index.
-__device__ __forceinline__ double bn_over_n(float n) {
-  const double x = double(n);
-  return (1.9992 * x - 0.3271) / x;
-}
-
-// The per-vector chain rule from the summed accumulators a[NACC] and the
-// parameters pf (FP64 arithmetic): gradient entry j.
-// ms, ml: bn_over_n of the source (pf[16]) and of the lens light (pf[9]).
-__device__ __forceinline__ double chain_rule(int j, const double* a, const float* pf, double ms, double ml) {
-  const double ln2 = 0.69314718055994530942;
-  if (j < 8) return j == 0 ? ms * (double(pf[1]) - 1.0) / double(pf[0]) * a[A_THETAE] : ms * a[A_THETAE + j];
-  const int l = j < 15 ? 0 : 1, k = j - (l == 0 ? 8 : 15);
-  const float* q = pf + (l == 0 ? 8 : 15);
-  const double* c = a + (l == 0 ? A_L_R : A_S_R);
-  const double m = l == 0 ? ml : ms;
-  switch (k) {
-    case 0: return m / double(q[0]) * c[0];
-    case 1: return -1.9992 * c[1] + m * ln2 * c[2];
-    case 2: return -0.5 * m * c[3];
-    case 3: return -0.5 * m * c[4];
-    case 4: return m * c[5];
-    case 5: return m * c[6];
-    default: return c[7];
-  }
-}
-
 // Ray type of the adjoint kernel: float (one ray per thread per step) or F2
 // (two pixels per step, their rays paired in packed f32x2 arithmetic), with
 // its block size and minimum resident blocks.
@@ -586,8 +558,6 @@ __global__ void __launch_bounds__(ADJ_THREADS, GL_ADJ_MINB) k_ray_adj(const __gr
   __shared__ VecConst sv;
   __shared__ Seg ss;
   __shared__ double red[ADJ_THREADS / 32][NACC];
-  __shared__ double sa[NACC];   // the vector's accumulators (its last tile)
-  __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
     int local;
@@ -665,51 +635,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, GL_ADJ_MINB) k_ray_adj(const __gr
       if (lane == 0) red[warp][a] = double(v);
     }
     __syncthreads();
-    // this tile's sums; the vector's last tile to finish adds all tiles' sums in
-    // tile order (the same order for every launch shape) and applies the chain rule
-    const int nt = ss.ntiles;
     if (threadIdx.x < NACC) {
       double v = 0.0;
       for (int w = 0; w < int(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
-      if (nt == 1) {
-        sa[threadIdx.x] = 0.0 + v;
-      } else {
-        ss.partial[(size_t(b) * nt + tile) * NACC + threadIdx.x] = v;
-        __threadfence();   // the partial is visible before this tile is counted
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = nt == 1 || atomicAdd(&ss.tiles_done[b], 1) == nt - 1;
-    __syncthreads();
-    if (s_last) {
-      if (nt > 1) {
-        __threadfence();
-        if (threadIdx.x < NACC) {
-          // eight loads in flight (from L2: other blocks wrote them), added in tile order
-          const double* part = ss.partial + size_t(b) * nt * NACC + threadIdx.x;
-          double a = 0.0;
-          int t = 0;
-          for (; t + 8 <= nt; t += 8) {
-            double v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + size_t(t + u) * NACC);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) a += v[u];
-          }
-          for (; t < nt; ++t) a += __ldcg(part + size_t(t) * NACC);
-          sa[threadIdx.x] = a;
-        }
-        __syncthreads();
-      }
-      if (threadIdx.x < NPARAM) {
-        double* g = ss.grad + size_t(b) * NPARAM;
-        if (sv.nterms < 0) {
-          g[threadIdx.x] = nan("");
-        } else {
-          const float* pf = ss.params + size_t(b) * NPARAM;
-          g[threadIdx.x] = chain_rule(threadIdx.x, sa, pf, bn_over_n(pf[16]), bn_over_n(pf[9]));
-        }
-      }
+      ss.partial[(size_t(b) * ss.ntiles + tile) * NACC + threadIdx.x] = v;
     }
     __syncthreads();
   }
@@ -1118,6 +1047,99 @@ __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src s
   }
 }
 
+// ------------------------------------------------------------- k_final ----
+
+// The per-vector chain rule from the summed accumulators a[NACC] and the
+// parameters p (both FP64): gradient entry j. Shared by the two k_final
+// variants so that they give identical results.
+// b_n / n of a Sersic index.
+__device__ __forceinline__ double bn_over_n(float n) {
+  const double x = double(n);
+  return (1.9992 * x - 0.3271) / x;
+}
+
+// ms, ml: bn_over_n of the source (pf[16]) and of the lens light (pf[9]).
+__device__ __forceinline__ double chain_rule(int j, const double* a, const float* pf, double ms, double ml) {
+  const double ln2 = 0.69314718055994530942;
+  if (j < 8) return j == 0 ? ms * (double(pf[1]) - 1.0) / double(pf[0]) * a[A_THETAE] : ms * a[A_THETAE + j];
+  const int l = j < 15 ? 0 : 1, k = j - (l == 0 ? 8 : 15);
+  const float* q = pf + (l == 0 ? 8 : 15);
+  const double* c = a + (l == 0 ? A_L_R : A_S_R);
+  const double m = l == 0 ? ml : ms;
+  switch (k) {
+    case 0: return m / double(q[0]) * c[0];
+    case 1: return -1.9992 * c[1] + m * ln2 * c[2];
+    case 2: return -0.5 * m * c[3];
+    case 3: return -0.5 * m * c[4];
+    case 4: return m * c[5];
+    case 5: return m * c[6];
+    default: return c[7];
+  }
+}
+
+// One thread per vector (calls whose vectors have one ray tile each).
+template <class Src>
+__global__ void k_final(const __grid_constant__ Src src) {
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < src.nvec(); item += gridDim.x * blockDim.x) {
+    int b;
+    const Seg* s = src.vec_seg(item, b);
+    double* g = s->grad + size_t(b) * NPARAM;
+    if (s->vc[b].nterms < 0) {
+      for (int i = 0; i < NPARAM; ++i) g[i] = nan("");
+      continue;
+    }
+    double a[NACC];
+    for (int i = 0; i < NACC; ++i) a[i] = 0.0;
+    const double* part = s->partial + size_t(b) * s->ntiles * NACC;
+    for (int t = 0; t < s->ntiles; ++t)
+      for (int i = 0; i < NACC; ++i) a[i] += part[t * NACC + i];
+    const float* pf = s->params + size_t(b) * NPARAM;
+    const double ms = bn_over_n(pf[16]), ml = bn_over_n(pf[9]);
+    for (int j = 0; j < NPARAM; ++j) g[j] = chain_rule(j, a, pf, ms, ml);
+  }
+}
+
+// One warp per vector (many tiles per vector, i.e. small batches): lane i <
+// NACC sums accumulator i over the tiles in tile order, lane j < NPARAM
+// applies the chain rule for entry j.
+template <class Src>
+__global__ void k_final_warp(const __grid_constant__ Src src) {
+  __shared__ double sa[FINAL_THREADS / 32][NACC];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int item = blockIdx.x * wpb + w; item < src.nvec(); item += gridDim.x * wpb) {
+    int b;
+    const Seg* s = src.vec_seg(item, b);
+    double* g = s->grad + size_t(b) * NPARAM;
+    if (s->vc[b].nterms < 0) {   // warp-uniform
+      if (lane < NPARAM) g[lane] = nan("");
+      continue;
+    }
+    if (lane < NACC) {
+      // eight loads in flight, then added in tile order (the same sum as k_final)
+      const double* part = s->partial + size_t(b) * s->ntiles * NACC + lane;
+      const int nt = s->ntiles;
+      double acc = 0.0;
+      int t = 0;
+      for (; t + 8 <= nt; t += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = part[size_t(t + u) * NACC];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+      }
+      for (; t < nt; ++t) acc += part[size_t(t) * NACC];
+      sa[w][lane] = acc;
+    }
+    __syncwarp();
+    const float* pf = s->params + size_t(b) * NPARAM;
+    double fac = 0.0;   // lanes 0, 1 compute the two factors once; the others receive them
+    if (lane < 2) fac = bn_over_n(pf[lane == 0 ? 16 : 9]);
+    const double ms = __shfl_sync(0xffffffffu, fac, 0), ml = __shfl_sync(0xffffffffu, fac, 1);
+    if (lane < NPARAM) g[lane] = chain_rule(lane, sa[w], pf, ms, ml);
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------- launch -----
 
 static int g_num_sms = 0;
@@ -1202,15 +1224,19 @@ static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t
 }
 
 template <class Src>
-static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj, cudaStream_t st,
-                            Hooks* hooks, bool persistent, bool fwd_rays = true) {
+static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj_final, cudaStream_t st,
+                            Hooks* hooks, bool persistent, bool one_tile = false, bool fwd_rays = true) {
   const int sms = num_sms();
   cudaError_t e;
   const int vthreads = 128, wpb = vthreads / 32;
   int sgrid = (nvec + wpb - 1) / wpb;
+  int fgrid = (nvec + FINAL_THREADS - 1) / FINAL_THREADS;
+  int wgrid = (nvec + FINAL_THREADS / 32 - 1) / (FINAL_THREADS / 32);
   int rgrid = nray;
   if (persistent) {
     sgrid = sgrid < sms * 4 ? sgrid : sms * 4;
+    fgrid = fgrid < sms ? fgrid : sms;
+    wgrid = wgrid < sms * 4 ? wgrid : sms * 4;
     rgrid = rgrid < sms * 4 ? rgrid : sms * 4;
   }
   if (fwd) {
@@ -1222,10 +1248,16 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
     k_ray_fwd<Src><<<rgrid, FWD_THREADS, 0, st>>>(src);
     return hooks->after(GL_K_RAY_FWD, st);
   }
-  if (adj) {   // the ray adjoint, ending in the per-vector chain rule
+  if (adj_final) {
     hooks->before(GL_K_RAY_ADJ, st);
     k_ray_adj<Src><<<rgrid, ADJ_THREADS, 0, st>>>(src);
-    return hooks->after(GL_K_RAY_ADJ, st);
+    if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
+    hooks->before(GL_K_FINAL, st);
+    if (one_tile)
+      k_final<Src><<<fgrid, FINAL_THREADS, 0, st>>>(src);
+    else
+      k_final_warp<Src><<<wgrid, FINAL_THREADS, 0, st>>>(src);
+    return hooks->after(GL_K_FINAL, st);
   }
   return cudaSuccess;
 }
@@ -1233,7 +1265,7 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
 cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   if (s.B <= 0) return cudaSuccess;
   OneSeg src{s};
-  cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, mode != MODE_CORR);
+  cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false, mode != MODE_CORR);
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_CONV, st);
   const size_t csmem = conv_smem_bytes(s.H, s.W, s.K, s.conv_two_buf != 0);
@@ -1242,13 +1274,13 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD && mode != MODE_CORR) return cudaSuccess;
-  return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false);
+  return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false, s.ntiles == 1);
 }
 
 cudaError_t launch_basis(const Seg& s, cudaStream_t st, Hooks* hooks) {
   if (s.B <= 0) return cudaSuccess;
   OneSeg src{s};
-  cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false);   // setup
+  cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false, false);   // setup
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_RAY_FWD, st);
   k_ray_fwd_basis<OneSeg><<<s.B * s.ntiles, FWD_THREADS, 0, st>>>(src);
@@ -1325,7 +1357,10 @@ cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size
   }
   hooks->before(GL_K_RAY_ADJ, st);
   k_ray_adj<DevTable><<<sms * GL_ADJ_MINB, ADJ_THREADS, 0, st>>>(src);
-  return hooks->after(GL_K_RAY_ADJ, st);
+  if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
+  hooks->before(GL_K_FINAL, st);
+  k_final_warp<DevTable><<<sms * 4, FINAL_THREADS, 0, st>>>(src);
+  return hooks->after(GL_K_FINAL, st);
 }
 
 }  // namespace gl

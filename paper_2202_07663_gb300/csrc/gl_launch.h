@@ -77,6 +77,6 @@ cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size
                             Hooks* hooks);
 
 // Kernels launched by one launch_devtable call.
-constexpr int DEVTABLE_LAUNCHES = 3 + CONV_CLASSES;
+constexpr int DEVTABLE_LAUNCHES = 4 + CONV_CLASSES;
 
 }  // namespace gl

@@ -64,8 +64,7 @@ int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* l
   const size_t vc_bytes = align256(sizeof(gl::VecConst) * size_t(B));
   const size_t work_bytes = align256(sizeof(float) * size_t(B) * g.H * g.W);
   const size_t part_bytes = align256(sizeof(double) * size_t(B) * g.ntiles * gl::NACC);
-  const size_t done_bytes = align256(sizeof(int) * size_t(B));
-  const size_t need = vc_bytes + work_bytes + part_bytes + done_bytes;
+  const size_t need = vc_bytes + work_bytes + part_bytes;
   if (need > kNoAllocScratchBytes) {
     char msg[200];
     snprintf(msg, sizeof(msg), "B = %d needs %zu bytes of static scratch; the limit is %zu bytes", B, need,
@@ -77,13 +76,11 @@ int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* l
   if (rc != GL_OK) return rc;
   unsigned char* p = static_cast<unsigned char*>(base);
   // Every element of these buffers is written before it is read within one
-  // call (setup writes all constants and zeroes the tile counters, the
-  // forward ray kernel every pixel, the adjoint ray kernel every tile
-  // partial), so nothing needs clearing.
+  // call (setup writes all constants, the forward ray kernel every pixel,
+  // the adjoint ray kernel every tile partial), so nothing needs clearing.
   g.vc = reinterpret_cast<gl::VecConst*>(p);
   g.work = reinterpret_cast<float*>(p + vc_bytes);
   g.partial = reinterpret_cast<double*>(p + vc_bytes + work_bytes);
-  g.tiles_done = reinterpret_cast<int*>(p + vc_bytes + work_bytes + part_bytes);
   g.loglik = loglik_out;
   g.chi2 = chi2_out;
   g.grad = grad_out;

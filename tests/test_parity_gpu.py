@@ -238,10 +238,9 @@ def test_full_size_workloads_sampled(abi, workload, nsample):
 
 
 def test_final_kernel_variants_agree_bitwise(abi):
-    """B large enough for one ray tile per vector: the single-system call takes
-    each vector's sums straight from its only tile, the grouped (persistent)
-    call through the same end of the adjoint kernel; both must give the same
-    bits (and match the oracle on a sample)."""
+    """B large enough for one ray tile per vector: the single-system call sums
+    the tiles in one thread per vector, the grouped call in a warp per vector;
+    both must give the same bits (and match the oracle on a sample)."""
     spec = inputs.SystemSpec(16, 16, 1, 3, "gaussian")
     truth, image, psf = make_system(spec, 300)
     params = inputs.draw_perturbed(np.random.default_rng(30), truth, 1400).astype(np.float32)
@@ -278,12 +277,12 @@ def test_high_ellipticity_long_series(abi, f):
                   ll_extra=ll_bound(spec, image, psf, params))
 
 
-def test_tile_counters_reset_between_calls(abi):
-    """Small batches split every vector into many ray tiles; the last tile of a
-    vector to finish applies the chain rule, found by a per-vector counter
-    that the setup kernel zeroes in every call. Calls of other sizes in
+def test_many_tile_paths_agree(abi):
+    """Small batches split every vector into many ray tiles (their partials
+    summed by the per-vector reduction kernel). Calls of other sizes in
     between (single, no-allocation and grouped paths over the same scratch)
-    leave no trace: the same input gives the same bits."""
+    leave no trace, and every path gives the bits of a single call of the
+    same size."""
     spec = inputs.SystemSpec(40, 40, 2, 11, "gaussian")
     truth, image, psf = make_system(spec, 310)
     params = inputs.draw_perturbed(np.random.default_rng(31), truth, 9).astype(np.float32)
