@@ -209,7 +209,7 @@ def synthetic_system(workload: str, device):
     return spec, truth, psf, image
 
 
-def run_hmc_workload(device, iterations: int = 200, chains: int = 512, leapfrog: int = 8):
+def run_hmc_workload(device, iterations: int = 200, chains: int = 512, leapfrog: int = 8, cpu: bool = False):
     """HMC through the adjoint, 100x100 pixels, k = 4, 21x21 Moffat PSF."""
     import torch
     from paper_2202_07663_gb300 import abi, hmc
@@ -222,14 +222,17 @@ def run_hmc_workload(device, iterations: int = 200, chains: int = 512, leapfrog:
     eps = sampler.tune_step_size(rounds=5, iters=2)
     st = sampler.run(iterations)
     s.close()
-    return {"workload": "hmc-100x100-k4-moffat21", "chains": chains, "leapfrog": leapfrog,
-            "iterations": iterations, "grad_evals": st.grad_evals, "seconds": st.seconds,
-            "evals_per_s": st.evals_per_s, "acceptance": st.acceptance, "step_size": eps,
-            "mass": "diagonal, 1/|d2 logL/dq2| at the truth (Laplace)",
-            "log_density": "log L (flat prior), physical parameters"}
+    out = {"workload": "hmc-100x100-k4-moffat21", "chains": chains, "leapfrog": leapfrog,
+           "iterations": iterations, "grad_evals": st.grad_evals, "seconds": st.seconds,
+           "evals_per_s": st.evals_per_s, "acceptance": st.acceptance, "step_size": eps,
+           "mass": "diagonal, 1/|d2 logL/dq2| at the truth (Laplace)",
+           "log_density": "log L (flat prior), physical parameters"}
+    if cpu:
+        out["cpu_oracle"] = oracle_sample(spec, psf, image, q0.cpu().numpy().astype(np.float32))
+    return out
 
 
-def run_stress_workload(device, steps: int = 3):
+def run_stress_workload(device, steps: int = 3, cpu: bool = False):
     """The stress workload: 200x200 pixels, k = 4, 21x21 PSF, B = 16384 vectors per call."""
     import torch
     from paper_2202_07663_gb300 import abi
@@ -259,10 +262,13 @@ def run_stress_workload(device, steps: int = 3):
     rays = spec.H * spec.W * spec.k * spec.k
     adj_tflops = rays * float(flops_ray_adj(N).sum()) / (ms_adj / n_adj * 1e-3) / 1e12
     s.close()
-    return {"workload": "stress-200x200-k4-psf21-B16384", "B": B, "steps": steps, "ms_per_step": ms,
-            "evals_per_s": B / (ms * 1e-3), "k_ray_adj_tflops": adj_tflops,
-            "kernel_ms_per_step": {k: v[1] / steps for k, v in prof.items() if v[0] > 0},
-            "finite": bool(torch.isfinite(ll).all().item() and torch.isfinite(g).all().item())}
+    out = {"workload": "stress-200x200-k4-psf21-B16384", "B": B, "steps": steps, "ms_per_step": ms,
+           "evals_per_s": B / (ms * 1e-3), "k_ray_adj_tflops": adj_tflops,
+           "kernel_ms_per_step": {k: v[1] / steps for k, v in prof.items() if v[0] > 0},
+           "finite": bool(torch.isfinite(ll).all().item() and torch.isfinite(g).all().item())}
+    if cpu:
+        out["cpu_oracle"] = oracle_sample(spec, psf, image, params)
+    return out
 
 
 def run_serving_workload(device, n_latency: int = 200, n_capacity: int = 1000):
@@ -485,6 +491,27 @@ def cpu_baseline(spec, psf, image, params, budget_s: float = 12.0):
             "value_1core": n1 / dt1, "sample_1core": "%d vectors, %.1f s" % (n1, dt1)}
 
 
+def oracle_sample(spec, psf, image, params, budget_s: float = 4.0):
+    """The FP64 oracle (log L + gradient) on all host cores over a bounded
+    sample of a workload's vectors (one per core first, then more if that
+    took well under the budget): evals/s and what the sample was."""
+    import oracle
+    oracle.build()
+    nt = oracle.max_threads()
+    args = (image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k, spec.gain_exposure)
+    n = min(len(params), nt)
+    t = time.perf_counter()
+    oracle.loglik(params[:n].astype(np.float64), *args, grad=True, nthreads=nt)
+    dt = time.perf_counter() - t
+    if dt < budget_s / 3:
+        n = int(min(len(params), max(n, math.floor(n * budget_s / max(dt, 1e-3)))))
+        t = time.perf_counter()
+        oracle.loglik(params[:n].astype(np.float64), *args, grad=True, nthreads=nt)
+        dt = time.perf_counter() - t
+    return {"evals_per_s": n / dt, "cores": nt, "kind": "oracle",
+            "sample": "%d of the workload's vectors (log L + forward-mode gradient, FP64), %.1f s" % (n, dt)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -648,7 +675,8 @@ def main():
         cpu = cpu_baseline(spec, psf, image, params)
     workloads = None
     if world == 1 and not args.no_workloads:
-        workloads = {"hmc": run_hmc_workload(device), "stress": run_stress_workload(device),
+        cpu_w = not args.no_cpu_baseline
+        workloads = {"hmc": run_hmc_workload(device, cpu=cpu_w), "stress": run_stress_workload(device, cpu=cpu_w),
                      "serving": run_serving_workload(device), "map": run_map_workload(device),
                      "hmc_paper": run_hmc_paper_workload(device), "variant": run_variant_workload(device),
                      "pipeline": run_pipeline_workload(device)}
