@@ -1158,7 +1158,7 @@ static int num_sms() {
 struct ConvClass {
   int K, R, NT;
 };
-static constexpr ConvClass kConvClasses[3] = {{11, 16, 128}, {21, 16, 256}, {0, 8, 128}};  // see launch_conv_class
+static constexpr ConvClass kConvClasses[3] = {{11, 16, 256}, {21, 16, 256}, {0, 8, 128}};  // see launch_conv_class
 
 int conv_class(int K) { return K == 11 ? 0 : (K == 21 ? 1 : 2); }
 
@@ -1215,7 +1215,7 @@ static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t
   switch (cls) {
     case 0:
       return wide ? launch_conv<11, 16, 512, 1>(src, nitems, smem, mode, st, persistent)
-                  : launch_conv<11, 16, 128, 5>(src, nitems, smem, mode, st, persistent);
+                  : launch_conv<11, 16, 256, 3>(src, nitems, smem, mode, st, persistent);
     case 1:
       return wide ? launch_conv<21, 16, 512, 1>(src, nitems, smem, mode, st, persistent)
                   : launch_conv<21, 16, 256, 1>(src, nitems, smem, mode, st, persistent);
@@ -1329,7 +1329,7 @@ static cudaError_t set_devtable_attr(size_t smem) {
 cudaError_t prepare_devtable(const size_t* conv_smem) {
   cudaError_t e;
   e = conv_smem[0] > CONV_WIDE_MIN_SMEM ? set_devtable_attr<11, 16, 512, 1>(conv_smem[0])
-                                        : set_devtable_attr<11, 16, 128, 5>(conv_smem[0]);
+                                        : set_devtable_attr<11, 16, 256, 3>(conv_smem[0]);
   if (e != cudaSuccess) return e;
   e = conv_smem[1] > CONV_WIDE_MIN_SMEM ? set_devtable_attr<21, 16, 512, 1>(conv_smem[1])
                                         : set_devtable_attr<21, 16, 256, 1>(conv_smem[1]);
