@@ -1178,7 +1178,7 @@ bool conv_two_buf(int H, int W, int K) { return conv_smem_bytes(H, W, K, true) <
 void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix) {
   const int HW = H * W;
   const long long rays = (long long)HW * k * k;
-  const int target = num_sms() * 8;   // 4 and 16 measured slower (80x80, B = 300: 185, 198 vs 180 us)
+  const int target = num_sms() * 8;
   long long nt = B > 0 ? (target + B - 1) / B : 1;
   const long long by_work = (rays + RAY_THREADS * 8 - 1) / (RAY_THREADS * 8);  // >= 8 rays per thread
   if (nt > by_work) nt = by_work;
