@@ -698,7 +698,7 @@ def main():
                      "mufu": {"achieved": mufu_achieved, "peak": mufu_peak, "unit": "Gop/s",
                               "frac": mufu_achieved / mufu_peak, "ops_per_ray": MUFU_RAY_ADJ,
                               "peak_basis": "%d SMs x 32 MUFU/clk (measured ex2 probe) x %.0f MHz" % (sms, sm_mhz)},
-                     "mean_series_terms": float(N.mean())},
+                     "mean_series_terms": float(N.mean()), "kernel_source": th},
         "kernels": kern,
         "cpu_baseline": cpu,
         "workloads": workloads,
