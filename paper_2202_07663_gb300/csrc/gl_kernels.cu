@@ -16,6 +16,7 @@
 // Every kernel loops over its items with a grid stride, so the same code
 // serves one-system launches (one segment passed by value) and grouped
 // launches over many systems (segment table in device memory).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -834,6 +835,23 @@ __device__ void conv_vector(const Seg& s, int b, int mode, float* smem, double* 
   }
 }
 
+// Likelihood terms of pixel p with model value M (Eq. for log L with the
+// model-dependent variance): adds chi^2 and chi^2 + log(2 pi v) to c2 and ll
+// and returns d log L / d M. Explicit roundings: the log-L-only and gradient
+// calls give identical sums. 1/v and log(2 pi v) by the hardware
+// approximations (relative error ~1e-7, far below the likelihood's FP32
+// summation error).
+__device__ __forceinline__ float pixel_terms(const Seg& s, int p, float M, float& ll, float& c2) {
+  const float v = fmaf(M, s.inv_gain, s.sigma2[p]);
+  const float res = __fsub_rn(s.image[p], M);
+  const float iv = rcp(v);
+  const float t2 = __fmul_rn(__fmul_rn(res, res), iv);
+  c2 = __fadd_rn(c2, t2);
+  ll = __fadd_rn(ll, __fadd_rn(t2, __fmul_rn(0.69314718055994531f, lg2(__fmul_rn(6.28318530717958648f, v)))));
+  // d log L / d M = res/v + (res^2/v^2 - 1/v) / (2 G t_exp)
+  return fmaf(0.5f * s.inv_gain, fmaf(t2, iv, -iv), res * iv);
+}
+
 // ---- row-strip convolution for the compile-time PSF sides (11, 21) ----
 //
 // Each thread computes S = 16 consecutive outputs of one image row; the lanes
@@ -966,19 +984,8 @@ __device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, dou
       s.sim[size_t(b) * HW + p] = M;
       continue;
     }
-    // explicit roundings: the log-L-only and gradient calls give identical sums.
-    // 1/v and log(2 pi v) by the hardware approximations (relative error ~1e-7,
-    // far below the likelihood's FP32 summation error)
-    const float v = fmaf(M, s.inv_gain, s.sigma2[p]);
-    const float res = __fsub_rn(s.image[p], M);
-    const float iv = rcp(v);
-    const float t2 = __fmul_rn(__fmul_rn(res, res), iv);
-    c2 = __fadd_rn(c2, t2);
-    ll = __fadd_rn(ll, __fadd_rn(t2, __fmul_rn(0.69314718055994531f, lg2(__fmul_rn(6.28318530717958648f, v)))));
-    if (want_grad) {
-      // d log L / d M = res/v + (res^2/v^2 - 1/v) / (2 G t_exp)
-      img[(i + c) * P + j + c] = fmaf(0.5f * s.inv_gain, fmaf(t2, iv, -iv), res * iv);
-    }
+    const float gm = pixel_terms(s, p, M, ll, c2);
+    if (want_grad) img[(i + c) * P + j + c] = gm;
   }
   if (!want_sim) {
     // FP32 within a thread (a few tens of pixels) and a warp (pairwise), FP64 across
@@ -1045,6 +1052,154 @@ __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src s
     }
     __syncthreads();
   }
+}
+
+// ---- small batches: one vector's convolution over a cluster of row bands ----
+//
+// Below half as many vectors as SMs, one block per vector leaves most SMs
+// idle. Here a thread-block cluster of nb blocks shares a vector: block r
+// convolves output rows [r rows, (r + 1) rows) from its band and the K - 1
+// halo rows of the binned image (global memory), evaluates the likelihood
+// terms of its rows and keeps their d log L / d M in shared memory. After a
+// cluster barrier each block copies the d log L / d M halo rows it needs out
+// of its neighbours' shared memory (distributed shared memory) and block 0
+// adds the bands' log L and chi^2 in rank order; after a second barrier (no
+// block reads another's shared memory beyond it) each block correlates its
+// rows with the PSF. Per pixel the arithmetic is that of conv_vector_rows,
+// so gradients are the same bits; log L is summed in a band-dependent order.
+constexpr int BAND_THREADS = 256;
+
+__host__ __device__ inline size_t conv_band_smem_bytes(int W, int K, int rows) {
+  const size_t KP = size_t((K + 3) & ~3), P = size_t(rowconv_pitch(W, K));
+  return (2 * size_t(K) * KP + (size_t(rows) + K - 1) * P + size_t(rows) * P) * sizeof(float);
+}
+
+template <int K>
+__global__ void __launch_bounds__(BAND_THREADS) k_conv_bands(const __grid_constant__ OneSeg src, int mode, int rows) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  __shared__ double red2[2 * (BAND_THREADS / 32)];
+  __shared__ double band_sum[2];
+  constexpr int S = 16, KP = (K + 3) & ~3, c = (K - 1) / 2;
+  const Seg& s = src.s;
+  const int nb = int(cluster.num_blocks()), rank = int(cluster.block_rank());
+  const int b = blockIdx.x / nb;
+  const int H = s.H, W = s.W, HW = H * W;
+  const int P = rowconv_pitch(W, K);
+  const int r0 = min(H, rank * rows), nr = min(H, r0 + rows) - r0;   // nr may be 0
+  const int Hb = rows + K - 1;
+  float* kerF = smem;
+  float* kerU = smem + K * KP;
+  float* img = smem + 2 * K * KP;   // [Hb][P], local row li holds image row r0 - c + li
+  float* stage = img + Hb * P;      // [rows][P]
+  float* work = s.work + size_t(b) * HW;
+  const bool want_sim = (mode == MODE_SIM);
+  const bool want_grad = (mode == MODE_GRAD);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+  for (int i = threadIdx.x; i < K * KP; i += blockDim.x) {
+    const int a = i / KP, bb = i - a * KP;
+    kerF[i] = bb < K ? s.psf[(K - 1 - a) * K + (K - 1 - bb)] : 0.f;
+    kerU[i] = bb < K ? s.psf[a * K + bb] : 0.f;
+  }
+  for (int li = wid; li < Hb; li += nw) {
+    const int g = r0 - c + li;
+    float* row = img + li * P;
+    if (g >= 0 && g < H) {
+      for (int j = lane; j < W; j += 32) cp_async4(&row[j + c], &work[g * W + j]);
+      for (int q = lane; q < P - W; q += 32) row[q < c ? q : W + q] = 0.f;
+    } else {
+      for (int j = lane; j < P; j += 32) row[j] = 0.f;
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // pass 1: M of this band's rows
+  const int nstrip = (W + S - 1) / S;
+  const int units = nstrip * nr;
+  float acc[S];
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int strip = u / nr, li = u - strip * nr, j0 = strip * S;
+    corr_row<K>(img, P, kerF, li, j0, acc);
+    float4* o4 = reinterpret_cast<float4*>(stage + li * P + j0);
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q) o4[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+  }
+  __syncthreads();
+
+  // pixel phase of the band: likelihood terms, d log L / d M into img's interior
+  float ll = 0.f, c2 = 0.f;
+  for (int li = wid; li < nr; li += nw)
+#pragma unroll 2
+    for (int j = lane; j < W; j += 32) {
+      const int p = (r0 + li) * W + j;
+      const float M = stage[li * P + j];
+      if (want_sim) {
+        s.sim[size_t(b) * HW + p] = M;
+        continue;
+      }
+      const float gm = pixel_terms(s, p, M, ll, c2);
+      if (want_grad) img[(li + c) * P + j + c] = gm;
+    }
+  ll = warp_sum_f(ll);
+  c2 = warp_sum_f(c2);
+  if (lane == 0) {
+    red2[2 * wid] = double(ll);
+    red2[2 * wid + 1] = double(c2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double L = 0.0, C = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      L += red2[2 * w];
+      C += red2[2 * w + 1];
+    }
+    band_sum[0] = L;
+    band_sum[1] = C;
+  }
+  cluster.sync();   // every band's d log L / d M and sums are in its shared memory
+  if (!want_sim && rank == 0 && threadIdx.x == 0) {
+    double L = 0.0, C = 0.0;
+    for (int r = 0; r < nb; ++r) {
+      const double* bs = cluster.map_shared_rank(band_sum, r);
+      L += bs[0];
+      C += bs[1];
+    }
+    if (s.loglik) s.loglik[b] = -0.5 * L;
+    if (s.chi2) s.chi2[b] = C;
+  }
+  if (want_grad) {
+    // the halo rows of d log L / d M from the bands that own them
+    for (int li = wid; li < Hb; li += nw) {
+      if (li >= c && li < c + nr) continue;
+      const int g = r0 - c + li;
+      if (g < 0 || g >= H) continue;   // stays zero
+      const int owner = g / rows;
+      const float* oimg = cluster.map_shared_rank(img, owner);
+      const float* orow = oimg + (g - owner * rows + c) * P + c;
+      for (int j = lane; j < W; j += 32) img[li * P + j + c] = orow[j];
+    }
+  }
+  cluster.sync();   // no block reads another's shared memory after this barrier
+  if (!want_grad) return;
+
+  // pass 2: subpixel adjoint of the band's rows = (PSF correlated with d log L / d M) / k^2
+  const float inv_k2 = 1.0f / float(s.k * s.k);
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int strip = u / nr, li = u - strip * nr, j0 = strip * S;
+    corr_row<K>(img, P, kerU, li, j0, acc);
+    float4* o4 = reinterpret_cast<float4*>(stage + li * P + j0);
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q)
+      o4[q] = make_float4(acc[4 * q] * inv_k2, acc[4 * q + 1] * inv_k2, acc[4 * q + 2] * inv_k2,
+                          acc[4 * q + 3] * inv_k2);
+  }
+  __syncthreads();
+  for (int li = wid; li < nr; li += nw)
+    for (int j = lane; j < W; j += 32) work[(r0 + li) * W + j] = stage[li * P + j];
 }
 
 // ------------------------------------------------------------- k_final ----
@@ -1223,6 +1378,45 @@ static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t
   }
 }
 
+// Row bands for the cluster convolution of a B-vector call (0: one block per
+// vector instead). Bands only below half as many vectors as SMs, at most 8 per
+// vector (a portable cluster), each at least max(16, (K - 1) / 2) rows and
+// within CONV_TWO_BUF_MAX_SMEM of shared memory.
+static int conv_bands(int B, int H, int W, int K) {
+  if ((K != 11 && K != 21) || B < 1 || 2 * B > num_sms()) return 0;
+  int nb = num_sms() / B;
+  if (nb > 8) nb = 8;
+  const int min_rows = (K - 1) / 2 > 16 ? (K - 1) / 2 : 16;
+  while (nb > 1 && (H + nb - 1) / nb < min_rows) --nb;
+  if (nb < 2 || conv_band_smem_bytes(W, K, (H + nb - 1) / nb) > CONV_TWO_BUF_MAX_SMEM) return 0;
+  return nb;
+}
+
+template <int K>
+static cudaError_t launch_conv_bands(const OneSeg& src, int nb, int mode, cudaStream_t st) {
+  static size_t attr = 48 * 1024;
+  const int rows = (src.s.H + nb - 1) / nb;
+  const size_t smem = conv_band_smem_bytes(src.s.W, K, rows);
+  if (smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_bands<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(src.s.B) * unsigned(nb));
+  cfg.blockDim = dim3(BAND_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = unsigned(nb);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_conv_bands<K>, src, mode, rows);
+}
+
 template <class Src>
 static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj_final, cudaStream_t st,
                             Hooks* hooks, bool persistent, bool one_tile = false, bool fwd_rays = true) {
@@ -1269,8 +1463,12 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_CONV, st);
   const size_t csmem = conv_smem_bytes(s.H, s.W, s.K, s.conv_two_buf != 0);
-  e = launch_conv_class(conv_class(s.K), src, s.B, csmem, mode, st, false,
-                        s.B < num_sms() || csmem > CONV_WIDE_MIN_SMEM);
+  const int nb = mode == MODE_CORR ? 0 : conv_bands(s.B, s.H, s.W, s.K);
+  if (nb > 0)
+    e = s.K == 11 ? launch_conv_bands<11>(src, nb, mode, st) : launch_conv_bands<21>(src, nb, mode, st);
+  else
+    e = launch_conv_class(conv_class(s.K), src, s.B, csmem, mode, st, false,
+                          s.B < num_sms() || csmem > CONV_WIDE_MIN_SMEM);
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD && mode != MODE_CORR) return cudaSuccess;
