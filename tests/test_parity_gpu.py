@@ -81,7 +81,8 @@ def test_simulate_matches_oracle(abi):
 
 @pytest.mark.parametrize("H,W,k,K,B", [
     (1, 1, 1, 1, 1), (2, 3, 1, 3, 2), (3, 3, 2, 3, 3), (5, 7, 3, 5, 1), (17, 13, 2, 3, 5),
-    (33, 31, 1, 11, 3), (45, 64, 3, 21, 2), (16, 16, 4, 9, 4), (61, 59, 2, 11, 7)])
+    (33, 31, 1, 11, 3), (45, 64, 3, 21, 2), (16, 16, 4, 9, 4), (61, 59, 2, 11, 7),
+    (100, 90, 1, 21, 4), (80, 80, 2, 11, 1)])
 def test_shapes_and_ragged_tiles(abi, H, W, k, K, B):
     spec = inputs.SystemSpec(H, W, k, K, "gaussian")
     truth, image, psf = make_system(spec, 100 + H * W + k + K)
