@@ -21,6 +21,8 @@
 
 #include <cmath>
 #include <cstdint>
+#include <atomic>
+#include <mutex>
 #include <type_traits>
 
 #include "gl_device.cuh"
@@ -1297,16 +1299,22 @@ __global__ void k_final_warp(const __grid_constant__ Src src) {
 
 // ------------------------------------------------------------- launch -----
 
-static int g_num_sms = 0;
+// Guards the cached dynamic shared-memory limits of the launch helpers: a
+// thread must not launch on a limit another thread has recorded but not yet set.
+static std::mutex g_attr_mutex;
+
+static std::atomic<int> g_num_sms{0};
 
 static int num_sms() {
-  if (g_num_sms == 0) {
+  int n = g_num_sms.load(std::memory_order_relaxed);
+  if (n == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+    g_num_sms.store(n, std::memory_order_relaxed);
   }
-  return g_num_sms;
+  return n;
 }
 
 // Convolution classes: (PSF side, strip rows, threads). Class 2 takes any odd side.
@@ -1347,11 +1355,14 @@ void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix) {
 template <int K, int R, int NT, int MINB, class Src>
 static cudaError_t launch_conv(const Src& src, int nitems, size_t smem, int mode, cudaStream_t st, bool persistent) {
   static size_t attr = 48 * 1024;
-  if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv<K, R, NT, MINB, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-    if (e != cudaSuccess) return e;
-    attr = smem;
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (smem > attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_conv<K, R, NT, MINB, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(smem));
+      if (e != cudaSuccess) return e;
+      attr = smem;
+    }
   }
   int grid = nitems;
   if (persistent) grid = grid < num_sms() * 4 ? grid : num_sms() * 4;
@@ -1397,10 +1408,13 @@ static cudaError_t launch_conv_bands(const OneSeg& src, int nb, int mode, cudaSt
   static size_t attr = 48 * 1024;
   const int rows = (src.s.H + nb - 1) / nb;
   const size_t smem = conv_band_smem_bytes(src.s.W, K, rows);
-  if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_bands<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    attr = smem;
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (smem > attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_conv_bands<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+      attr = smem;
+    }
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(src.s.B) * unsigned(nb));
