@@ -553,6 +553,46 @@ def run_reference(args):
     return 0
 
 
+def run_small_batch(args, B: int = 50):
+    """The call the samplers make (50 chains, Table 1): per-call time of
+    log L + gradient for B vectors of one 80x80 system (k = 2, 11x11 PSF,
+    the paper's noise), inputs resident, CUDA events around K calls."""
+    import torch
+    from paper_2202_07663_gb300 import abi, build
+    build.build()
+    device = torch.device("cuda", 0)
+    spec = inputs.PAPER_SAMPLE_SPEC
+    rng = np.random.default_rng(50)
+    truth = inputs.draw_table(rng, inputs.PAPER_SIM, 1)[0]
+    psf = inputs.make_psf(spec).astype(np.float32)
+    blank = np.zeros((spec.H, spec.W), np.float32)
+    s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
+    s0.close()
+    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    s.reserve(B)
+    p = torch.from_numpy(inputs.draw_perturbed(np.random.default_rng(51), truth, B, frac=0.01)
+                         .astype(np.float32)).to(device)
+    ll = torch.empty(B, dtype=torch.float64, device=device)
+    g = torch.empty(B, 22, dtype=torch.float64, device=device)
+    for _ in range(args.warmup):
+        s.loglik_grad(p, out=(ll, g, None))
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        s.loglik_grad(p, out=(ll, g, None))
+    e.record()
+    torch.cuda.synchronize()
+    us = 1e3 * a.elapsed_time(e) / args.steps
+    s.close()
+    print(json.dumps({"workload": "small-batch-80x80-k2-psf11-B50", "B": B, "steps": args.steps,
+                      "us_per_call": us, "evals_per_s": B / (us * 1e-6),
+                      "finite": bool(torch.isfinite(ll).all().item() and torch.isfinite(g).all().item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,11 +602,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the HMC (100x100, k=4), stress (200x200, B=16384) and serving runs reported beside the metric")
+    ap.add_argument("--small-batch", action="store_true",
+                    help="only the sampler-sized call: B = 50 vectors of an 80x80, k = 2, 11x11-PSF system")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.small_batch:
+        return run_small_batch(args)
 
     import torch
     import torch.distributed as dist
