@@ -89,7 +89,10 @@ def test_shapes_and_ragged_tiles(abi, H, W, k, K, B):
     params = inputs.draw_perturbed(np.random.default_rng(H + W), truth, B).astype(np.float32)
     ll, g = _gpu(abi, spec, image, psf, params)
     rl, _, rg = oracle_eval(spec, image, psf, params)
-    assert_parity(ll, g, rl, rg, "%dx%d k=%d K=%d" % (H, W, k, K), ll_extra=ll_bound(spec, image, psf, params))
+    # the conditioned FP32 bound covers near-cancelling gradient entries (at
+    # 80x80 the lens-light centre: |dg| 32 against eps * C_i = 436)
+    assert_parity(ll, g, rl, rg, "%dx%d k=%d K=%d" % (H, W, k, K), extra=conditioned_bound(spec, image, psf, params),
+                  ll_extra=ll_bound(spec, image, psf, params))
 
 
 def test_no_poisson_term_and_pixel_noise_map(abi):
