@@ -321,3 +321,24 @@ def test_many_tile_paths_agree(abi):
     rl, _, rg = oracle_eval(spec, image, psf, params[idx])
     assert_parity(ref[0][idx], ref[1][idx], rl, rg, "many tiles per vector",
                   ll_extra=ll_bound(spec, image, psf, params[idx]))
+
+
+@pytest.mark.parametrize("H,W,k,K,B", [(80, 80, 2, 11, 1), (61, 59, 2, 11, 7), (100, 90, 1, 21, 4), (64, 40, 2, 21, 30)])
+def test_banded_convolution_equals_one_block(abi, H, W, k, K, B):
+    """Below half as many vectors as SMs a single call convolves each vector
+    on a cluster of row bands (halo rows through distributed shared memory);
+    a grouped call convolves it in one block. Per pixel the arithmetic is the
+    same, so the gradients must be the same bits (log L only sums in another
+    order)."""
+    spec = inputs.SystemSpec(H, W, k, K, "gaussian")
+    truth, image, psf = make_system(spec, 500 + H * W + K)
+    params = inputs.draw_perturbed(np.random.default_rng(H * W), truth, B).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    p = torch.from_numpy(params).cuda()
+    ll1, g1 = (t.cpu().numpy() for t in s.loglik_grad(p))
+    lls, grads, _ = abi.loglik_grad_grouped([s], [p])
+    sim1 = s.simulate(p).cpu().numpy()
+    s.close()
+    np.testing.assert_array_equal(grads[0].cpu().numpy(), g1)
+    np.testing.assert_allclose(lls[0].cpu().numpy(), ll1, rtol=1e-6, atol=0)
+    assert np.all(np.isfinite(sim1))
