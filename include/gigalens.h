@@ -345,6 +345,28 @@ int gl_hmc_chees(int B, int d, const double* q_prev, const double* q_prop, const
                  const double* inv_mass, const double* accept_prob, double t, double* out, void* stream);
 
 /*
+ * The whitened posterior in two calls (the HMC preconditioning of Sec. 2.5 on
+ * the posterior of the unconstrained parameters, Eq. reparam-post), one
+ * warp per chain, d = 22:
+ * gl_posterior_whitened_transform - z_out = mu + L x (L lower triangular,
+ *   row-major 22 x 22 float64; the sums of gl_hmc_affine) and
+ *   theta_out = (float) g(z) (the bijectors of gl_map_transform);
+ * gl_posterior_whitened_grad - logp_out = loglik + log p(g(z)) + log|J| and,
+ *   with grad_theta (d log L / d theta at theta), grad_x_out = L^T grad_z
+ *   (gl_posterior_grad followed by gl_hmc_affine_pullback: the same sums).
+ * Between them the caller evaluates log L and its gradient at theta_out.
+ * Device pointers: x, z_out [B, 22] float64; theta_out [B, 22] float32;
+ * loglik, logp_out [B]; grad_theta, grad_x_out [B, 22]; mu [22]. Outputs must
+ * not alias inputs; GL_ERR_INVALID_ARG for a bad prior table, B < 0 or a
+ * null pointer.
+ */
+int gl_posterior_whitened_transform(int B, const double* x, const double* mu, const double* L,
+                                    const gl_prior_entry* prior, double* z_out, float* theta_out, void* stream);
+int gl_posterior_whitened_grad(int B, const double* z, const double* loglik, const double* grad_theta,
+                               const double* L, const gl_prior_entry* prior, double* logp_out, double* grad_x_out,
+                               void* stream);
+
+/*
  * Dense preconditioning (Sec. 2.5: the mass matrix set to the inverse of a
  * posterior covariance Sigma = L L^T, e.g. the variational one). HMC with
  * identity mass on whitened coordinates x is HMC with mass Sigma^-1 on

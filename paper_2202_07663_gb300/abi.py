@@ -67,6 +67,8 @@ SIGNATURES = {
     "gl_vi_moments": ([_i, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp], _i),
     "gl_vi_apply": ([_i, _i, _i, _vp, _i, _vp, _vp, _vp, _i, _d, _d, _d, _d, _vp, _vp, _vp], _i),
     "gl_posterior_grad": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "gl_posterior_whitened_transform": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "gl_posterior_whitened_grad": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_error_string": ([_i], ctypes.c_char_p),
     "gl_last_error_message": ([], ctypes.c_char_p),
     "gl_profile_enable": ([_i], _i),

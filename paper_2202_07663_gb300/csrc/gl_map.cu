@@ -93,6 +93,70 @@ __global__ void k_posterior(int B, const double* __restrict__ z, const double* _
   }
 }
 
+// The whitened posterior of the HMC preconditioning (Sec. 2.5), z = mu + L x
+// with L lower triangular: one warp per chain, lane i for parameter i.
+// k_whitened_transform forms z (the sums of gl_hmc_affine) and theta = g(z);
+// k_whitened_posterior forms log p~(z) and its gradient in z (as k_posterior)
+// and pulls the gradient back to x, grad_x = L^T grad_z (the sums of
+// gl_hmc_affine_pullback). Two launches per evaluation instead of four.
+constexpr int kWhitenedThreads = 128;
+
+__global__ void __launch_bounds__(kWhitenedThreads) k_whitened_transform(int B, const double* __restrict__ x,
+                                                                         const double* __restrict__ mu,
+                                                                         const double* __restrict__ Lc,
+                                                                         double* __restrict__ z,
+                                                                         float* __restrict__ theta, PriorTable P) {
+  constexpr int D = GL_NPARAM;
+  __shared__ double sL[D * D];
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = Lc[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb) {
+    if (lane >= D) continue;
+    const double* xb = x + size_t(b) * D;
+    double acc = mu[lane];
+    for (int j = 0; j <= lane; ++j) acc += sL[lane * D + j] * xb[j];
+    z[size_t(b) * D + lane] = acc;
+    double th, d, lj, dlj;
+    bij(P.e[lane], acc, th, d, lj, dlj);
+    theta[size_t(b) * D + lane] = float(th);
+  }
+}
+
+__global__ void __launch_bounds__(kWhitenedThreads) k_whitened_posterior(int B, const double* __restrict__ z,
+                                                                         const double* __restrict__ loglik,
+                                                                         const double* __restrict__ grad,
+                                                                         const double* __restrict__ Lc,
+                                                                         double* __restrict__ logp_out,
+                                                                         double* __restrict__ grad_x, PriorTable P) {
+  constexpr int D = GL_NPARAM;
+  __shared__ double sL[D * D];
+  __shared__ double sg[kWhitenedThreads / 32][32];
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = Lc[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + w; b < B; b += gridDim.x * wpb) {
+    const size_t i = size_t(b) * D + lane;
+    double part = 0.0;
+    if (lane < D) {
+      double th, d, lj, dlj, lp, dlp;
+      bij(P.e[lane], z[i], th, d, lj, dlj);
+      logpdf(P.e[lane], th, lp, dlp);
+      part = lp + lj;
+      if (grad) sg[w][lane] = (grad[i] + dlp) * d + dlj;
+    }
+    const double tot = warp_sum(part);
+    if (lane == 0) logp_out[b] = loglik[b] + tot;
+    __syncwarp();
+    if (grad && lane < D) {
+      double acc = 0.0;
+      for (int r = lane; r < D; ++r) acc += sL[r * D + lane] * sg[w][r];
+      grad_x[i] = acc;
+    }
+    __syncwarp();
+  }
+}
+
 int grid_for(int B) {
   const int g = (B + 3) / 4;
   return g < 1 ? 1 : (g > 4096 ? 4096 : g);
@@ -165,6 +229,40 @@ int gl_posterior_grad(int B, const double* z, const double* loglik, const double
   gl_internal::hooks()->before(GL_K_OTHER, st);
   k_posterior<<<grid_for(B), 128, 0, st>>>(B, z, loglik, grad_theta, logp_out, grad_z_out, P);
   return finish(st, "k_posterior");
+}
+
+int gl_posterior_whitened_transform(int B, const double* x, const double* mu, const double* L,
+                                    const gl_prior_entry* prior, double* z_out, float* theta_out, void* stream) {
+  PriorTable P;
+  int rc = load_table(prior, P);
+  if (rc != GL_OK) return rc;
+  if (B < 0) return gl_internal::set_error(GL_ERR_INVALID_ARG, "B < 0");
+  if (B == 0) return GL_OK;
+  if (!x || !mu || !L || !z_out || !theta_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if (z_out == x) return gl_internal::set_error(GL_ERR_INVALID_ARG, "z_out and x alias");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gl_internal::hooks()->before(GL_K_OTHER, st);
+  k_whitened_transform<<<grid_for(B), kWhitenedThreads, 0, st>>>(B, x, mu, L, z_out, theta_out, P);
+  return finish(st, "k_whitened_transform");
+}
+
+int gl_posterior_whitened_grad(int B, const double* z, const double* loglik, const double* grad_theta,
+                               const double* L, const gl_prior_entry* prior, double* logp_out, double* grad_x_out,
+                               void* stream) {
+  PriorTable P;
+  int rc = load_table(prior, P);
+  if (rc != GL_OK) return rc;
+  if (B < 0) return gl_internal::set_error(GL_ERR_INVALID_ARG, "B < 0");
+  if (B == 0) return GL_OK;
+  if (!z || !loglik || !L || !logp_out || (grad_theta && !grad_x_out))
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if (grad_theta && grad_x_out == grad_theta)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "grad_x_out and grad_theta alias");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gl_internal::hooks()->before(GL_K_OTHER, st);
+  k_whitened_posterior<<<grid_for(B), kWhitenedThreads, 0, st>>>(B, z, loglik, grad_theta, L, logp_out, grad_x_out,
+                                                                   P);
+  return finish(st, "k_whitened_posterior");
 }
 
 }  // extern "C"

@@ -148,13 +148,33 @@ class WhitenedTarget:
             dev = q64.device
             self._buf = (torch.empty(B, d, dtype=torch.float64, device=dev),
                          torch.empty(B, d, dtype=torch.float32, device=dev),
-                         torch.empty(B, d, dtype=torch.float64, device=dev))
-        z, z32, gz = self._buf
+                         torch.empty(B, d, dtype=torch.float64, device=dev),
+                         torch.empty(B, dtype=torch.float64, device=dev))
+        z, z32, gz, ll = self._buf
         st = torch.cuda.current_stream(q64.device).cuda_stream
+        if isinstance(self.inner, PosteriorTarget) and d == NPARAM:
+            # the lens posterior: whitening and bijectors in one launch, the
+            # posterior gradient and its pull-back in another (same sums)
+            lib = abi.lib_handle()
+            pp = ctypes.addressof(self.inner.prior)
+            abi._check(lib.gl_posterior_whitened_transform(B, q64.data_ptr(), self.mu.data_ptr(), self.L.data_ptr(),
+                                                           pp, z.data_ptr(), z32.data_ptr(), st),
+                       "gl_posterior_whitened_transform")
+            if g_out is None:
+                self.inner.system.loglik(z32, out=ll)
+            else:
+                self.inner.system.loglik_grad(z32, out=(ll, gz, None))
+            abi._check(lib.gl_posterior_whitened_grad(B, z.data_ptr(), ll.data_ptr(),
+                                                      gz.data_ptr() if g_out is not None else None,
+                                                      self.L.data_ptr(), pp, lp_out.data_ptr(),
+                                                      g_out.data_ptr() if g_out is not None else None, st),
+                       "gl_posterior_whitened_grad")
+            return
         abi.gl_hmc_affine(B, d, q64.data_ptr(), self.mu.data_ptr(), self.L.data_ptr(), z.data_ptr(),
                           z32.data_ptr() if self.inner.needs_q32 else None, st)
-        self.inner(z, z32, lp_out, gz)
-        abi.gl_hmc_affine_pullback(B, d, gz.data_ptr(), self.L.data_ptr(), g_out.data_ptr(), st)
+        self.inner(z, z32, lp_out, gz if g_out is not None else None)
+        if g_out is not None:
+            abi.gl_hmc_affine_pullback(B, d, gz.data_ptr(), self.L.data_ptr(), g_out.data_ptr(), st)
 
 
 def laplace_inv_mass(system, q: torch.Tensor, rel_step: float = 1e-3, floor: float = 1e-12) -> torch.Tensor:

@@ -225,3 +225,40 @@ def test_graph_replay_matches_eager(mods):
     assert runs[0].step_size == runs[1].step_size
     assert runs[0].trajectory_length == runs[1].trajectory_length
     assert torch.equal(runs[0].samples, runs[1].samples)
+
+
+def test_fused_whitened_posterior_equals_the_four_calls(mods):
+    """The whitened lens posterior in two launches (whitening + bijectors,
+    posterior gradient + pull-back) gives the bits of gl_hmc_affine,
+    gl_map_transform, gl_posterior_grad and gl_hmc_affine_pullback."""
+    abi, hmc, gmap = mods
+    spec, truth, psf, image = _paper_system(40, 9)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    post = hmc.PosteriorTarget(s)
+    z0 = torch.from_numpy(mo.inverse_bijector(truth)[0]).cuda()
+    g = torch.Generator(device="cuda").manual_seed(11)
+    A = torch.randn(22, 22, dtype=torch.float64, device="cuda", generator=g) * 0.01
+    L = torch.tril(A) + torch.diag(torch.full((22,), 0.02, dtype=torch.float64, device="cuda"))
+    target = hmc.WhitenedTarget(post, z0, L)
+    B = 37
+    x = torch.randn(B, 22, dtype=torch.float64, device="cuda", generator=g)
+    lp1 = torch.empty(B, dtype=torch.float64, device="cuda")
+    g1 = torch.empty(B, 22, dtype=torch.float64, device="cuda")
+    target(x, None, lp1, g1)
+    lp0 = torch.empty_like(lp1)
+    target(x, None, lp0, None)
+    st = torch.cuda.current_stream().cuda_stream
+    z = torch.empty(B, 22, dtype=torch.float64, device="cuda")
+    gz = torch.empty(B, 22, dtype=torch.float64, device="cuda")
+    lp2 = torch.empty_like(lp1)
+    g2 = torch.empty_like(g1)
+    abi.gl_hmc_affine(B, 22, x.data_ptr(), target.mu.data_ptr(), target.L.data_ptr(), z.data_ptr(), None, st)
+    post(z, None, lp2, gz)
+    abi.gl_hmc_affine_pullback(B, 22, gz.data_ptr(), target.L.data_ptr(), g2.data_ptr(), st)
+    lp3 = torch.empty_like(lp1)
+    post(z, None, lp3, None)
+    torch.cuda.synchronize()
+    s.close()
+    assert torch.equal(lp1, lp2) and torch.equal(g1, g2)
+    assert torch.equal(lp0, lp3)
+    assert torch.isfinite(lp1).all() and torch.isfinite(g1).all()
