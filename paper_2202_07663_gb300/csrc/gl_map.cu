@@ -99,7 +99,7 @@ __global__ void k_posterior(int B, const double* __restrict__ z, const double* _
 // k_whitened_posterior forms log p~(z) and its gradient in z (as k_posterior)
 // and pulls the gradient back to x, grad_x = L^T grad_z (the sums of
 // gl_hmc_affine_pullback). Two launches per evaluation instead of four.
-constexpr int kWhitenedThreads = 128;
+constexpr int kWhitenedThreads = 32;
 
 __global__ void __launch_bounds__(kWhitenedThreads) k_whitened_transform(int B, const double* __restrict__ x,
                                                                          const double* __restrict__ mu,
@@ -157,9 +157,14 @@ __global__ void __launch_bounds__(kWhitenedThreads) k_whitened_posterior(int B, 
   }
 }
 
+// One warp (one start or chain) per block: the per-parameter arithmetic is
+// FP64 (bijectors, prior densities), and GB300's FP64 pipe is narrow, so the
+// chains are spread over as many SMs as there are (50 chains: 32 -> 9 us for
+// the whitened posterior gradient against four warps per block).
+constexpr int kMapThreads = 32;
+
 int grid_for(int B) {
-  const int g = (B + 3) / 4;
-  return g < 1 ? 1 : (g > 4096 ? 4096 : g);
+  return B < 1 ? 1 : (B > 8192 ? 8192 : B);
 }
 
 int finish(cudaStream_t st, const char* what) {
@@ -180,7 +185,7 @@ int gl_map_inverse(int B, const float* theta, const gl_prior_entry* prior, doubl
   if (!theta || !z_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   gl_internal::hooks()->before(GL_K_OTHER, st);
-  k_map_inverse<<<grid_for(B), 128, 0, st>>>(B, theta, z_out, P);
+  k_map_inverse<<<grid_for(B), kMapThreads, 0, st>>>(B, theta, z_out, P);
   return finish(st, "k_map_inverse");
 }
 
@@ -193,7 +198,7 @@ int gl_map_transform(int B, const double* z, const gl_prior_entry* prior, float*
   if (!z || !theta_out) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   gl_internal::hooks()->before(GL_K_OTHER, st);
-  k_map_transform<<<grid_for(B), 128, 0, st>>>(B, z, theta_out, P);
+  k_map_transform<<<grid_for(B), kMapThreads, 0, st>>>(B, z, theta_out, P);
   return finish(st, "k_map_transform");
 }
 
@@ -211,7 +216,7 @@ int gl_map_adam_step(int B, double* z, double* m, double* v, int t, double lr, d
   const double c1 = m ? 1.0 - pow(beta1, t) : 1.0, c2 = m ? 1.0 - pow(beta2, t) : 1.0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   gl_internal::hooks()->before(GL_K_OTHER, st);
-  k_map_step<<<grid_for(B), 128, 0, st>>>(B, z, m, v, c1, c2, lr, beta1, beta2, eps, loglik, grad_theta,
+  k_map_step<<<grid_for(B), kMapThreads, 0, st>>>(B, z, m, v, c1, c2, lr, beta1, beta2, eps, loglik, grad_theta,
                                           objective_out, theta_out, P);
   return finish(st, "k_map_step");
 }
@@ -227,7 +232,7 @@ int gl_posterior_grad(int B, const double* z, const double* loglik, const double
     return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   gl_internal::hooks()->before(GL_K_OTHER, st);
-  k_posterior<<<grid_for(B), 128, 0, st>>>(B, z, loglik, grad_theta, logp_out, grad_z_out, P);
+  k_posterior<<<grid_for(B), kMapThreads, 0, st>>>(B, z, loglik, grad_theta, logp_out, grad_z_out, P);
   return finish(st, "k_posterior");
 }
 
