@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdint>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <type_traits>
 
@@ -1352,6 +1353,24 @@ void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix) {
   *ntiles = (HW + tp - 1) / tp;
 }
 
+// Blocks of a convolution kernel resident on the whole GPU at a dynamic
+// shared-memory size (occupancy query, cached per kernel and size; the
+// grouped path warms it before a graph capture).
+template <int K, int R, int NT, int MINB, class Src>
+static cudaError_t conv_resident(size_t smem, int* resident) {
+  static std::map<size_t, int> per_sm;   // by dynamic shared memory
+  std::lock_guard<std::mutex> lock(g_attr_mutex);
+  auto it = per_sm.find(smem);
+  if (it == per_sm.end()) {
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_conv<K, R, NT, MINB, Src>, NT, smem);
+    if (e != cudaSuccess) return e;
+    it = per_sm.emplace(smem, n > 0 ? n : 1).first;
+  }
+  *resident = num_sms() * it->second;
+  return cudaSuccess;
+}
+
 template <int K, int R, int NT, int MINB, class Src>
 static cudaError_t launch_conv(const Src& src, int nitems, size_t smem, int mode, cudaStream_t st, bool persistent) {
   static size_t attr = 48 * 1024;
@@ -1365,7 +1384,15 @@ static cudaError_t launch_conv(const Src& src, int nitems, size_t smem, int mode
     }
   }
   int grid = nitems;
-  if (persistent) grid = grid < num_sms() * 4 ? grid : num_sms() * 4;
+  if (persistent) {
+    // as many blocks as fit on the GPU at once: with a static split of the
+    // items, blocks beyond that would start only after others have finished
+    // their whole share
+    int resident = 0;
+    cudaError_t e = conv_resident<K, R, NT, MINB, Src>(smem, &resident);
+    if (e != cudaSuccess) return e;
+    grid = grid < resident ? grid : resident;
+  }
   k_conv<K, R, NT, MINB, Src><<<grid, NT, smem, st>>>(src, mode);
   return cudaSuccess;
 }
@@ -1534,8 +1561,13 @@ cudaError_t launch_table(const Seg* d_segs, int nseg, int vec_total, int ray_tot
 // class c and must cover every segment of that class.
 template <int K, int R, int NT, int MINB>
 static cudaError_t set_devtable_attr(size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(k_conv<K, R, NT, MINB, DevTable>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_conv<K, R, NT, MINB, DevTable>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  int resident = 0;   // the occupancy query before any capture
+  return conv_resident<K, R, NT, MINB, DevTable>(smem, &resident);
 }
 
 cudaError_t prepare_devtable(const size_t* conv_smem) {
