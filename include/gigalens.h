@@ -365,6 +365,17 @@ int gl_posterior_whitened_transform(int B, const double* x, const double* mu, co
 int gl_posterior_whitened_grad(int B, const double* z, const double* loglik, const double* grad_theta,
                                const double* L, const gl_prior_entry* prior, double* logp_out, double* grad_x_out,
                                void* stream);
+/*
+ * gl_hmc_leapfrog_whitened - one leapfrog update of HMC on the whitened
+ *   coordinates (identity mass on x would be inv_mass = 1): p += kick eps grad,
+ *   x += eps inv_mass p (gl_hmc_leapfrog's arithmetic; eps from *eps_dev when
+ *   eps_dev is not NULL), then gl_posterior_whitened_transform at the new x,
+ *   in one launch. x, p, grad [B, 22] float64 (x and p updated in place),
+ *   inv_mass [22]; other arguments as for gl_posterior_whitened_transform.
+ */
+int gl_hmc_leapfrog_whitened(int B, double* x, double* p, const double* grad, const double* inv_mass, double eps,
+                             const double* eps_dev, double kick, const double* mu, const double* L,
+                             const gl_prior_entry* prior, double* z_out, float* theta_out, void* stream);
 
 /*
  * Dense preconditioning (Sec. 2.5: the mass matrix set to the inverse of a

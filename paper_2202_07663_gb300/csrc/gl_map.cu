@@ -123,6 +123,48 @@ __global__ void __launch_bounds__(kWhitenedThreads) k_whitened_transform(int B, 
   }
 }
 
+// The leapfrog update of HMC on the whitened coordinates followed by
+// k_whitened_transform at the new point: p += kick eps grad, x += eps M^-1 p
+// (the arithmetic of gl_hmc_leapfrog), z = mu + L x, theta = g(z).
+__global__ void __launch_bounds__(kWhitenedThreads) k_leapfrog_whitened(int B, double* __restrict__ x,
+                                                                        double* __restrict__ p,
+                                                                        const double* __restrict__ grad,
+                                                                        const double* __restrict__ inv_mass,
+                                                                        double eps_arg,
+                                                                        const double* __restrict__ eps_dev,
+                                                                        double kick, const double* __restrict__ mu,
+                                                                        const double* __restrict__ Lc,
+                                                                        double* __restrict__ z,
+                                                                        float* __restrict__ theta, PriorTable P) {
+  constexpr int D = GL_NPARAM;
+  __shared__ double sL[D * D];
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = Lc[i];
+  __syncthreads();
+  const double eps = eps_dev ? *eps_dev : eps_arg;
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb) {
+    const size_t i = size_t(b) * D + lane;
+    double xi = 0.0;
+    if (lane < D) {
+      const double pi = p[i] + kick * eps * grad[i];
+      xi = x[i] + eps * inv_mass[lane] * pi;
+      p[i] = pi;
+      x[i] = xi;
+    }
+    double acc = lane < D ? mu[lane] : 0.0;
+    for (int j = 0; j < D; ++j) {
+      const double xj = __shfl_sync(0xffffffffu, xi, j);
+      if (j <= lane) acc += sL[lane * D + j] * xj;
+    }
+    if (lane < D) {
+      z[i] = acc;
+      double th, d, lj, dlj;
+      bij(P.e[lane], acc, th, d, lj, dlj);
+      theta[i] = float(th);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kWhitenedThreads) k_whitened_posterior(int B, const double* __restrict__ z,
                                                                          const double* __restrict__ loglik,
                                                                          const double* __restrict__ grad,
@@ -268,6 +310,25 @@ int gl_posterior_whitened_grad(int B, const double* z, const double* loglik, con
   k_whitened_posterior<<<grid_for(B), kWhitenedThreads, 0, st>>>(B, z, loglik, grad_theta, L, logp_out, grad_x_out,
                                                                    P);
   return finish(st, "k_whitened_posterior");
+}
+
+int gl_hmc_leapfrog_whitened(int B, double* x, double* p, const double* grad, const double* inv_mass, double eps,
+                             const double* eps_dev, double kick, const double* mu, const double* L,
+                             const gl_prior_entry* prior, double* z_out, float* theta_out, void* stream) {
+  PriorTable P;
+  int rc = load_table(prior, P);
+  if (rc != GL_OK) return rc;
+  if (B < 0) return gl_internal::set_error(GL_ERR_INVALID_ARG, "B < 0");
+  if (B == 0) return GL_OK;
+  if (!x || !p || !grad || !inv_mass || !mu || !L || !z_out || !theta_out)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if (!eps_dev && !std::isfinite(eps)) return gl_internal::set_error(GL_ERR_INVALID_ARG, "eps not finite");
+  if (z_out == x) return gl_internal::set_error(GL_ERR_INVALID_ARG, "z_out and x alias");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gl_internal::hooks()->before(GL_K_OTHER, st);
+  k_leapfrog_whitened<<<grid_for(B), kWhitenedThreads, 0, st>>>(B, x, p, grad, inv_mass, eps, eps_dev, kick, mu, L,
+                                                                  z_out, theta_out, P);
+  return finish(st, "k_leapfrog_whitened");
 }
 
 }  // extern "C"

@@ -142,17 +142,43 @@ class WhitenedTarget:
                           None, torch.cuda.current_stream(x.device).cuda_stream)
         return z
 
-    def __call__(self, q64, q32, lp_out, g_out):
-        B, d = q64.shape
+    def _buffers(self, B, dev):
         if self._buf is None or self._buf[0].shape[0] != B:
-            dev = q64.device
+            d = self.d
             self._buf = (torch.empty(B, d, dtype=torch.float64, device=dev),
                          torch.empty(B, d, dtype=torch.float32, device=dev),
                          torch.empty(B, d, dtype=torch.float64, device=dev),
                          torch.empty(B, dtype=torch.float64, device=dev))
-        z, z32, gz, ll = self._buf
+        return self._buf
+
+    @property
+    def lens_posterior(self) -> bool:
+        """Whether this is the whitened lens posterior (the fused launches apply)."""
+        return isinstance(self.inner, PosteriorTarget) and self.d == NPARAM
+
+    def leapfrog_and_eval(self, x, p, grad, inv_mass, eps, eps_dev, kick, lp_out, g_out):
+        """gl_hmc_leapfrog on (x, p), then this target at the new x (lens
+        posterior only): the update, whitening and bijectors in one launch,
+        the likelihood, then the posterior gradient and its pull-back."""
+        B = x.shape[0]
+        z, z32, gz, ll = self._buffers(B, x.device)
+        st = torch.cuda.current_stream(x.device).cuda_stream
+        lib = abi.lib_handle()
+        pp = ctypes.addressof(self.inner.prior)
+        abi._check(lib.gl_hmc_leapfrog_whitened(B, x.data_ptr(), p.data_ptr(), grad.data_ptr(), inv_mass.data_ptr(),
+                                                float(eps), eps_dev.data_ptr() if eps_dev is not None else None,
+                                                float(kick), self.mu.data_ptr(), self.L.data_ptr(), pp, z.data_ptr(),
+                                                z32.data_ptr(), st), "gl_hmc_leapfrog_whitened")
+        self.inner.system.loglik_grad(z32, out=(ll, gz, None))
+        abi._check(lib.gl_posterior_whitened_grad(B, z.data_ptr(), ll.data_ptr(), gz.data_ptr(), self.L.data_ptr(),
+                                                  pp, lp_out.data_ptr(), g_out.data_ptr(), st),
+                   "gl_posterior_whitened_grad")
+
+    def __call__(self, q64, q32, lp_out, g_out):
+        B, d = q64.shape
+        z, z32, gz, ll = self._buffers(B, q64.device)
         st = torch.cuda.current_stream(q64.device).cuda_stream
-        if isinstance(self.inner, PosteriorTarget) and d == NPARAM:
+        if self.lens_posterior:
             # the lens posterior: whitening and bijectors in one launch, the
             # posterior gradient and its pull-back in another (same sums)
             lib = abi.lib_handle()
@@ -311,7 +337,7 @@ class HMC:
 
     def __init__(self, q0: torch.Tensor, inv_mass: torch.Tensor, step_size: float, n_leapfrog: int,
                  system=None, logp_grad: Optional[Callable] = None, target=None, seed: int = 0,
-                 graphs: bool = False, group=None):
+                 graphs: bool = False, group=None, fuse: bool = True):
         # with a process group, q0 holds every chain and this process runs its
         # shard of them; random draws are made for all chains and sliced
         self.group = group
@@ -331,6 +357,8 @@ class HMC:
         if target is None:
             target = FunctionTarget(logp_grad) if logp_grad is not None else LensTarget(system)
         self.target = target
+        # the whitened lens posterior takes the leapfrog update in its first launch
+        self.fused = bool(fuse) and isinstance(target, WhitenedTarget) and target.lens_posterior
         self.gen = torch.Generator(device=self.dev)
         self.gen.manual_seed(seed)
         B, d = self.B, self.d
@@ -380,6 +408,10 @@ class HMC:
                 self._eps_dev_val = self.eps
             for l in range(L):
                 self._leapfrog_graph(0.5 if l == 0 else 1.0).replay()
+        elif self.fused:
+            for l in range(L):
+                self.target.leapfrog_and_eval(self.qp, self.p, self.gp, self.inv_mass, self.eps, None,
+                                              0.5 if l == 0 else 1.0, self.lp_new, self.gp)
         else:
             for l in range(L):
                 abi.gl_hmc_leapfrog(B, d, self.qp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
@@ -399,11 +431,18 @@ class HMC:
         if g is None:
             g = torch.cuda.CUDAGraph()
             q32 = self.q32.data_ptr() if self.target.needs_q32 else None
+            if self.fused:   # buffers allocated before the capture
+                self.target._buffers(self.B, self.dev)
             with torch.cuda.graph(g, capture_error_mode="thread_local"):
                 st = torch.cuda.current_stream(self.dev).cuda_stream
-                abi.gl_hmc_leapfrog_dev(self.B, self.d, self.qp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
-                                        self.inv_mass.data_ptr(), self.eps_dev.data_ptr(), kick, q32, st)
-                self.target(self.qp, self.q32, self.lp_new, self.gp)
+                if self.fused:
+                    self.target.leapfrog_and_eval(self.qp, self.p, self.gp, self.inv_mass, 0.0, self.eps_dev, kick,
+                                                  self.lp_new, self.gp)
+                else:
+                    abi.gl_hmc_leapfrog_dev(self.B, self.d, self.qp.data_ptr(), self.p.data_ptr(),
+                                            self.gp.data_ptr(), self.inv_mass.data_ptr(), self.eps_dev.data_ptr(),
+                                            kick, q32, st)
+                    self.target(self.qp, self.q32, self.lp_new, self.gp)
             self._graph[kick] = g
         return g
 

@@ -8,7 +8,8 @@
 - the ChEES trajectory-length gradient kernel against its oracle, and
   ChEES-adapted HMC on a standard normal (trajectory length, moments);
 - leapfrog steps replayed as CUDA graphs give the eager path's chains bit
-  for bit (same kernels, same order, step size read from device memory);
+  for bit (same kernels, same order, step size read from device memory),
+  and so does the leapfrog update fused into the whitened posterior;
 - the paper's sampler on a small lens system: Laplace covariance at the
   truth as the preconditioner, chains drawn from it, HMC with dual-averaged
   step size and ChEES trajectory length; R-hat,
@@ -216,15 +217,19 @@ def test_graph_replay_matches_eager(mods):
     g = torch.Generator(device="cuda").manual_seed(5)
     x0 = torch.randn(16, 22, dtype=torch.float64, device="cuda", generator=g)
     runs = []
-    for graphs in (False, True):
+    # eager and graph-replayed, with the leapfrog update fused into the
+    # whitened posterior's first launch and as separate launches: same bits
+    for graphs, fuse in ((False, False), (False, True), (True, True), (True, False)):
         target = hmc.WhitenedTarget(hmc.PosteriorTarget(s), z_truth, L)
         sm = hmc.HMC(x0, torch.ones(22, dtype=torch.float64, device="cuda"), 0.3, 5, target=target, seed=3,
-                     graphs=graphs)
+                     graphs=graphs, fuse=fuse)
+        assert sm.fused == fuse
         runs.append(sm.run_adaptive(n_burn=8, n_samples=5, adapt_trajectory=True))
     s.close()
-    assert runs[0].step_size == runs[1].step_size
-    assert runs[0].trajectory_length == runs[1].trajectory_length
-    assert torch.equal(runs[0].samples, runs[1].samples)
+    for r in runs[1:]:
+        assert runs[0].step_size == r.step_size
+        assert runs[0].trajectory_length == r.trajectory_length
+        assert torch.equal(runs[0].samples, r.samples)
 
 
 def test_fused_whitened_posterior_equals_the_four_calls(mods):
