@@ -152,9 +152,9 @@ __global__ void __launch_bounds__(kWhitenedThreads) k_leapfrog_whitened(int B, d
       x[i] = xi;
     }
     double acc = lane < D ? mu[lane] : 0.0;
-    for (int j = 0; j < D; ++j) {
+    for (int j = 0; j < D; ++j) {   // every lane shuffles; lanes >= D read no matrix row
       const double xj = __shfl_sync(0xffffffffu, xi, j);
-      if (j <= lane) acc += sL[lane * D + j] * xj;
+      if (lane < D && j <= lane) acc += sL[lane * D + j] * xj;
     }
     if (lane < D) {
       z[i] = acc;
