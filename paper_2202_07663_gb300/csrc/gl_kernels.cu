@@ -556,8 +556,12 @@ constexpr int ADJ_THREADS = GL_ADJ_THREADS;
 __device__ __forceinline__ float lane_sum(float v) { return v; }
 __device__ __forceinline__ float lane_sum(F2 v) { return v.v.x + v.v.y; }
 
-template <class Src>
-__global__ void __launch_bounds__(ADJ_THREADS, GL_ADJ_MINB) k_ray_adj(const __grid_constant__ Src src) {
+// MINB: resident blocks per SM the registers are fitted for. Two (218
+// registers, no spills) suit long ray tiles; three (168 registers, 48 bytes
+// of spills) overlap more blocks' prologues and epilogues and suit short ones
+// (60x60 k=2: 654 -> 637 us; 100x100 k=4 at 80K rays per tile: 1725 -> 1736 us).
+template <class Src, int MINB = GL_ADJ_MINB>
+__global__ void __launch_bounds__(ADJ_THREADS, MINB) k_ray_adj(const __grid_constant__ Src src) {
   using RT = typename std::conditional<GL_ADJ_PAIRED != 0, F2, float>::type;
   __shared__ VecConst sv;
   __shared__ Seg ss;
@@ -1458,9 +1462,13 @@ static cudaError_t launch_conv_bands(const OneSeg& src, int nb, int mode, cudaSt
   return cudaLaunchKernelEx(&cfg, k_conv_bands<K>, src, mode, rows);
 }
 
+// Ray tiles of at most this many rays take the three-blocks-per-SM adjoint.
+constexpr long long ADJ_SHORT_TILE_RAYS = 32768;
+
 template <class Src>
 static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj_final, cudaStream_t st,
-                            Hooks* hooks, bool persistent, bool one_tile = false, bool fwd_rays = true) {
+                            Hooks* hooks, bool persistent, bool one_tile = false, bool fwd_rays = true,
+                            bool short_tiles = false) {
   const int sms = num_sms();
   cudaError_t e;
   const int vthreads = 128, wpb = vthreads / 32;
@@ -1485,7 +1493,10 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
   }
   if (adj_final) {
     hooks->before(GL_K_RAY_ADJ, st);
-    k_ray_adj<Src><<<rgrid, ADJ_THREADS, 0, st>>>(src);
+    if (short_tiles)
+      k_ray_adj<Src, 3><<<rgrid, ADJ_THREADS, 0, st>>>(src);
+    else
+      k_ray_adj<Src><<<rgrid, ADJ_THREADS, 0, st>>>(src);
     if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
     hooks->before(GL_K_FINAL, st);
     if (one_tile)
@@ -1513,7 +1524,8 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD && mode != MODE_CORR) return cudaSuccess;
-  return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false, s.ntiles == 1);
+  const bool short_tiles = (long long)s.tile_pix * s.k * s.k <= ADJ_SHORT_TILE_RAYS;
+  return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false, s.ntiles == 1, true, short_tiles);
 }
 
 cudaError_t launch_basis(const Seg& s, cudaStream_t st, Hooks* hooks) {
