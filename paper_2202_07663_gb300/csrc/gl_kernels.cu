@@ -1524,7 +1524,13 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD && mode != MODE_CORR) return cudaSuccess;
-  const bool short_tiles = (long long)s.tile_pix * s.k * s.k <= ADJ_SHORT_TILE_RAYS;
+  // three blocks per SM for short tiles when the waves favour it: a block's
+  // time grows with the blocks sharing its SM, three share 1.027x the work of
+  // two, so three win when 3 w3 < 2.054 w2 (w_m = tiles / (SMs m), rounded up;
+  // B = 300 on 80x80: 4 waves against 5, two blocks win, as measured)
+  const long long items = (long long)s.B * s.ntiles, sms = num_sms();
+  const long long w2 = (items + 2 * sms - 1) / (2 * sms), w3 = (items + 3 * sms - 1) / (3 * sms);
+  const bool short_tiles = (long long)s.tile_pix * s.k * s.k <= ADJ_SHORT_TILE_RAYS && 3000 * w3 < 2054 * w2;
   return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false, s.ntiles == 1, true, short_tiles);
 }
 
