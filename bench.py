@@ -85,7 +85,7 @@ def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
 # DRAM bytes per launch of k_ray_adj from one ncu capture, valid only for the
 # kernel source it was taken on (sha256 prefix of gl_kernels.cu + gl_device.cuh).
 MUFU_RAY_ADJ = 12   # ex2/lg2/rcp per ray in the adjoint (EPL power, two Sersic profiles)
-TRAFFIC = {"352f9dbfdae0ce6f": 64.801792e6}   # ncu dram read + write, one launch at B = 4096
+TRAFFIC = {"484cf7d85eb9f23b": 64.712192e6}   # ncu dram read + write, one launch at B = 4096
 
 
 def kernel_source_hash() -> str:
