@@ -11,7 +11,8 @@ HEADER = os.path.join(ROOT, "include", "gigalens.h")
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    with open(HEADER) as f:
+        src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:int|size_t|long long|const char\s*\*)\s*\**\s*(gl_\w+)\s*\(", src, flags=re.M)
     assert names, "no declarations parsed"
