@@ -96,7 +96,7 @@ def test_gloo_ranks_agree_with_one_process(world):
     from oracle import hmc_oracle as ho
     from paper_2202_07663_gb300.hmc import DualAveraging
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of a threaded process
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
