@@ -48,14 +48,50 @@ def test_error_strings_without_gpu(lib):
     assert lib.gl_loglik(None, None, 1, None, None, None) == -1
 
 
+def test_error_codes_mirror_header():
+    from paper_2202_07663_gb300 import abi
+    codes = dict(re.findall(r"(GL_(?:OK|ERR_\w+))\s*=\s*(-?\d+)", _read(HEADER)))
+    assert len(codes) == 7
+    for name, value in codes.items():
+        assert getattr(abi, name) == int(value), name
+
+
+# calls that accept NULL (destroy), only read state, or take no pointer
+NULL_TOLERANT = {"gl_system_destroy", "gl_batcher_destroy", "gl_profile_read", "gl_error_string",
+                 "gl_last_error_message", "gl_kernel_name", "gl_launch_count", "gl_profile_enable",
+                 "gl_profile_reset", "gl_vi_param_count", "gl_vi_workspace_bytes", "gl_system_scratch_bytes",
+                 "gl_system_resident_bytes", "gl_batcher_segment_bytes"}
+
+
+@pytest.mark.parametrize("name", [n for n in declared_functions() if n not in NULL_TOLERANT])
+def test_null_pointers_are_refused_before_any_launch(lib, name):
+    """Each call that takes pointers returns GL_ERR_INVALID_ARG, with a
+    message, for NULL ones at size 1, and launches nothing: the checks come
+    before any device work (this runs without a GPU)."""
+    import ctypes
+    from paper_2202_07663_gb300 import abi
+    args, _ = abi.SIGNATURES[name]
+    vals = [1 if a in (ctypes.c_int, ctypes.c_size_t) else 1.0 if a in (ctypes.c_double, ctypes.c_float) else None
+            for a in args]
+    n0 = lib.gl_launch_count()
+    assert getattr(lib, name)(*vals) == abi.GL_ERR_INVALID_ARG
+    assert lib.gl_last_error_message().startswith(b"null")
+    assert lib.gl_launch_count() == n0
+
+
+def _read(path):
+    with open(path) as f:
+        return f.read()
+
+
 def test_product_never_imports_the_oracle():
     pkg = os.path.join(ROOT, "paper_2202_07663_gb300")
     for dirpath, _, files in os.walk(pkg):
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
-                text = open(os.path.join(dirpath, f)).read()
+                text = _read(os.path.join(dirpath, f))
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
                 assert "gl_oracle" not in text, f
     # and the oracle never includes the CUDA sources
-    osrc = open(os.path.join(ROOT, "oracle", "gl_oracle.cpp")).read()
+    osrc = _read(os.path.join(ROOT, "oracle", "gl_oracle.cpp"))
     assert "gl_device" not in osrc and "gigalens.h" not in osrc
