@@ -376,6 +376,26 @@ int gl_posterior_whitened_grad(int B, const double* z, const double* loglik, con
 int gl_hmc_leapfrog_whitened(int B, double* x, double* p, const double* grad, const double* inv_mass, double eps,
                              const double* eps_dev, double kick, const double* mu, const double* L,
                              const gl_prior_entry* prior, double* z_out, float* theta_out, void* stream);
+/*
+ * gl_hmc_leapfrog_whitened_chain - a leapfrog step after the first of a
+ *   trajectory, in one launch: the whitened posterior's gradient at the
+ *   current point (grad_x of gl_posterior_whitened_grad, same sums; its log p~
+ *   is not formed), then gl_hmc_leapfrog_whitened with that gradient.
+ *   z [B, 22] float64 is read as the current point (the z_out of the previous
+ *   step) and overwritten with the new one; grad_theta [B, 22] is
+ *   d log L / d theta at the current point's theta. x, p, inv_mass, eps,
+ *   eps_dev, kick, mu, L, prior, theta_out as for gl_hmc_leapfrog_whitened.
+ *   A trajectory of n steps is gl_hmc_leapfrog_whitened (kick 1/2), then n - 1
+ *   of these (kick 1) with log L evaluated after each launch, then
+ *   gl_posterior_whitened_grad at the last point: the bits of n pairs of
+ *   gl_hmc_leapfrog_whitened and gl_posterior_whitened_grad.
+ *   GL_ERR_INVALID_ARG for a bad prior table, B < 0, a null pointer, a
+ *   non-finite eps (eps_dev NULL) or aliased x, p, z, grad_theta.
+ */
+int gl_hmc_leapfrog_whitened_chain(int B, double* x, double* p, double* z, const double* grad_theta,
+                                   const double* inv_mass, double eps, const double* eps_dev, double kick,
+                                   const double* mu, const double* L, const gl_prior_entry* prior, float* theta_out,
+                                   void* stream);
 
 /*
  * Dense preconditioning (Sec. 2.5: the mass matrix set to the inverse of a

@@ -71,6 +71,7 @@ SIGNATURES = {
     "gl_posterior_whitened_transform": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_posterior_whitened_grad": ([_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_hmc_leapfrog_whitened": ([_i, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp, _vp, _vp, _vp, _vp], _i),
+    "gl_hmc_leapfrog_whitened_chain": ([_i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _d, _vp, _vp, _vp, _vp, _vp], _i),
     "gl_error_string": ([_i], ctypes.c_char_p),
     "gl_last_error_message": ([], ctypes.c_char_p),
     "gl_profile_enable": ([_i], _i),

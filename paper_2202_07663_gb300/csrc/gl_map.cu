@@ -199,6 +199,65 @@ __global__ void __launch_bounds__(kWhitenedThreads) k_whitened_posterior(int B, 
   }
 }
 
+// A leapfrog step after the first of a trajectory, in one launch: the
+// gradient at the current point z (the sums of k_whitened_posterior, without
+// log p~, which the trajectory does not need until its last point), then
+// k_whitened_posterior's gradient into k_leapfrog_whitened's update and
+// transform. z holds the current point on entry and the new one on exit: lane
+// i reads and writes element i of its chain only, the read first.
+__global__ void __launch_bounds__(kWhitenedThreads) k_leapfrog_whitened_chain(int B, double* __restrict__ x,
+                                                                              double* __restrict__ p,
+                                                                              double* __restrict__ z,
+                                                                              const double* __restrict__ grad_theta,
+                                                                              const double* __restrict__ inv_mass,
+                                                                              double eps_arg,
+                                                                              const double* __restrict__ eps_dev,
+                                                                              double kick,
+                                                                              const double* __restrict__ mu,
+                                                                              const double* __restrict__ Lc,
+                                                                              float* __restrict__ theta,
+                                                                              PriorTable P) {
+  constexpr int D = GL_NPARAM;
+  __shared__ double sL[D * D];
+  __shared__ double sg[kWhitenedThreads / 32][32];
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = Lc[i];
+  __syncthreads();
+  const double eps = eps_dev ? *eps_dev : eps_arg;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + w; b < B; b += gridDim.x * wpb) {
+    const size_t i = size_t(b) * D + lane;
+    if (lane < D) {
+      double th, d, lj, dlj, lp, dlp;
+      bij(P.e[lane], z[i], th, d, lj, dlj);
+      logpdf(P.e[lane], th, lp, dlp);
+      sg[w][lane] = (grad_theta[i] + dlp) * d + dlj;
+    }
+    __syncwarp();
+    double xi = 0.0;
+    if (lane < D) {
+      double acc = 0.0;
+      for (int r = lane; r < D; ++r) acc += sL[r * D + lane] * sg[w][r];
+      const double g = acc;
+      const double pi = p[i] + kick * eps * g;
+      xi = x[i] + eps * inv_mass[lane] * pi;
+      p[i] = pi;
+      x[i] = xi;
+    }
+    double acc = lane < D ? mu[lane] : 0.0;
+    for (int j = 0; j < D; ++j) {   // every lane shuffles; lanes >= D read no matrix row
+      const double xj = __shfl_sync(0xffffffffu, xi, j);
+      if (lane < D && j <= lane) acc += sL[lane * D + j] * xj;
+    }
+    if (lane < D) {
+      z[i] = acc;
+      double th, d, lj, dlj;
+      bij(P.e[lane], acc, th, d, lj, dlj);
+      theta[i] = float(th);
+    }
+    __syncwarp();   // sg is rewritten for the warp's next chain
+  }
+}
+
 // One warp (one start or chain) per block: the per-parameter arithmetic is
 // FP64 (bijectors, prior densities), and GB300's FP64 pipe is narrow, so the
 // chains are spread over as many SMs as there are (50 chains: 32 -> 9 us for
@@ -329,6 +388,27 @@ int gl_hmc_leapfrog_whitened(int B, double* x, double* p, const double* grad, co
   k_leapfrog_whitened<<<grid_for(B), kWhitenedThreads, 0, st>>>(B, x, p, grad, inv_mass, eps, eps_dev, kick, mu, L,
                                                                   z_out, theta_out, P);
   return finish(st, "k_leapfrog_whitened");
+}
+
+int gl_hmc_leapfrog_whitened_chain(int B, double* x, double* p, double* z, const double* grad_theta,
+                                   const double* inv_mass, double eps, const double* eps_dev, double kick,
+                                   const double* mu, const double* L, const gl_prior_entry* prior, float* theta_out,
+                                   void* stream) {
+  PriorTable P;
+  int rc = load_table(prior, P);
+  if (rc != GL_OK) return rc;
+  if (B < 0) return gl_internal::set_error(GL_ERR_INVALID_ARG, "B < 0");
+  if (B == 0) return GL_OK;
+  if (!x || !p || !z || !grad_theta || !inv_mass || !mu || !L || !theta_out)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "null pointer");
+  if (!eps_dev && !std::isfinite(eps)) return gl_internal::set_error(GL_ERR_INVALID_ARG, "eps not finite");
+  if (z == x || z == p || x == p || z == grad_theta || p == grad_theta || x == grad_theta)
+    return gl_internal::set_error(GL_ERR_INVALID_ARG, "state arrays alias");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gl_internal::hooks()->before(GL_K_OTHER, st);
+  k_leapfrog_whitened_chain<<<grid_for(B), kWhitenedThreads, 0, st>>>(B, x, p, z, grad_theta, inv_mass, eps, eps_dev,
+                                                                        kick, mu, L, theta_out, P);
+  return finish(st, "k_leapfrog_whitened_chain");
 }
 
 }  // extern "C"

@@ -156,23 +156,45 @@ class WhitenedTarget:
         """Whether this is the whitened lens posterior (the fused launches apply)."""
         return isinstance(self.inner, PosteriorTarget) and self.d == NPARAM
 
-    def leapfrog_and_eval(self, x, p, grad, inv_mass, eps, eps_dev, kick, lp_out, g_out):
-        """gl_hmc_leapfrog on (x, p), then this target at the new x (lens
-        posterior only): the update, whitening and bijectors in one launch,
-        the likelihood, then the posterior gradient and its pull-back."""
+    def leapfrog_first(self, x, p, grad, inv_mass, eps, eps_dev, kick):
+        """The first leapfrog step of a trajectory (lens posterior only):
+        gl_hmc_leapfrog_whitened on (x, p) with the gradient ``grad`` (the
+        update, whitening and bijectors in one launch), then log L and its
+        gradient at the new point, kept in this target's buffers."""
         B = x.shape[0]
         z, z32, gz, ll = self._buffers(B, x.device)
         st = torch.cuda.current_stream(x.device).cuda_stream
         lib = abi.lib_handle()
-        pp = ctypes.addressof(self.inner.prior)
         abi._check(lib.gl_hmc_leapfrog_whitened(B, x.data_ptr(), p.data_ptr(), grad.data_ptr(), inv_mass.data_ptr(),
                                                 float(eps), eps_dev.data_ptr() if eps_dev is not None else None,
-                                                float(kick), self.mu.data_ptr(), self.L.data_ptr(), pp, z.data_ptr(),
-                                                z32.data_ptr(), st), "gl_hmc_leapfrog_whitened")
+                                                float(kick), self.mu.data_ptr(), self.L.data_ptr(),
+                                                ctypes.addressof(self.inner.prior), z.data_ptr(), z32.data_ptr(), st),
+                   "gl_hmc_leapfrog_whitened")
         self.inner.system.loglik_grad(z32, out=(ll, gz, None))
-        abi._check(lib.gl_posterior_whitened_grad(B, z.data_ptr(), ll.data_ptr(), gz.data_ptr(), self.L.data_ptr(),
-                                                  pp, lp_out.data_ptr(), g_out.data_ptr(), st),
-                   "gl_posterior_whitened_grad")
+
+    def leapfrog_next(self, x, p, inv_mass, eps, eps_dev, kick):
+        """A later leapfrog step: the posterior gradient at the point of the
+        last evaluation, the update and the transform in one launch
+        (gl_hmc_leapfrog_whitened_chain), then log L at the new point."""
+        B = x.shape[0]
+        z, z32, gz, ll = self._buffers(B, x.device)
+        st = torch.cuda.current_stream(x.device).cuda_stream
+        lib = abi.lib_handle()
+        abi._check(lib.gl_hmc_leapfrog_whitened_chain(B, x.data_ptr(), p.data_ptr(), z.data_ptr(), gz.data_ptr(),
+                                                      inv_mass.data_ptr(), float(eps),
+                                                      eps_dev.data_ptr() if eps_dev is not None else None,
+                                                      float(kick), self.mu.data_ptr(), self.L.data_ptr(),
+                                                      ctypes.addressof(self.inner.prior), z32.data_ptr(), st),
+                   "gl_hmc_leapfrog_whitened_chain")
+        self.inner.system.loglik_grad(z32, out=(ll, gz, None))
+
+    def posterior_at_last(self, B, dev, lp_out, g_out):
+        """log p~ and its gradient in x at the point of the last evaluation."""
+        z, _, gz, ll = self._buffers(B, dev)
+        abi._check(abi.lib_handle().gl_posterior_whitened_grad(
+            B, z.data_ptr(), ll.data_ptr(), gz.data_ptr(), self.L.data_ptr(), ctypes.addressof(self.inner.prior),
+            lp_out.data_ptr(), g_out.data_ptr(), torch.cuda.current_stream(dev).cuda_stream),
+            "gl_posterior_whitened_grad")
 
     def __call__(self, q64, q32, lp_out, g_out):
         B, d = q64.shape
@@ -395,6 +417,8 @@ class HMC:
         stream = torch.cuda.current_stream(self.dev).cuda_stream
         B, d = self.B, self.d
         L = self.L if n_leapfrog is None else int(n_leapfrog)
+        if L < 1:
+            raise ValueError("an HMC iteration needs at least one leapfrog step")
         self.q_prev.copy_(self.q)
         torch.randn(self.B_total, d, generator=self.gen, dtype=torch.float64, device=self.dev, out=self.p0_all)
         self.p0.mul_(torch.rsqrt(self.inv_mass))
@@ -410,13 +434,17 @@ class HMC:
                 self._leapfrog_graph(0.5 if l == 0 else 1.0).replay()
         elif self.fused:
             for l in range(L):
-                self.target.leapfrog_and_eval(self.qp, self.p, self.gp, self.inv_mass, self.eps, None,
-                                              0.5 if l == 0 else 1.0, self.lp_new, self.gp)
+                if l == 0:
+                    self.target.leapfrog_first(self.qp, self.p, self.gp, self.inv_mass, self.eps, None, 0.5)
+                else:
+                    self.target.leapfrog_next(self.qp, self.p, self.inv_mass, self.eps, None, 1.0)
         else:
             for l in range(L):
                 abi.gl_hmc_leapfrog(B, d, self.qp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
                                     self.inv_mass.data_ptr(), self.eps, 0.5 if l == 0 else 1.0, q32, stream)
                 self.target(self.qp, self.q32, self.lp_new, self.gp)
+        if self.fused:   # the fused steps leave log p~ and its gradient at the last point to here
+            self.target.posterior_at_last(B, self.dev, self.lp_new, self.gp)
         torch.rand(self.B_total, generator=self.gen, dtype=torch.float64, device=self.dev, out=self.u_all)
         log_u = self.u_all[self.rows[0]:self.rows[1]].log_()
         abi.gl_hmc_finish(B, d, self.p0.data_ptr(), self.logp.data_ptr(), self.p.data_ptr(), self.gp.data_ptr(),
@@ -435,9 +463,10 @@ class HMC:
                 self.target._buffers(self.B, self.dev)
             with torch.cuda.graph(g, capture_error_mode="thread_local"):
                 st = torch.cuda.current_stream(self.dev).cuda_stream
-                if self.fused:
-                    self.target.leapfrog_and_eval(self.qp, self.p, self.gp, self.inv_mass, 0.0, self.eps_dev, kick,
-                                                  self.lp_new, self.gp)
+                if self.fused and kick == 0.5:
+                    self.target.leapfrog_first(self.qp, self.p, self.gp, self.inv_mass, 0.0, self.eps_dev, kick)
+                elif self.fused:
+                    self.target.leapfrog_next(self.qp, self.p, self.inv_mass, 0.0, self.eps_dev, kick)
                 else:
                     abi.gl_hmc_leapfrog_dev(self.B, self.d, self.qp.data_ptr(), self.p.data_ptr(),
                                             self.gp.data_ptr(), self.inv_mass.data_ptr(), self.eps_dev.data_ptr(),

@@ -79,6 +79,28 @@ def test_null_pointers_are_refused_before_any_launch(lib, name):
     assert lib.gl_launch_count() == n0
 
 
+def test_chained_leapfrog_refuses_aliased_state(lib):
+    """gl_hmc_leapfrog_whitened_chain reads z before overwriting it lane by
+    lane, so x, p, z and grad_theta must be distinct; the check runs before
+    any launch (the pointers below are never dereferenced)."""
+    import ctypes
+    from paper_2202_07663_gb300 import abi, map as gmap
+    table = gmap.prior_table()   # held: the call reads it on the host
+    prior = ctypes.addressof(table)
+    a, b, c, d, m = 0x1000, 0x2000, 0x3000, 0x4000, 0x5000
+    n0 = lib.gl_launch_count()
+    for x, p, z, g in ((a, b, a, c), (a, b, b, c), (a, a, b, c), (a, b, c, c), (a, c, b, c), (c, b, d, c)):
+        assert lib.gl_hmc_leapfrog_whitened_chain(4, x, p, z, g, m, 0.1, None, 1.0, m, m, prior, m,
+                                                  None) == abi.GL_ERR_INVALID_ARG
+        assert b"alias" in lib.gl_last_error_message()
+    assert lib.gl_hmc_leapfrog_whitened_chain(4, a, b, c, d, m, float("nan"), None, 1.0, m, m, prior, m,
+                                              None) == abi.GL_ERR_INVALID_ARG
+    assert lib.gl_hmc_leapfrog_whitened_chain(-1, a, b, c, d, m, 0.1, None, 1.0, m, m, prior, m,
+                                              None) == abi.GL_ERR_INVALID_ARG
+    assert lib.gl_hmc_leapfrog_whitened_chain(0, a, b, c, d, m, 0.1, None, 1.0, m, m, prior, m, None) == abi.GL_OK
+    assert lib.gl_launch_count() == n0
+
+
 def _read(path):
     with open(path) as f:
         return f.read()

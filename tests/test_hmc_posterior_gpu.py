@@ -10,6 +10,9 @@
 - leapfrog steps replayed as CUDA graphs give the eager path's chains bit
   for bit (same kernels, same order, step size read from device memory),
   and so does the leapfrog update fused into the whitened posterior;
+- gl_hmc_leapfrog_whitened_chain (the gradient at the last point, the
+  update and the transform in one launch) gives the bits of
+  gl_posterior_whitened_grad followed by gl_hmc_leapfrog_whitened;
 - the paper's sampler on a small lens system: Laplace covariance at the
   truth as the preconditioner, chains drawn from it, HMC with dual-averaged
   step size and ChEES trajectory length; R-hat,
@@ -267,3 +270,46 @@ def test_fused_whitened_posterior_equals_the_four_calls(mods):
     assert torch.equal(lp1, lp2) and torch.equal(g1, g2)
     assert torch.equal(lp0, lp3)
     assert torch.isfinite(lp1).all() and torch.isfinite(g1).all()
+
+
+@pytest.mark.parametrize("B", [1, 37])
+def test_chained_leapfrog_equals_gradient_then_leapfrog(mods, B):
+    import ctypes
+    abi, hmc, gmap = mods
+    lib = abi.lib_handle()
+    table = gmap.prior_table()
+    pp = ctypes.addressof(table)
+    st = torch.cuda.current_stream().cuda_stream
+    g = torch.Generator(device="cuda").manual_seed(17 + B)
+    f64 = dict(dtype=torch.float64, device="cuda")
+    spec, truth, psf, image = _paper_system(40, 9)
+    z0 = torch.from_numpy(mo.inverse_bijector(truth)[0]).cuda()
+    A = torch.randn(22, 22, **f64, generator=g) * 0.01
+    L = torch.tril(A) + torch.diag(torch.full((22,), 0.02, **f64))
+    mu = z0.contiguous()
+    inv_mass = torch.rand(22, **f64, generator=g) + 0.5
+    z = z0 + 0.05 * torch.randn(B, 22, **f64, generator=g)           # the last evaluated point
+    gt = torch.randn(B, 22, **f64, generator=g) * 100.0               # d log L / d theta there
+    ll = torch.randn(B, **f64, generator=g)
+    x = torch.randn(B, 22, **f64, generator=g)
+    p = torch.randn(B, 22, **f64, generator=g)
+    eps_dev = torch.full((1,), 0.0371, **f64)
+    for eps, ed in ((0.0371, None), (0.0, eps_dev)):
+        # reference: the gradient in its own launch, then the leapfrog update and transform
+        x1, p1, z1 = x.clone(), p.clone(), torch.empty_like(z)
+        lp1, gx1 = torch.empty_like(ll), torch.empty_like(x)
+        th1 = torch.empty(B, 22, dtype=torch.float32, device="cuda")
+        assert lib.gl_posterior_whitened_grad(B, z.data_ptr(), ll.data_ptr(), gt.data_ptr(), L.data_ptr(), pp,
+                                              lp1.data_ptr(), gx1.data_ptr(), st) == 0
+        assert lib.gl_hmc_leapfrog_whitened(B, x1.data_ptr(), p1.data_ptr(), gx1.data_ptr(), inv_mass.data_ptr(),
+                                            eps, ed.data_ptr() if ed is not None else None, 1.0, mu.data_ptr(),
+                                            L.data_ptr(), pp, z1.data_ptr(), th1.data_ptr(), st) == 0
+        # one launch, z overwritten in place
+        x2, p2, z2 = x.clone(), p.clone(), z.clone()
+        th2 = torch.empty_like(th1)
+        assert lib.gl_hmc_leapfrog_whitened_chain(B, x2.data_ptr(), p2.data_ptr(), z2.data_ptr(), gt.data_ptr(),
+                                                  inv_mass.data_ptr(), eps, ed.data_ptr() if ed is not None else None,
+                                                  1.0, mu.data_ptr(), L.data_ptr(), pp, th2.data_ptr(), st) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(x1, x2) and torch.equal(p1, p2) and torch.equal(z1, z2) and torch.equal(th1, th2)
+        assert not torch.equal(x2, x) and torch.isfinite(z2).all()
