@@ -359,7 +359,7 @@ class HMC:
 
     def __init__(self, q0: torch.Tensor, inv_mass: torch.Tensor, step_size: float, n_leapfrog: int,
                  system=None, logp_grad: Optional[Callable] = None, target=None, seed: int = 0,
-                 graphs: bool = False, group=None, fuse: bool = True):
+                 graphs: bool = False, group=None, fuse: bool = True, graph_chunk: int = 8):
         # with a process group, q0 holds every chain and this process runs its
         # shard of them; random draws are made for all chains and sliced
         self.group = group
@@ -401,8 +401,13 @@ class HMC:
         self.chees = torch.zeros(3, **f64)
         # one leapfrog update + one target evaluation, captured once per kick
         # (0.5 opens a trajectory, 1 continues it) and replayed; eps is read
-        # from eps_dev when the graph runs
+        # from eps_dev when the graph runs. Continuing steps are also captured
+        # graph_chunk at a time, so that most of a trajectory's steps share a
+        # graph launch.
         self.graphs = bool(graphs)
+        if int(graph_chunk) < 1:
+            raise ValueError("graph_chunk must be at least 1")
+        self.graph_chunk = int(graph_chunk)
         self.eps_dev = torch.full((1,), self.eps, **f64)
         self._eps_dev_val = self.eps
         self._graph = {}
@@ -430,8 +435,16 @@ class HMC:
             if self._eps_dev_val != self.eps:
                 self.eps_dev.fill_(self.eps)
                 self._eps_dev_val = self.eps
-            for l in range(L):
-                self._leapfrog_graph(0.5 if l == 0 else 1.0).replay()
+            # the first step, then the others in graphs of graph_chunk steps and single-step graphs
+            self._leapfrog_graph(0.5).replay()
+            rest = L - 1
+            if self.graph_chunk > 1:
+                chunk = self._leapfrog_graph(1.0, self.graph_chunk)
+                while rest >= self.graph_chunk:
+                    chunk.replay()
+                    rest -= self.graph_chunk
+            for _ in range(rest):
+                self._leapfrog_graph(1.0).replay()
         elif self.fused:
             for l in range(L):
                 if l == 0:
@@ -454,8 +467,8 @@ class HMC:
         self.grad_evals += B * L
         self.n_proposed += B
 
-    def _leapfrog_graph(self, kick: float):
-        g = self._graph.get(kick)
+    def _leapfrog_graph(self, kick: float, steps: int = 1):
+        g = self._graph.get((kick, steps))
         if g is None:
             g = torch.cuda.CUDAGraph()
             q32 = self.q32.data_ptr() if self.target.needs_q32 else None
@@ -463,16 +476,17 @@ class HMC:
                 self.target._buffers(self.B, self.dev)
             with torch.cuda.graph(g, capture_error_mode="thread_local"):
                 st = torch.cuda.current_stream(self.dev).cuda_stream
-                if self.fused and kick == 0.5:
-                    self.target.leapfrog_first(self.qp, self.p, self.gp, self.inv_mass, 0.0, self.eps_dev, kick)
-                elif self.fused:
-                    self.target.leapfrog_next(self.qp, self.p, self.inv_mass, 0.0, self.eps_dev, kick)
-                else:
-                    abi.gl_hmc_leapfrog_dev(self.B, self.d, self.qp.data_ptr(), self.p.data_ptr(),
-                                            self.gp.data_ptr(), self.inv_mass.data_ptr(), self.eps_dev.data_ptr(),
-                                            kick, q32, st)
-                    self.target(self.qp, self.q32, self.lp_new, self.gp)
-            self._graph[kick] = g
+                for _ in range(steps):
+                    if self.fused and kick == 0.5:
+                        self.target.leapfrog_first(self.qp, self.p, self.gp, self.inv_mass, 0.0, self.eps_dev, kick)
+                    elif self.fused:
+                        self.target.leapfrog_next(self.qp, self.p, self.inv_mass, 0.0, self.eps_dev, kick)
+                    else:
+                        abi.gl_hmc_leapfrog_dev(self.B, self.d, self.qp.data_ptr(), self.p.data_ptr(),
+                                                self.gp.data_ptr(), self.inv_mass.data_ptr(),
+                                                self.eps_dev.data_ptr(), kick, q32, st)
+                        self.target(self.qp, self.q32, self.lp_new, self.gp)
+            self._graph[(kick, steps)] = g
         return g
 
     def chees_gradient(self, t: float):

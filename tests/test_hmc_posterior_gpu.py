@@ -7,8 +7,9 @@
   acceptance at the 0.75 target, sample mean and covariance of the target;
 - the ChEES trajectory-length gradient kernel against its oracle, and
   ChEES-adapted HMC on a standard normal (trajectory length, moments);
-- leapfrog steps replayed as CUDA graphs give the eager path's chains bit
-  for bit (same kernels, same order, step size read from device memory),
+- leapfrog steps replayed as CUDA graphs (one or several steps per graph)
+  give the eager path's chains bit for bit (same kernels, same order, step
+  size read from device memory),
   and so does the leapfrog update fused into the whitened posterior;
 - gl_hmc_leapfrog_whitened_chain (the gradient at the last point, the
   update and the transform in one launch) gives the bits of
@@ -222,10 +223,12 @@ def test_graph_replay_matches_eager(mods):
     runs = []
     # eager and graph-replayed, with the leapfrog update fused into the
     # whitened posterior's first launch and as separate launches: same bits
-    for graphs, fuse in ((False, False), (False, True), (True, True), (True, False)):
+    # whatever the number of steps a graph holds
+    for graphs, fuse, chunk in ((False, False, 8), (False, True, 8), (True, True, 8), (True, False, 8),
+                                (True, True, 1), (True, True, 3), (True, False, 2)):
         target = hmc.WhitenedTarget(hmc.PosteriorTarget(s), z_truth, L)
         sm = hmc.HMC(x0, torch.ones(22, dtype=torch.float64, device="cuda"), 0.3, 5, target=target, seed=3,
-                     graphs=graphs, fuse=fuse)
+                     graphs=graphs, fuse=fuse, graph_chunk=chunk)
         assert sm.fused == fuse
         runs.append(sm.run_adaptive(n_burn=8, n_samples=5, adapt_trajectory=True))
     s.close()
