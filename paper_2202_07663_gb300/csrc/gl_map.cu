@@ -101,6 +101,24 @@ __global__ void k_posterior(int B, const double* __restrict__ z, const double* _
 // gl_hmc_affine_pullback). Two launches per evaluation instead of four.
 constexpr int kWhitenedThreads = 32;
 
+// The 22 x 22 factor into shared memory (blocks of kWhitenedThreads threads):
+// each thread issues all of its loads before its first store, so the block
+// waits for one round trip to L2 instead of one per row of the loop.
+__device__ __forceinline__ void load_factor(double* sL, const double* __restrict__ Lc) {
+  constexpr int N = GL_NPARAM * GL_NPARAM, PER = (N + kWhitenedThreads - 1) / kWhitenedThreads;
+  double v[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int i = int(threadIdx.x) + u * kWhitenedThreads;
+    v[u] = i < N ? Lc[i] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int i = int(threadIdx.x) + u * kWhitenedThreads;
+    if (i < N) sL[i] = v[u];
+  }
+}
+
 __global__ void __launch_bounds__(kWhitenedThreads) k_whitened_transform(int B, const double* __restrict__ x,
                                                                          const double* __restrict__ mu,
                                                                          const double* __restrict__ Lc,
@@ -108,7 +126,7 @@ __global__ void __launch_bounds__(kWhitenedThreads) k_whitened_transform(int B, 
                                                                          float* __restrict__ theta, PriorTable P) {
   constexpr int D = GL_NPARAM;
   __shared__ double sL[D * D];
-  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = Lc[i];
+  load_factor(sL, Lc);
   __syncthreads();
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
   for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < B; b += gridDim.x * wpb) {
@@ -138,7 +156,7 @@ __global__ void __launch_bounds__(kWhitenedThreads) k_leapfrog_whitened(int B, d
                                                                         float* __restrict__ theta, PriorTable P) {
   constexpr int D = GL_NPARAM;
   __shared__ double sL[D * D];
-  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = Lc[i];
+  load_factor(sL, Lc);
   __syncthreads();
   const double eps = eps_dev ? *eps_dev : eps_arg;
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -174,7 +192,7 @@ __global__ void __launch_bounds__(kWhitenedThreads) k_whitened_posterior(int B, 
   constexpr int D = GL_NPARAM;
   __shared__ double sL[D * D];
   __shared__ double sg[kWhitenedThreads / 32][32];
-  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = Lc[i];
+  load_factor(sL, Lc);
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   for (int b = blockIdx.x * wpb + w; b < B; b += gridDim.x * wpb) {
@@ -220,13 +238,19 @@ __global__ void __launch_bounds__(kWhitenedThreads) k_leapfrog_whitened_chain(in
   constexpr int D = GL_NPARAM;
   __shared__ double sL[D * D];
   __shared__ double sg[kWhitenedThreads / 32][32];
-  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = Lc[i];
+  load_factor(sL, Lc);
   __syncthreads();
   const double eps = eps_dev ? *eps_dev : eps_arg;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   for (int b = blockIdx.x * wpb + w; b < B; b += gridDim.x * wpb) {
     const size_t i = size_t(b) * D + lane;
+    // this lane's state, loaded up front (lane i reads and writes element i only)
+    double p0 = 0.0, x0 = 0.0, im = 0.0, m0 = 0.0;
     if (lane < D) {
+      p0 = p[i];
+      x0 = x[i];
+      im = inv_mass[lane];
+      m0 = mu[lane];
       double th, d, lj, dlj, lp, dlp;
       bij(P.e[lane], z[i], th, d, lj, dlj);
       logpdf(P.e[lane], th, lp, dlp);
@@ -238,12 +262,12 @@ __global__ void __launch_bounds__(kWhitenedThreads) k_leapfrog_whitened_chain(in
       double acc = 0.0;
       for (int r = lane; r < D; ++r) acc += sL[r * D + lane] * sg[w][r];
       const double g = acc;
-      const double pi = p[i] + kick * eps * g;
-      xi = x[i] + eps * inv_mass[lane] * pi;
+      const double pi = p0 + kick * eps * g;
+      xi = x0 + eps * im * pi;
       p[i] = pi;
       x[i] = xi;
     }
-    double acc = lane < D ? mu[lane] : 0.0;
+    double acc = lane < D ? m0 : 0.0;
     for (int j = 0; j < D; ++j) {   // every lane shuffles; lanes >= D read no matrix row
       const double xj = __shfl_sync(0xffffffffu, xi, j);
       if (lane < D && j <= lane) acc += sL[lane * D + j] * xj;
