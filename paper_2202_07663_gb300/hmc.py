@@ -84,16 +84,16 @@ class PosteriorTarget:
         from . import map as gmap
         self.system = system
         self.prior = gmap.prior_table(prior if prior is not None else gmap.PAPER_PRIOR)
-        self._buf = None
+        self._buf = {}   # per batch size, kept: captured graphs hold their pointers
 
     def __call__(self, q64, q32, lp_out, g_out):
         B = q64.shape[0]
-        if self._buf is None or self._buf[0].shape[0] != B:
+        if B not in self._buf:
             dev = q64.device
-            self._buf = (torch.empty(B, NPARAM, dtype=torch.float32, device=dev),
-                         torch.empty(B, dtype=torch.float64, device=dev),
-                         torch.empty(B, NPARAM, dtype=torch.float64, device=dev))
-        th, ll, gt = self._buf
+            self._buf[B] = (torch.empty(B, NPARAM, dtype=torch.float32, device=dev),
+                            torch.empty(B, dtype=torch.float64, device=dev),
+                            torch.empty(B, NPARAM, dtype=torch.float64, device=dev))
+        th, ll, gt = self._buf[B]
         lib = abi.lib_handle()
         st = torch.cuda.current_stream(q64.device).cuda_stream
         pp = ctypes.addressof(self.prior)
@@ -133,7 +133,7 @@ class WhitenedTarget:
         self.mu = mu.to(torch.float64).contiguous()
         self.L = torch.tril(L.to(torch.float64)).contiguous()
         self.d = self.mu.shape[0]
-        self._buf = None
+        self._buf = {}   # per batch size, kept: captured graphs and the chained steps hold their pointers
 
     def to_z(self, x: torch.Tensor) -> torch.Tensor:
         xc = x.to(torch.float64).contiguous()
@@ -143,13 +143,13 @@ class WhitenedTarget:
         return z
 
     def _buffers(self, B, dev):
-        if self._buf is None or self._buf[0].shape[0] != B:
+        if B not in self._buf:
             d = self.d
-            self._buf = (torch.empty(B, d, dtype=torch.float64, device=dev),
-                         torch.empty(B, d, dtype=torch.float32, device=dev),
-                         torch.empty(B, d, dtype=torch.float64, device=dev),
-                         torch.empty(B, dtype=torch.float64, device=dev))
-        return self._buf
+            self._buf[B] = (torch.empty(B, d, dtype=torch.float64, device=dev),
+                            torch.empty(B, d, dtype=torch.float32, device=dev),
+                            torch.empty(B, d, dtype=torch.float64, device=dev),
+                            torch.empty(B, dtype=torch.float64, device=dev))
+        return self._buf[B]
 
     @property
     def lens_posterior(self) -> bool:
