@@ -117,3 +117,26 @@ def test_product_never_imports_the_oracle():
     # and the oracle never includes the CUDA sources
     osrc = _read(os.path.join(ROOT, "oracle", "gl_oracle.cpp"))
     assert "gl_device" not in osrc and "gigalens.h" not in osrc
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without the built CUDA library every call raises."""
+    from paper_2202_07663_gb300 import abi
+    monkeypatch.setattr(abi, "_lib", None)
+    monkeypatch.setattr(abi, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libgigalens.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        abi.lib_handle()
+
+
+def test_benchmark_without_a_gpu_exits_nonzero():
+    """The benchmark's own arm has no host path: on a machine without a GPU it
+    stops with an error instead of timing anything."""
+    import subprocess
+    import sys
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    r = subprocess.run([sys.executable, "bench.py", "--steps", "1", "--warmup", "3", "--no-workloads",
+                        "--no-cpu-baseline"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0
+    assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
