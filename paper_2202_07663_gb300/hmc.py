@@ -438,7 +438,7 @@ class HMC:
             # the first step, then the others in graphs of graph_chunk steps and single-step graphs
             self._leapfrog_graph(0.5).replay()
             rest = L - 1
-            if self.graph_chunk > 1:
+            if 1 < self.graph_chunk <= rest:   # captured the first time a trajectory is long enough
                 chunk = self._leapfrog_graph(1.0, self.graph_chunk)
                 while rest >= self.graph_chunk:
                     chunk.replay()
