@@ -175,7 +175,8 @@ class WhitenedTarget:
     def leapfrog_next(self, x, p, inv_mass, eps, eps_dev, kick):
         """A later leapfrog step: the posterior gradient at the point of the
         last evaluation, the update and the transform in one launch
-        (gl_hmc_leapfrog_whitened_chain), then log L at the new point."""
+        (gl_hmc_leapfrog_whitened_chain), then log L and its gradient at
+        the new point, in this target's buffers."""
         B = x.shape[0]
         z, z32, gz, ll = self._buffers(B, x.device)
         st = torch.cuda.current_stream(x.device).cuda_stream
