@@ -82,9 +82,10 @@ def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
     return first.astype(np.int64)
 
 
-# DRAM bytes per launch of k_ray_adj from one ncu capture, valid only for the
-# kernel source it was taken on (sha256 prefix of gl_kernels.cu + gl_device.cuh).
 MUFU_RAY_ADJ = 12   # ex2/lg2/rcp per ray in the adjoint (EPL power, two Sersic profiles)
+# DRAM bytes per launch of k_ray_adj from one ncu capture, valid only for the
+# kernel source it was taken on (sha256 prefix of gl_kernels.cu + gl_device.cuh);
+# any other source reports null traffic until it is captured again.
 TRAFFIC = {"484cf7d85eb9f23b": 64.712192e6}   # ncu dram read + write, one launch at B = 4096
 
 
