@@ -1,7 +1,8 @@
 """The benchmark's reference arm (the FP64 oracle on the host cores) runs
 without a GPU: one JSON line with the benchmark's keys, the oracle's own
 rate in ``value``, ``cpu_baseline`` and ``e2e``, no host-device bytes and at
-least three warm-up steps; ranks other than 0 print nothing and exit 0."""
+least three warm-up steps; ranks other than 0 print nothing and exit 0.
+The clocks record of the benchmark line is parsed from nvidia-smi samples."""
 import json
 import os
 import subprocess
@@ -42,3 +43,22 @@ def test_reference_arm_json_line():
 def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1"})
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_clock_summary_parses_throttle_reasons():
+    """The clocks record of the benchmark line: median SM clock under load,
+    the maximum clock, and which throttle reasons were active at any sample."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.Clocks(0)
+    c.lines = ["0, 2070, 2070, 850.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "0, 2040, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 900.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "0, [N/A], 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage"]
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines = ["0, 1500, 2070, 700.0, 0x0000000000000048, Active, Not Active, Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary() is None
