@@ -2,8 +2,10 @@
 without a GPU: one JSON line with the benchmark's keys, the oracle's own
 rate in ``value``, ``cpu_baseline`` and ``e2e``, no host-device bytes and at
 least three warm-up steps; ranks other than 0 print nothing and exit 0.
-The clocks record of the benchmark line is parsed from nvidia-smi samples."""
+The clocks record of the benchmark line is parsed from nvidia-smi samples,
+and the EPL series length behind its flop count follows its stated rule."""
 import json
+import math
 import os
 import subprocess
 import sys
@@ -62,3 +64,36 @@ def test_clock_summary_parses_throttle_reasons():
     assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     c.lines = []
     assert c.summary() is None
+
+
+def test_series_terms_by_brute_force():
+    """The per-vector EPL series length behind the roofline's flop count:
+    the smallest N with |a_(N+1)| f^(N+1) / (1 - f max(1, c_(N+2))) <= tol,
+    a_n = c_1 ... c_n, c_k = (2k - 2 + t) / (2k + 2 - t), t = gamma - 1,
+    f = |e| (at least one term in the adjoint), by a plain loop."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+
+    def brute(gamma, e1, e2, adjoint):
+        f, t = math.hypot(e1, e2), gamma - 1.0
+        c = lambda k: (2 * k - 2 + t) / (2 * k + 2 - t)   # noqa: E731
+        a = 1.0
+        for N in range(0, bench.NMAX + 1):
+            a *= c(N + 1)                                  # a_(N+1)
+            r = min(f * max(1.0, c(N + 2)), 0.999999)
+            if abs(a) * f ** (N + 1) / (1.0 - r) <= bench.SERIES_TOL:
+                return max(N, 1) if adjoint else N
+        return max(bench.NMAX, 1) if adjoint else bench.NMAX
+
+    rng = np.random.default_rng(9)
+    P = np.zeros((400, 22))
+    P[:, 1] = rng.uniform(1.5, 2.5, 400)
+    P[:, 2:4] = rng.normal(0.0, 0.15, (400, 2))
+    P[:4, 2:4] = 0.0                          # circular: no series term needed
+    P[4:8, 2] = [0.5, 0.7, 0.9, 0.95]         # long series
+    for adjoint in (False, True):
+        N = bench.series_terms(P, adjoint)
+        ref = [brute(P[i, 1], P[i, 2], P[i, 3], adjoint) for i in range(len(P))]
+        assert list(N) == ref
+    assert list(bench.series_terms(P[:4], False)) == [0] * 4 and list(bench.series_terms(P[:4], True)) == [1] * 4
