@@ -1,6 +1,7 @@
 """Host-only checks of the C ABI: the library builds for sm_103a, loads, and
 exports every function that include/gigalens.h declares; the Python binding
-covers the same names. No kernel is launched."""
+covers the same names; the header is plain C and a C program links against
+the library. No kernel is launched."""
 import os
 import re
 
@@ -140,3 +141,34 @@ def test_benchmark_without_a_gpu_exits_nonzero():
                         "--no-cpu-baseline"], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/gigalens.h compiles as strict C99 and as C++; a C program that
+    takes the address of every declared call links against the library and
+    runs its GPU-free calls."""
+    import shutil
+    import subprocess
+    from paper_2202_07663_gb300 import abi
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    names = declared_functions()
+    src = tmp_path / "abi_probe.c"
+    src.write_text('#include <stdio.h>\n#include "gigalens.h"\n'
+                   "typedef void (*fn_t)(void);\n"
+                   "static fn_t table[] = {" + ", ".join("(fn_t)%s" % n for n in names) + "};\n"
+                   "int main(void) {\n"
+                   "  printf(\"%d %s %s\\n\", (int)(sizeof table / sizeof table[0]), gl_error_string(GL_ERR_INVALID_ARG),"
+                   " gl_kernel_name(GL_K_RAY_ADJ));\n"
+                   "  return gl_loglik(NULL, NULL, 1, NULL, NULL, NULL) == GL_ERR_INVALID_ARG ? 0 : 1;\n}\n")
+    inc = os.path.join(ROOT, "include")
+    libdir = os.path.dirname(abi.LIB_PATH)
+    exe = tmp_path / "abi_probe"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-Wno-cast-function-type",
+                    "-I", inc, str(src), "-o", str(exe), "-L", libdir, "-lgigalens", "-Wl,-rpath," + libdir],
+                   check=True, capture_output=True, text=True)
+    subprocess.run(["g++", "-std=c++17", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", "c++",
+                    "-I", inc, "-"], input='#include "gigalens.h"\n', check=True, capture_output=True, text=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split() == [str(len(names)), "GL_ERR_INVALID_ARG", "k_ray_adj"]
