@@ -12,7 +12,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
-from typing import Optional, Sequence
+from typing import Sequence
 
 import numpy as np
 

@@ -14,7 +14,6 @@ import dataclasses
 import time
 from typing import Optional
 
-import numpy as np
 import torch
 
 from . import abi

@@ -3,7 +3,6 @@ returns GL_ERR_INVALID_ARG (-1) before launching anything, and B = 0 is a
 no-op where the header says so."""
 import ctypes
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

@@ -11,8 +11,6 @@ import subprocess
 import sys
 import tempfile
 
-import pytest
-
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "gl_oracle.cpp")
 

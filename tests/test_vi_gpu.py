@@ -13,8 +13,6 @@
   z - mu from z, so an L far from diagonal, which a much larger step would
   make, costs it digits that the GPU, working with the draws, keeps.)
 """
-import math
-
 import numpy as np
 import pytest
 

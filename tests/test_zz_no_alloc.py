@@ -8,8 +8,6 @@ static scratch array. This file is named to be collected last, so that a
 run stopping at its first failure has already run every other test; it also
 passes on its own in a fresh process.
 """
-import ctypes
-
 import numpy as np
 import pytest
 
