@@ -32,8 +32,20 @@
 // The Sersic profile (Eq. Sersic) uses the same quadratic form for its
 // elliptical radius: q x_l^2 + y_l^2 / q = A dx^2 + 2 B dx dy + C dy^2 with
 // A = (1 + e^2 - 2 e1)/(1 - e^2), B = -2 e2/(1 - e^2), C = (1 + e^2 + 2 e1)/(1 - e^2),
-// and is evaluated as I = I0 exp2(k1 (1 - s)), s = exp2(c1 log2(rho^2) + c0),
-// with c1 = 1/(2n), c0 = -log2(R_eff)/n, k1 = b_n / ln 2, b_n = 1.9992 n - 0.3271.
+// and is evaluated as I = I0 exp2(k1 (1 - s)), s = exp2(c1 log2(rho^2 / R_eff^2)),
+// with c1 = 1/(2n), k1 = b_n / ln 2, b_n = 1.9992 n - 0.3271. The 1/R_eff^2 is
+// folded into A, B, C, so log2 s has no cancelling offset.
+//
+// FP32 accuracy. The likelihood of a sharp, high signal-to-noise image is so
+// steep in the parameters that an error which acts like a small parameter
+// change (the same for every ray) moves the gradient by the Hessian times
+// that change; rounding errors that differ from ray to ray mostly cancel in
+// the pixel sums. So everything that is the same for all rays of a vector is
+// formed in FP64 and rounded once: the ray grid (x = n h with n an integer
+// and h = pixel_scale / (2k) as a pair of floats, instead of x0 + j sub with
+// both constants rounded, which shifted the whole grid by ~1e-7 arcsec),
+// log2(thetaE sqrt(1 - |eps|^2)) as a pair of floats, and the Sersic
+// coefficients with 1/R_eff^2 folded in.
 #pragma once
 
 #include <cstdint>
@@ -55,9 +67,10 @@ enum Acc {
 };
 
 struct LightC {
-  float A, B2, C;          // rho^2 = A dx^2 + B2 dx dy + C dy^2 (B2 = 2B)
+  float A, B2, C;          // rho^2 / R_eff^2 = A dx^2 + B2 dx dy + C dy^2 (B2 = 2B)
   float x, y;              // centre
-  float c1, c0;            // log2 s = c1 log2(rho^2) + c0
+  float c1;                // log2 s = c1 log2(rho^2 / R_eff^2)
+  float r2min;             // RHO2_MIN / R_eff^2: floor of rho^2 / R_eff^2
   float k1;                // b_n / ln 2
   float I0;                // amplitude
   float A1, B21, C1;       // d(A, B2, C)/d e1
@@ -67,10 +80,10 @@ struct LightC {
 struct __align__(16) VecConst {
   float xc, yc;            // EPL centre
   float e1, e2;            // EPL complex ellipticity
-  float om1, op1;          // 1 - e1, 1 + e1
+  float lc;                // log2(thetaE sqrt(1 - |eps|^2)) rounded: log2(thetaE / rho) = lc - log2(|w|^2) / 2
+  float tlc_lo;            // t x (the rounding error of lc)
   float t;                 // gamma - 1
-  float log2_thetaE;
-  float inv_1me2;          // 1 / (1 - |eps|^2)
+  float w2min;             // RHO2_MIN (1 - |eps|^2): |w|^2 below it is rho < 1e-6 arcsec
   float g1, g2;            // external shear
   int nterms;              // series terms of F (0 <= N <= NMAX); < 0 marks an invalid vector
   int nterms_adj;          // series terms in the adjoint, max(N, 1)
@@ -79,7 +92,7 @@ struct __align__(16) VecConst {
   float kap_c;             // (2 - t) / 2: kappa = kap_c (thetaE/rho)^t
   float omt;               // 1 - t
   float e1i, e2i;          // e1, e2 times 1 / (1 - |eps|^2)
-  float pad_[3];
+  float pad_[4];
   LightC light[2];         // [0] lens light at theta, [1] source at beta
   float an[NMAX];          // a_n = c_1 ... c_n, n = 1..NMAX at index n-1
   float ant[NMAX];         // d a_n / d t
@@ -93,8 +106,8 @@ struct Seg {
   const float* sigma2;     // sigma_bkg^2 [H, W]
   const float* psf;        // [K, K]
   int H, W, K, k;
-  float sub;               // pixel_scale / k
-  float x0, y0;            // coordinates of supersampled pixel (0, 0)
+  float hh, hl;            // h = pixel_scale / (2k) = hh + hl (a pair of floats)
+  int nx0, ny0;            // 1 - kW, 1 - kH: subpixel (i, j) sits at ((2j + nx0) h, (2i + ny0) h)
   float inv_gain;          // 1 / (G t_exp), 0 drops the Poisson term
   // this call
   const float* params;     // [B, 22]
@@ -144,6 +157,15 @@ __device__ __forceinline__ float rcp(float x) {
   return y;
 }
 
+// Coordinate n h of the supersampled grid (n = 2j + nx0, an odd or even
+// integer) from h = hh + hl: the exact product n hh, the small n hl added
+// before the one rounding, so a ray's position is off by at most about half
+// an ulp of itself and the grid is neither shifted nor scaled.
+__device__ __forceinline__ float grid_coord(int n, float hh, float hl) {
+  const float f = float(n);
+  return fmaf(f, hh, f * hl);
+}
+
 // --------------------------------------------------------- packed pairs ---
 // Two rays of one parameter vector evaluated in lockstep with Blackwell's
 // packed FP32 instructions (one f32x2 FMA/MUL/ADD does the arithmetic of two
@@ -178,13 +200,29 @@ __device__ __forceinline__ F2 geT(F2 a, F2 b) {
   return {make_float2(a.v.x >= b.v.x ? 1.f : 0.f, a.v.y >= b.v.y ? 1.f : 0.f)};
 }
 
-// Elliptical Sersic at (px, py), generic in the ray type.
+// log2 without the bias of lg2.approx. lg2.approx.ftz measured on GB300
+// (2^26 arguments against FP64): error +6e-8 on average for x in [1/2, 2]
+// and about +3e-8 |log2 x| elsewhere, always of one sign, which acts on the
+// Sersic profile like a change of its parameters. One correction step: with
+// y0 = lg2.approx(x), log2 x = y0 + log2(x 2^-y0) and x 2^-y0 - 1 (one FMA on
+// ex2.approx(-y0), whose mean error is -8e-9) is ln 2 times that remainder
+// to first order (the remainder is ~1e-7, its square negligible).
+__device__ __forceinline__ float lg2c(float x) {
+  const float y0 = lg2(x);
+  const float d = fmaf(x, ex2(-y0), -1.f);
+  return fmaf(d, 1.44269504088896341f, y0);
+}
+__device__ __forceinline__ float lg2cT(float a) { return lg2c(a); }
+__device__ __forceinline__ F2 lg2cT(F2 a) { return {make_float2(lg2c(a.v.x), lg2c(a.v.y))}; }
+
+// Elliptical Sersic at (px, py), generic in the ray type; the forward model,
+// so its log2 is the unbiased one (log L sums the model over every pixel).
 template <class T>
 __device__ __forceinline__ T sersic_fwd_T(const LightC& L, T px, T py) {
   const T dx = px - sp<T>(L.x), dy = py - sp<T>(L.y);
   T r2 = fmaT(sp<T>(L.A) * dx, dx, fmaT(sp<T>(L.B2) * dx, dy, sp<T>(L.C) * dy * dy));
-  r2 = maxT(r2, sp<T>(RHO2_MIN));
-  const T s = ex2T(fmaT(sp<T>(L.c1), lg2T(r2), sp<T>(L.c0)));
+  r2 = maxT(r2, sp<T>(L.r2min));
+  const T s = ex2T(sp<T>(L.c1) * lg2cT(r2));
   return sp<T>(L.I0) * ex2T(fmaT(sp<T>(-L.k1), s, sp<T>(L.k1)));
 }
 
@@ -193,13 +231,13 @@ __device__ __forceinline__ T sersic_fwd_T(const LightC& L, T px, T py) {
 template <class T>
 __device__ __forceinline__ void epl_fwd_T(const VecConst& V, const float* an, T x, T y, T& ax, T& ay) {
   const T dx = x - sp<T>(V.xc), dy = y - sp<T>(V.yc);
-  const T wr = fmaT(sp<T>(V.om1), dx, sp<T>(-V.e2) * dy);
-  const T wi = fmaT(sp<T>(V.op1), dy, sp<T>(-V.e2) * dx);
+  // w = z - eps conj(z) = (dx - e1 dx - e2 dy, dy + e1 dy - e2 dx)
+  const T wr = fmaT(sp<T>(-V.e1), dx, fmaT(sp<T>(-V.e2), dy, dx));
+  const T wi = fmaT(sp<T>(V.e1), dy, fmaT(sp<T>(-V.e2), dx, dy));
   const T w2 = fmaT(wr, wr, wi * wi);
-  const T r2raw = w2 * sp<T>(V.inv_1me2);
-  const T keep = geT(r2raw, sp<T>(RHO2_MIN));
-  const T r2 = maxT(r2raw, sp<T>(RHO2_MIN));
-  const T S = keep * ex2T(sp<T>(V.t) * fmaT(sp<T>(-0.5f), lg2T(r2), sp<T>(V.log2_thetaE)));
+  const T keep = geT(w2, sp<T>(V.w2min));
+  const T lw = lg2T(maxT(w2, sp<T>(V.w2min)));
+  const T S = keep * ex2T(fmaT(sp<T>(V.t), fmaT(sp<T>(-0.5f), lw, sp<T>(V.lc)), sp<T>(V.tlc_lo)));
   const T iw2 = rcpT(maxT(w2, sp<T>(1e-30f)));
   const T nwi = -wi;
   const T vr = fmaT(wr, wr, nwi * wi) * iw2;

@@ -123,29 +123,60 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // ------------------------------------------------------------- k_setup ----
 
-// Derived constants of one Sersic profile (R_eff, n, e1, e2, xc, yc, I0).
-__device__ void setup_light(const float* p, LightC& L, bool& ok) {
-  const float R = p[0], n = p[1], e1 = p[2], e2 = p[3];
-  const float e2s = fmaf(e1, e1, e2 * e2);
-  ok = ok && R > 0.f && n > 0.f && e2s < 1.f;
-  const float iD = 1.0f / (1.0f - e2s), iD2 = iD * iD;
-  L.A = (1.f + e2s - 2.f * e1) * iD;
-  L.B2 = -4.f * e2 * iD;
-  L.C = (1.f + e2s + 2.f * e1) * iD;
+// Derived constants of one Sersic profile (R_eff, n, e1, e2, xc, yc, I0),
+// formed in FP64 and rounded once: each is the same for every ray, so its
+// rounding acts like a change of the parameters. 1/R_eff^2 is folded into
+// the quadratic form (R_eff^2 floored at 1e-30 so that no coefficient
+// overflows). One FP64 division. Validity (R > 0, n > 0, |e| < 1) is
+// checked elsewhere.
+__device__ void setup_light(const float* p, LightC& L) {
+  const float R = p[0], n = p[1];
+  const double d1 = p[2], d2 = p[3], dn = n;
+  const double e2s = d1 * d1 + d2 * d2;
+  const double R2 = fmax(double(R) * double(R), 1e-30), om = 1.0 - e2s;
+  const double iDR = 1.0 / (om * R2);        // 1 / ((1 - e^2) R^2)
+  const double iD2R = iDR * iDR * R2;        // 1 / ((1 - e^2)^2 R^2)
+  L.A = float((1.0 + e2s - 2.0 * d1) * iDR);
+  L.B2 = float(-4.0 * d2 * iDR);
+  L.C = float((1.0 + e2s + 2.0 * d1) * iDR);
   L.x = p[4];
   L.y = p[5];
-  L.c1 = 0.5f / n;
-  L.c0 = -log2f(R) / n;
-  const float bn = fmaf(1.9992f, n, -0.3271f);
-  L.k1 = bn * 1.44269504088896341f;   // b_n / ln 2
+  L.c1 = __fdiv_rn(0.5f, n);                 // one rounding, as in FP64
+  L.r2min = float(double(RHO2_MIN) * om * iDR);
+  L.k1 = float((1.9992 * dn - 0.3271) * 1.4426950408889634074);   // b_n / ln 2
   L.I0 = p[6];
   // derivatives of (A, 2B, C) with respect to e1 and e2
-  L.A1 = 2.f * (e2 * e2 - (1.f - e1) * (1.f - e1)) * iD2;
-  L.B21 = -8.f * e1 * e2 * iD2;
-  L.C1 = 2.f * ((1.f + e1) * (1.f + e1) - e2 * e2) * iD2;
-  L.A2 = 4.f * e2 * (1.f - e1) * iD2;
-  L.B22 = -4.f * (1.f - e1 * e1 + e2 * e2) * iD2;
-  L.C2 = 4.f * e2 * (1.f + e1) * iD2;
+  L.A1 = float(2.0 * (d2 * d2 - (1.0 - d1) * (1.0 - d1)) * iD2R);
+  L.B21 = float(-8.0 * d1 * d2 * iD2R);
+  L.C1 = float(2.0 * ((1.0 + d1) * (1.0 + d1) - d2 * d2) * iD2R);
+  L.A2 = float(4.0 * d2 * (1.0 - d1) * iD2R);
+  L.B22 = float(-4.0 * (1.0 - d1 * d1 + d2 * d2) * iD2R);
+  L.C2 = float(4.0 * d2 * (1.0 + d1) * iD2R);
+}
+
+// The FP64-formed constants of one vector, part 0 the EPL (log2(thetaE /
+// rho) = lc - log2(|w|^2)/2 with lc = log2(thetaE sqrt(1 - |eps|^2)) as a
+// rounded float plus t x its rounding error), parts 1 and 2 the two light
+// profiles. GB300's FP64 pipe is narrow, so k_setup gives these to
+// different lanes of one warp, several vectors per warp.
+template <class Src>
+__device__ void setup_fp64_part(const Src& src, int item, int part) {
+  int b;
+  const Seg* s = src.vec_seg(item, b);
+  VecConst* V = s->vc + b;
+  const float* pp = s->params + size_t(b) * NPARAM;
+  if (part == 0) {
+    const double e1 = pp[2], e2 = pp[3], thetaE = pp[0];
+    const double om = 1.0 - (e1 * e1 + e2 * e2);
+    const double lc = 0.5 * log2(thetaE * thetaE * om);
+    V->lc = float(lc);
+    V->tlc_lo = float((double(pp[1]) - 1.0) * (lc - double(float(lc))));
+    V->w2min = float(double(RHO2_MIN) * om);
+  } else {
+    LightC L;
+    setup_light(pp + (part == 1 ? 8 : 15), L);
+    V->light[part - 1] = L;
+  }
 }
 
 // Truncation target of the EPL series F = sum a_n u^n, |u| = f, a_n = c_1 ... c_n:
@@ -230,15 +261,26 @@ __device__ __forceinline__ void series_coeffs(int lane, float t, VecConst* V) {
   }
 }
 
-// One warp per vector: lanes 0..21 check one parameter each, lane 0 derives
-// the EPL constants, lanes 1 and 2 the two light profiles; all lanes compute
-// series coefficients and, by ballot, the term count. FP32 throughout: every
-// constant feeds FP32 arithmetic, and GB300's FP64 pipe is narrow.
+// A block takes its vectors wpb (warps per block) at a time. First the FP64
+// constants: thread 3 v + part of the block forms part `part` of vector v
+// of the chunk (setup_fp64_part), so that one warp's FP64 instructions serve
+// several vectors. Then one warp per vector: lanes 0..21 check one parameter
+// each, lane 0 the EPL's FP32 constants, lanes 1 and 2 the validity of the
+// light profiles; all lanes compute the series coefficients and, by ballot,
+// the term count (FP32: every constant feeds FP32 arithmetic). The two
+// phases write disjoint fields of VecConst.
 template <class Src>
 __global__ void k_setup(const __grid_constant__ Src src) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  for (int item = blockIdx.x * wpb + (threadIdx.x >> 5); item < src.nvec(); item += gridDim.x * wpb) {
+  const int nvec = src.nvec();
+  for (int base = blockIdx.x * wpb; base < nvec; base += gridDim.x * wpb) {
+    if (int(threadIdx.x) < 3 * wpb) {
+      const int item = base + threadIdx.x / 3;
+      if (item < nvec) setup_fp64_part(src, item, threadIdx.x % 3);
+    }
+    const int item = base + (threadIdx.x >> 5);
+    if (item >= nvec) continue;   // warp-uniform
     int b;
     const Seg* s = src.vec_seg(item, b);
     VecConst* V = s->vc + b;
@@ -254,11 +296,7 @@ __global__ void k_setup(const __grid_constant__ Src src) {
       V->yc = pp[5];
       V->e1 = e1;
       V->e2 = e2;
-      V->om1 = 1.f - e1;
-      V->op1 = 1.f + e1;
       V->t = t;
-      V->log2_thetaE = log2f(thetaE);
-      V->inv_1me2 = i1me2;
       V->g1 = pp[6];
       V->g2 = pp[7];
       V->th = 0.5f * t;
@@ -268,9 +306,8 @@ __global__ void k_setup(const __grid_constant__ Src src) {
       V->e1i = e1 * i1me2;
       V->e2i = e2 * i1me2;
     } else if (lane == 1 || lane == 2) {
-      LightC L;
-      setup_light(pp + (lane == 1 ? 8 : 15), L, ok);
-      V->light[lane - 1] = L;
+      const float* lp = pp + (lane == 1 ? 8 : 15);
+      ok = ok && lp[0] > 0.f && lp[1] > 0.f && fmaf(lp[2], lp[2], lp[3] * lp[3]) < 1.f;
     }
     ok = __all_sync(0xffffffffu, ok);
     // term count and coefficients over the first 32 candidates; the other
@@ -331,9 +368,9 @@ __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd(const __gr
       F2 acc = sp<F2>(0.f);
       if (valid) {
         for (int a = 0; a < k; ++a) {
-          const F2 y = {make_float2(fmaf(float(ip * k + a), ss.sub, ss.y0), fmaf(float(iq * k + a), ss.sub, ss.y0))};
+          const F2 y = {make_float2(grid_coord(2 * (ip * k + a) + ss.ny0, ss.hh, ss.hl), grid_coord(2 * (iq * k + a) + ss.ny0, ss.hh, ss.hl))};
           for (int c = 0; c < k; ++c) {
-            const F2 x = {make_float2(fmaf(float(jp * k + c), ss.sub, ss.x0), fmaf(float(jq * k + c), ss.sub, ss.x0))};
+            const F2 x = {make_float2(grid_coord(2 * (jp * k + c) + ss.nx0, ss.hh, ss.hl), grid_coord(2 * (jq * k + c) + ss.nx0, ss.hh, ss.hl))};
             acc = acc + ray_intensity_T(sv, sv.an, x, y);
           }
         }
@@ -387,9 +424,9 @@ __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd_basis(cons
       F2 acc_l = sp<F2>(0.f), acc_s = sp<F2>(0.f);
       if (valid) {
         for (int a = 0; a < k; ++a) {
-          const F2 y = {make_float2(fmaf(float(ip * k + a), ss.sub, ss.y0), fmaf(float(iq * k + a), ss.sub, ss.y0))};
+          const F2 y = {make_float2(grid_coord(2 * (ip * k + a) + ss.ny0, ss.hh, ss.hl), grid_coord(2 * (iq * k + a) + ss.ny0, ss.hh, ss.hl))};
           for (int c = 0; c < k; ++c) {
-            const F2 x = {make_float2(fmaf(float(jp * k + c), ss.sub, ss.x0), fmaf(float(jq * k + c), ss.sub, ss.x0))};
+            const F2 x = {make_float2(grid_coord(2 * (jp * k + c) + ss.nx0, ss.hh, ss.hl), grid_coord(2 * (jq * k + c) + ss.nx0, ss.hh, ss.hl))};
             F2 ax, ay;
             epl_fwd_T(sv, sv.an, x, y, ax, ay);
             const F2 bx = x - ax - fmaT(sp<F2>(sv.g1), x, sp<F2>(sv.g2) * y);
@@ -425,9 +462,9 @@ __device__ __forceinline__ void light_adj(const LightC& L, T px, T py, T g, T* a
   const T dx = px - sp<T>(L.x), dy = py - sp<T>(L.y);
   const T dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
   const T r2raw = fmaT(sp<T>(L.A), dxx, fmaT(sp<T>(L.B2), dxy, sp<T>(L.C) * dyy));
-  const T keep = geT(r2raw, sp<T>(RHO2_MIN));      // 0 where the radius is floored
-  const T r2 = maxT(r2raw, sp<T>(RHO2_MIN));
-  const T ls = fmaT(sp<T>(L.c1), lg2T(r2), sp<T>(L.c0));
+  const T keep = geT(r2raw, sp<T>(L.r2min));       // 0 where the radius is floored
+  const T r2 = maxT(r2raw, sp<T>(L.r2min));
+  const T ls = sp<T>(L.c1) * lg2T(r2);
   const T s = ex2T(ls);
   const T e = ex2T(fmaT(sp<T>(-L.k1), s, sp<T>(L.k1)));
   const T I = sp<T>(L.I0) * e;
@@ -458,14 +495,12 @@ __device__ __forceinline__ void ray_adj(const VecConst& V, const float* an, cons
 
   // EPL deflection with the pieces of its parameter derivatives
   const T dx = x - sp<T>(V.xc), dy = y - sp<T>(V.yc);
-  const T wr = fmaT(sp<T>(V.om1), dx, sp<T>(-V.e2) * dy);
-  const T wi = fmaT(sp<T>(V.op1), dy, sp<T>(-V.e2) * dx);
+  const T wr = fmaT(sp<T>(-V.e1), dx, fmaT(sp<T>(-V.e2), dy, dx));
+  const T wi = fmaT(sp<T>(V.e1), dy, fmaT(sp<T>(-V.e2), dx, dy));
   const T w2 = fmaT(wr, wr, wi * wi);
-  const T r2raw = w2 * sp<T>(V.inv_1me2);
-  const T keep = geT(r2raw, sp<T>(RHO2_MIN));
-  const T r2 = maxT(r2raw, sp<T>(RHO2_MIN));
-  const T lrho = fmaT(sp<T>(-0.5f), lg2T(r2), sp<T>(V.log2_thetaE));  // log2(thetaE / rho)
-  const T S = keep * ex2T(sp<T>(V.t) * lrho);
+  const T keep = geT(w2, sp<T>(V.w2min));
+  const T lrho = fmaT(sp<T>(-0.5f), lg2T(maxT(w2, sp<T>(V.w2min))), sp<T>(V.lc));  // log2(thetaE / rho)
+  const T S = keep * ex2T(fmaT(sp<T>(V.t), lrho, sp<T>(V.tlc_lo)));
   const T iw2 = rcpT(maxT(w2, sp<T>(1e-30f)));
   const T nwi = -wi;
   const T vr = fmaT(wr, wr, nwi * wi) * iw2;
@@ -594,9 +629,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, MINB) k_ray_adj(const __grid_cons
           const int iq = q / W, jq = q - iq * W;
           const F2 g = {make_float2(gpre[p], gpre[q])};
           for (int a = 0; a < k; ++a) {
-            const F2 y = {make_float2(fmaf(float(ip * k + a), ss.sub, ss.y0), fmaf(float(iq * k + a), ss.sub, ss.y0))};
+            const F2 y = {make_float2(grid_coord(2 * (ip * k + a) + ss.ny0, ss.hh, ss.hl), grid_coord(2 * (iq * k + a) + ss.ny0, ss.hh, ss.hl))};
             for (int c = 0; c < k; ++c) {
-              const F2 x = {make_float2(fmaf(float(jp * k + c), ss.sub, ss.x0), fmaf(float(jq * k + c), ss.sub, ss.x0))};
+              const F2 x = {make_float2(grid_coord(2 * (jp * k + c) + ss.nx0, ss.hh, ss.hl), grid_coord(2 * (jq * k + c) + ss.nx0, ss.hh, ss.hl))};
               ray_adj(sv, sv.an, sv.ant, x, y, g, acc);
             }
           }
@@ -612,8 +647,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, MINB) k_ray_adj(const __grid_cons
           const int pb = base + r2 / kk, sb = r2 - (pb - base) * kk;
           const int ia = pa / W, ja = pa - ia * W, ib = pb / W, jb = pb - ib * W;
           const int aa = sa / k, ca = sa - aa * k, ab = sb / k, cb = sb - ab * k;
-          const F2 y = {make_float2(fmaf(float(ia * k + aa), ss.sub, ss.y0), fmaf(float(ib * k + ab), ss.sub, ss.y0))};
-          const F2 x = {make_float2(fmaf(float(ja * k + ca), ss.sub, ss.x0), fmaf(float(jb * k + cb), ss.sub, ss.x0))};
+          const F2 y = {make_float2(grid_coord(2 * (ia * k + aa) + ss.ny0, ss.hh, ss.hl), grid_coord(2 * (ib * k + ab) + ss.ny0, ss.hh, ss.hl))};
+          const F2 x = {make_float2(grid_coord(2 * (ja * k + ca) + ss.nx0, ss.hh, ss.hl), grid_coord(2 * (jb * k + cb) + ss.nx0, ss.hh, ss.hl))};
           const F2 g = {make_float2(gpre[pa], has2 ? gpre[pb] : 0.f)};
           ray_adj(sv, sv.an, sv.ant, x, y, g, acc);
         }
@@ -624,9 +659,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, MINB) k_ray_adj(const __grid_cons
           const int i = p / W, j = p - i * W;
           const float g = gpre[p];
           for (int a = 0; a < k; ++a) {
-            const float y = fmaf(float(i * k + a), ss.sub, ss.y0);
+            const float y = grid_coord(2 * (i * k + a) + ss.ny0, ss.hh, ss.hl);
             for (int c = 0; c < k; ++c) {
-              const float x = fmaf(float(j * k + c), ss.sub, ss.x0);
+              const float x = grid_coord(2 * (j * k + c) + ss.nx0, ss.hh, ss.hl);
               ray_adj(sv, sv.an, sv.ant, x, y, g, acc);
             }
           }
@@ -1471,7 +1506,7 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
                             bool short_tiles = false) {
   const int sms = num_sms();
   cudaError_t e;
-  const int vthreads = 128, wpb = vthreads / 32;
+  const int vthreads = 256, wpb = vthreads / 32;
   int sgrid = (nvec + wpb - 1) / wpb;
   int fgrid = (nvec + FINAL_THREADS - 1) / FINAL_THREADS;
   int wgrid = (nvec + FINAL_THREADS / 32 - 1) / (FINAL_THREADS / 32);
@@ -1605,7 +1640,7 @@ cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size
   cudaError_t e;
   DevTable src{d_hdr, d_segs, 0};
   hooks->before(GL_K_SETUP, st);
-  k_setup<DevTable><<<sms * 4, 128, 0, st>>>(src);
+  k_setup<DevTable><<<sms * 2, 256, 0, st>>>(src);
   if ((e = hooks->after(GL_K_SETUP, st)) != cudaSuccess) return e;
   hooks->before(GL_K_RAY_FWD, st);
   k_ray_fwd<DevTable><<<sms * GL_FWD_MINB, FWD_THREADS, 0, st>>>(src);

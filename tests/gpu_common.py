@@ -1,31 +1,30 @@
 """Shared helpers of the GPU parity tests: seeded systems whose observed image
 comes from the FP64 oracle, and the parity tolerances.
 
-Tolerances (FP32 GPU path vs FP64 oracle), per vector:
-  log L:  |l_gpu - l_ref| <= 1e-4 * max(|l_ref|, 1)  [+ the conditioned term below]
+Plain tolerances (FP32 GPU path vs FP64 oracle), per vector:
+  log L:  |l_gpu - l_ref| <= 1e-4 * max(|l_ref|, 1)
   grad:   |g_gpu - g_ref|_i <= 1e-3 * (|g_ref,i| + 1e-2 * max_j |g_ref,j|)
   images: |M_gpu - M_ref| <= 1e-4 * |M_ref| + 1e-5 * max |M_ref|
+The gradient's floor term (1e-2 of the vector's largest component) is there
+because single components cross zero.
 
-Where the gradient is a near-cancelling pixel sum (at the posterior mode,
-or dominated by a Sersic cusp), the FP32 model error itself sets the floor:
-a relative error eps in the model image M and its Jacobian J = dM/dparams
-moves component i by at most
-  eps * C_i,   C_i = sum_pixels (|g| + |M dg/dM|) |J_i|,
-with g = d log L / d M. Those cases add eps * C_i to the gradient tolerance;
-the oracle supplies M and J. log L itself is a sum over pixels of terms
-l_i = -(r_i^2/v_i + log(2 pi v_i))/2 of both signs; where they nearly cancel
-(a model close to the data) |l| says nothing of the size of the terms, so
-the log L tolerance adds
+Every parity test asserts these (assert_plain_parity) and reports its errors
+in their units (plain_report; appended to $GL_PARITY_LOG when set). The
+named exceptions are rays that land within a few mas of a Sersic centre
+with n > 1.5, where the profile's slope diverges like rho^(1/n - 1): there a
+ray's position, exact to FP32 rounding (about 1e-7 arcsec at 1.5 arcsec),
+moves its large gradient term by ~1e-5 of itself. Each such case names the
+parameters allowed above 1 and by how much, and where log L is affected it
+adds the second bound ll_bound:
   LL_TERM * sum_i |l_i| + EPS_MODEL * sum_i |g_i M_i|,
-FP32 arithmetic and in-warp FP32 sums of the terms (a few ulp of each,
-2e-6 with margin) plus the model error carried through g = dl/dM.
-EPS_MODEL = 1e-5 is the FP32 accuracy of the
-per-pixel model: ray positions carry ~1-2e-7 arcsec of rounding (coordinates
-and deflections of ~2 arcsec at unit roundoff 6e-8), which the steepest
-Sersic profiles of the workloads (log-slope up to ~40/arcsec at R_eff = 0.05)
-turn into relative intensity errors of a few 1e-6; the per-pixel model error
-measured on GB300 stays below 3.5e-6.
+log L being a sum of pixel terms l_i = -(r_i^2/v_i + log(2 pi v_i))/2 of
+both signs (FP32 arithmetic and in-warp FP32 sums of the terms, a few ulp of
+each: 2e-6 with margin) plus a relative model error EPS_MODEL carried
+through g = dl/dM.
 """
+import json
+import os
+
 import numpy as np
 
 import oracle
@@ -51,24 +50,6 @@ def make_system(spec, seed, psf=None):
 def oracle_eval(spec, image, psf, params, grad=True):
     return oracle.loglik(np.asarray(params, np.float32).astype(np.float64), image, np.float32(spec.sigma_bkg),
                          psf, spec.pixel_scale, spec.k, spec.gain_exposure, grad=grad)
-
-
-def conditioned_bound(spec, image, psf, params, sigma=None, gain=None):
-    """eps * C_i per vector and parameter (see the module docstring)."""
-    sigma = np.float32(spec.sigma_bkg) if sigma is None else sigma
-    G = spec.gain_exposure if gain is None else gain
-    inv = 1.0 / G if G > 0 else 0.0
-    D = image.astype(np.float64)
-    s2 = np.asarray(sigma, np.float64) ** 2
-    out = np.empty((len(params), 22))
-    for b, p in enumerate(np.asarray(params, np.float32).astype(np.float64)):
-        M, J = oracle.model_jacobian(p, spec.H, spec.W, psf, spec.pixel_scale, spec.k)
-        v = s2 + M * inv
-        r = D - M
-        g = r / v + (r * r / (v * v) - 1 / v) * inv / 2
-        dg = -1 / v - r * inv / v ** 2 + 0.5 * inv * (-2 * r / v ** 2 - 2 * r * r * inv / v ** 3 + inv / v ** 2)
-        out[b] = EPS_MODEL * np.einsum("hw,hwj->j", np.abs(g) + np.abs(M * dg), np.abs(J))
-    return out
 
 
 def ll_bound(spec, image, psf, params, sigma=None, gain=None):
@@ -106,6 +87,10 @@ def grad_err(g, ref, extra=None):
 
 
 def assert_parity(ll, g, rl, rg, what="", extra=None, ll_extra=None):
+    """The tolerances with the conditioned terms (extra on the gradient,
+    ll_extra on log L) added; the errors against the plain tolerance are
+    reported too (plain_report)."""
+    plain_report(ll, g, rl, rg, what)
     e1 = ll_err(ll, rl, ll_extra)
     assert np.all(e1 <= 1.0), "%s log L: worst %.3g x tol at %d" % (what, e1.max(), int(np.argmax(e1)))
     if g is not None:
@@ -113,3 +98,48 @@ def assert_parity(ll, g, rl, rg, what="", extra=None, ll_extra=None):
         i, j = np.unravel_index(np.argmax(e2), e2.shape)
         assert np.all(e2 <= 1.0), "%s grad: worst %.3g x tol at vector %d param %s (gpu %r ref %r)" % (
             what, e2.max(), i, inputs.PARAM_NAMES[j], g[i, j], rg[i, j])
+
+
+def plain_report(ll, g, rl, rg, what=""):
+    """Errors in units of the plain tolerance (no conditioned term), as a
+    dict: max, p99 and count above 1 for log L and for the gradient, and the
+    worst gradient entry. With GL_PARITY_LOG set, the record is appended to
+    that file (one JSON object per line)."""
+    e1 = ll_err(ll, rl)
+    rec = {"case": what, "vectors": int(len(ll)), "ll_max": float(e1.max()), "ll_p99": float(np.percentile(e1, 99)),
+           "ll_over1": int((e1 > 1).sum())}
+    if g is not None:
+        e2 = grad_err(g, rg)
+        i, j = np.unravel_index(np.argmax(e2), e2.shape)
+        over = np.argwhere(e2 > 1)
+        rec.update(g_max=float(e2.max()), g_p99=float(np.percentile(e2, 99)), g_over1=int((e2 > 1).sum()),
+                   over1=[[int(a), inputs.PARAM_NAMES[b], round(float(e2[a, b]), 3)] for a, b in over],
+                   g_entries=int(e2.size), worst=[int(i), inputs.PARAM_NAMES[j], float(g[i, j]), float(rg[i, j])],
+                   per_param_max={inputs.PARAM_NAMES[k]: round(float(e2[:, k].max()), 4) for k in range(e2.shape[1])})
+    path = os.environ.get("GL_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(rec) + "\n")
+    return rec
+
+
+def assert_plain_parity(ll, g, rl, rg, what="", grad_exceptions=None, ll_extra=None):
+    """The plain tolerances of the module docstring, with no conditioned term
+    on the gradient. grad_exceptions maps a parameter name to the largest
+    multiple of the plain tolerance its entries may reach; every exception is
+    listed, with its measured excess and cause, in the design notes. ll_extra
+    (an explicit second bound on log L) is added where the test names why."""
+    rep = plain_report(ll, g, rl, rg, what)
+    e1 = ll_err(ll, rl, ll_extra)
+    assert np.all(e1 <= 1.0), "%s log L: worst %.3g x tol at %d (%r)" % (what, e1.max(), int(np.argmax(e1)), rep)
+    if g is None:
+        return rep
+    e2 = grad_err(g, rg)
+    limit = np.ones(e2.shape[1])
+    for name, lim in (grad_exceptions or {}).items():
+        limit[inputs.PARAM_NAMES.index(name)] = lim
+    over = e2 > limit[None, :]
+    i, j = np.unravel_index(np.argmax(e2 / limit[None, :]), e2.shape)
+    assert not over.any(), "%s grad: %d entries over the plain tolerance; worst %.3g x at vector %d param %s " \
+        "(gpu %r ref %r)" % (what, int(over.sum()), e2[i, j], i, inputs.PARAM_NAMES[j], g[i, j], rg[i, j])
+    return rep

@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from paper_2202_07663_gb300 import inputs  # noqa: E402
-from gpu_common import assert_parity, conditioned_bound, ll_bound, make_system, oracle_eval  # noqa: E402
+from gpu_common import assert_plain_parity, ll_bound, make_system, oracle_eval  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -49,8 +49,7 @@ def test_plain_60x60_b64(abi):
     params = inputs.draw_perturbed(np.random.default_rng(1), truth, 64).astype(np.float32)
     ll, g = _gpu(abi, spec, image, psf, params)
     rl, _, rg = oracle_eval(spec, image, psf, params)
-    assert_parity(ll, g, rl, rg, "plain 60x60 B=64", extra=conditioned_bound(spec, image, psf, params),
-                  ll_extra=ll_bound(spec, image, psf, params))
+    assert_plain_parity(ll, g, rl, rg, "plain 60x60 B=64")
 
 
 def test_near_truth_gradient(abi):
@@ -63,8 +62,7 @@ def test_near_truth_gradient(abi):
     params[0] = truth.astype(np.float32)
     ll, g = _gpu(abi, spec, image, psf, params)
     rl, _, rg = oracle_eval(spec, image, psf, params)
-    assert_parity(ll, g, rl, rg, "near truth", extra=conditioned_bound(spec, image, psf, params),
-                  ll_extra=ll_bound(spec, image, psf, params))
+    assert_plain_parity(ll, g, rl, rg, "near truth")
 
 
 def test_simulate_matches_oracle(abi):
@@ -79,6 +77,17 @@ def test_simulate_matches_oracle(abi):
     assert np.all(np.abs(m - ref) <= tol), np.max(np.abs(m - ref) / tol)
 
 
+# Cases with a ray within a few mas of a Sersic centre (n > 1.5): the
+# parameters allowed above the plain gradient tolerance (and by how much),
+# and whether log L takes the named second bound ll_bound.
+SHAPE_EXCEPTIONS = {
+    # vector 4: a ray 0.86 mas from the lens-light centre (n_l = 2.8); measured y_l 1.76, log L 1.07
+    (17, 13, 2, 3): ({"y_l": 2.5}, True),
+    # vector 1: a source-plane ray 1.2 mas from the source centre (n_s = 3.6); measured gamma_epl 1.34
+    (45, 64, 3, 21): ({"gamma_epl": 2.0}, False),
+}
+
+
 @pytest.mark.parametrize("H,W,k,K,B", [
     (1, 1, 1, 1, 1), (2, 3, 1, 3, 2), (3, 3, 2, 3, 3), (5, 7, 3, 5, 1), (17, 13, 2, 3, 5),
     (33, 31, 1, 11, 3), (45, 64, 3, 21, 2), (16, 16, 4, 9, 4), (61, 59, 2, 11, 7),
@@ -89,10 +98,9 @@ def test_shapes_and_ragged_tiles(abi, H, W, k, K, B):
     params = inputs.draw_perturbed(np.random.default_rng(H + W), truth, B).astype(np.float32)
     ll, g = _gpu(abi, spec, image, psf, params)
     rl, _, rg = oracle_eval(spec, image, psf, params)
-    # the conditioned FP32 bound covers near-cancelling gradient entries (at
-    # 80x80 the lens-light centre: |dg| 32 against eps * C_i = 436)
-    assert_parity(ll, g, rl, rg, "%dx%d k=%d K=%d" % (H, W, k, K), extra=conditioned_bound(spec, image, psf, params),
-                  ll_extra=ll_bound(spec, image, psf, params))
+    exc, ll_second = SHAPE_EXCEPTIONS.get((H, W, k, K), (None, False))
+    assert_plain_parity(ll, g, rl, rg, "%dx%d k=%d K=%d" % (H, W, k, K), grad_exceptions=exc,
+                        ll_extra=ll_bound(spec, image, psf, params) if ll_second else None)
 
 
 def test_no_poisson_term_and_pixel_noise_map(abi):
@@ -104,8 +112,7 @@ def test_no_poisson_term_and_pixel_noise_map(abi):
     ll, g = s.loglik_grad(torch.from_numpy(params).cuda())
     s.close()
     rl, _, rg = oracle.loglik(params.astype(np.float64), image, sigma, psf, spec.pixel_scale, spec.k, 0.0, grad=True)
-    assert_parity(ll.cpu().numpy(), g.cpu().numpy(), rl, rg, "no Poisson, noise map",
-                  ll_extra=ll_bound(spec, image, psf, params, sigma=sigma, gain=0.0))
+    assert_plain_parity(ll.cpu().numpy(), g.cpu().numpy(), rl, rg, "no Poisson, noise map")
 
 
 def test_zero_ellipticity(abi):
@@ -123,7 +130,7 @@ def test_zero_ellipticity(abi):
         near[:, j] = 1e-9
     _, _, rg = oracle.loglik(near, image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k,
                              spec.gain_exposure, grad=True)
-    assert_parity(ll, g, rl, rg, "e = 0", ll_extra=ll_bound(spec, image, psf, params))
+    assert_plain_parity(ll, g, rl, rg, "e = 0")
 
 
 def test_lens_centre_on_a_ray(abi):
@@ -137,8 +144,7 @@ def test_lens_centre_on_a_ray(abi):
     ll, g = _gpu(abi, spec, image, psf, p)
     rl, _, rg = oracle_eval(spec, image, psf, p)
     # a 9 x 9 cut-out around the lens-light cusp: add the FP32 model error bound
-    assert_parity(ll, g, rl, rg, "centre on a ray", extra=conditioned_bound(spec, image, psf, p),
-                  ll_extra=ll_bound(spec, image, psf, p))
+    assert_plain_parity(ll, g, rl, rg, "centre on a ray")
 
 
 def test_invalid_vectors_give_nan_and_leave_others(abi):
@@ -153,7 +159,7 @@ def test_invalid_vectors_give_nan_and_leave_others(abi):
     assert np.all(np.isnan(ll[1:5])) and np.all(np.isnan(g[1:5]))
     good = [0, 5]
     rl, _, rg = oracle_eval(spec, image, psf, p[good])
-    assert_parity(ll[good], g[good], rl, rg, "valid neighbours", ll_extra=ll_bound(spec, image, psf, p[good]))
+    assert_plain_parity(ll[good], g[good], rl, rg, "valid neighbours")
 
 
 def test_batch_zero_and_argument_errors(abi):
@@ -221,10 +227,42 @@ def test_grouped_launch_equals_single_calls(abi):
         s.close()
 
 
-@pytest.mark.parametrize("workload,nsample", [(inputs.MULTISTART, 24), (inputs.HMC, 3), (inputs.STRESS, 2)])
+def _sample_indices(B, nsample, seed):
+    """First and last vector, the vectors on both sides of the launch
+    boundaries (the per-vector kernels' 8-vector setup blocks and 128-vector
+    final blocks, the ray kernels' waves of 152 SMs x 4 blocks), the rest
+    drawn at random without repeats."""
+    fixed = {0, B - 1}
+    for step in (8192, 2048, 1024, 608, 152, 128, 8):
+        for m in (step, (B // step) * step):   # the first and the last boundary of this kind
+            if 0 < m < B and len(fixed) + 2 <= nsample // 2:
+                fixed.update((m - 1, m))
+    fixed = sorted(fixed)
+    rest = np.setdiff1d(np.arange(B), fixed)
+    extra = np.random.default_rng(seed).choice(rest, max(0, nsample - len(fixed)), replace=False)
+    return np.sort(np.concatenate([np.asarray(fixed, np.int64), extra]))
+
+
+# Entries allowed above the plain gradient tolerance in the full-size samples,
+# by workload and parameter (multiple of the plain tolerance): rays that land
+# within a few mas of a Sersic centre with n > 1.5, where the profile's slope
+# diverges and FP32 ray positions (about 1e-7 arcsec at 1.5 arcsec) move the
+# ray's large gradient term by ~1e-5 of itself.
+FULL_SIZE_EXCEPTIONS = {
+    # measured: gamma_epl 2.54 (vector 0: a source-plane ray 3.2 mas from the
+    # source centre, n_s = 3.9), x_epl 1.78
+    inputs.MULTISTART: {"gamma_epl": 3.0, "x_epl": 2.5},
+}
+
+
+# (workload, vectors checked against the oracle, plain-tolerance exceptions by
+# parameter: entries of rays within a few mas of a Sersic cusp, see FULL_SIZE_EXCEPTIONS)
+@pytest.mark.parametrize("workload,nsample", [(inputs.MULTISTART, 256), (inputs.HMC, 32), (inputs.STRESS, 16)])
 def test_full_size_workloads_sampled(abi, workload, nsample):
-    """Full batch sizes in the launch configuration of the benchmark; the oracle
-    checks a seeded sample of the vectors one by one."""
+    """Full batch sizes in the launch configuration of the benchmark; the
+    oracle checks a sample of the vectors one by one at the plain tolerance
+    (log L 1e-4 max(|l|, 1); gradient 1e-3 (|g_i| + 1e-2 max|g|)), except
+    the named entries of FULL_SIZE_EXCEPTIONS; every vector is finite."""
     c = inputs.WORKLOADS[workload]
     spec, B = c["spec"], c["B"]
     truth, image, psf = make_system(spec, c["seed"])
@@ -235,10 +273,11 @@ def test_full_size_workloads_sampled(abi, workload, nsample):
         params = inputs.draw_perturbed(rng, truth, B).astype(np.float32)
     ll, g = _gpu(abi, spec, image, psf, params)
     assert np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
-    idx = np.sort(rng.choice(B, nsample, replace=False))
-    idx[-1] = B - 1  # include the last vector of the batch
+    idx = _sample_indices(B, nsample, c["seed"])
+    assert len(idx) == nsample and idx[0] == 0 and idx[-1] == B - 1
     rl, _, rg = oracle_eval(spec, image, psf, params[idx])
-    assert_parity(ll[idx], g[idx], rl, rg, "%s sample" % workload, ll_extra=ll_bound(spec, image, psf, params[idx]))
+    assert_plain_parity(ll[idx], g[idx], rl, rg, "%s sample" % workload,
+                        grad_exceptions=FULL_SIZE_EXCEPTIONS.get(workload))
 
 
 def test_final_kernel_variants_agree_bitwise(abi):
@@ -257,7 +296,7 @@ def test_final_kernel_variants_agree_bitwise(abi):
     np.testing.assert_array_equal(grads[0].cpu().numpy(), g1)
     idx = np.array([0, 701, 1399])
     rl, _, rg = oracle_eval(spec, image, psf, params[idx])
-    assert_parity(ll1[idx], g1[idx], rl, rg, "one-tile batch", ll_extra=ll_bound(spec, image, psf, params[idx]))
+    assert_plain_parity(ll1[idx], g1[idx], rl, rg, "one-tile batch")
 
 
 @pytest.mark.parametrize("f", [0.8, 0.85])
@@ -277,8 +316,7 @@ def test_high_ellipticity_long_series(abi, f):
     params[:, 1] = np.linspace(1.6, 2.6, 6)     # gamma across the prior's range
     ll, g = _gpu(abi, spec, image, psf, params)
     rl, _, rg = oracle_eval(spec, image, psf, params)
-    assert_parity(ll, g, rl, rg, "|e| = %.2f" % f, extra=conditioned_bound(spec, image, psf, params),
-                  ll_extra=ll_bound(spec, image, psf, params))
+    assert_plain_parity(ll, g, rl, rg, "|e| = %.2f" % f)
 
 
 def test_many_tile_paths_agree(abi):
@@ -319,8 +357,7 @@ def test_many_tile_paths_agree(abi):
     s2.close()
     idx = np.array([0, 8])
     rl, _, rg = oracle_eval(spec, image, psf, params[idx])
-    assert_parity(ref[0][idx], ref[1][idx], rl, rg, "many tiles per vector",
-                  ll_extra=ll_bound(spec, image, psf, params[idx]))
+    assert_plain_parity(ref[0][idx], ref[1][idx], rl, rg, "many tiles per vector")
 
 
 @pytest.mark.parametrize("H,W,k,K,B", [(80, 80, 2, 11, 1), (61, 59, 2, 11, 7), (100, 90, 1, 21, 4), (64, 40, 2, 21, 30)])
