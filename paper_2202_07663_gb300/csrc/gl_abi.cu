@@ -172,10 +172,12 @@ Seg make_seg(const gl_system* s, const float* params, int B) {
   g.W = s->W;
   g.K = s->K;
   g.k = s->k;
-  const double sub = s->pixel_scale / s->k;
-  g.sub = float(sub);
-  g.x0 = float(-0.5 * (double(s->k) * s->W - 1.0) * sub);
-  g.y0 = float(-0.5 * (double(s->k) * s->H - 1.0) * sub);
+  // subpixel centres at (j - (kW - 1)/2) pixel_scale/k = (2j + 1 - kW) h, h = pixel_scale/(2k)
+  const double h = s->pixel_scale / (2.0 * s->k);
+  g.hh = float(h);
+  g.hl = float(h - double(g.hh));
+  g.nx0 = 1 - s->k * s->W;
+  g.ny0 = 1 - s->k * s->H;
   g.inv_gain = s->gain_exposure > 0.0 ? float(1.0 / s->gain_exposure) : 0.f;
   g.params = params;
   g.B = B;
@@ -187,11 +189,24 @@ Seg make_seg(const gl_system* s, const float* params, int B) {
   return g;
 }
 
+// A system's data and scratch live on the device that was current when it was
+// created; a call made with another device current would launch there on
+// pointers of the first one. Refused, not switched: the caller owns the
+// current device and the stream, which belongs to one device.
+int check_device(const gl_system* s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != s->device)
+    return fail(GL_ERR_INVALID_ARG, "the system lives on device %d but device %d is current", s->device, dev);
+  return GL_OK;
+}
+
 int check_call(const gl_system* s, const float* params, int B) {
   if (!s) return fail(GL_ERR_INVALID_ARG, "null gl_system");
   if (B < 0 || B > (1 << 24)) return fail(GL_ERR_INVALID_ARG, "B = %d outside [0, 2^24]", B);
   if (B > 0 && !params) return fail(GL_ERR_INVALID_ARG, "null params");
-  return GL_OK;
+  return check_device(s);
 }
 
 int run_one(gl_system* s, const float* params, int B, double* ll, double* c2, double* grad, float* sim, int mode,
@@ -215,6 +230,13 @@ int run_one(gl_system* s, const float* params, int B, double* ll, double* c2, do
 
 // Internal helpers for other translation units of the library (not ABI).
 namespace gl_internal {
+
+int system_device_check(const gl_system* s) { return check_device(s); }
+
+size_t scratch_held(const gl_system* s) {
+  return sizeof(VecConst) * size_t(s->cap_B) + sizeof(float) * size_t(s->cap_B) * s->H * s->W +
+         sizeof(double) * size_t(s->cap_partial);
+}
 
 // Segment of a call on sys with every scratch pointer left null.
 gl::Seg seg_without_scratch(const gl_system* s, const float* params, int B) {
@@ -341,6 +363,10 @@ int gl_system_create_obsvar(gl_system** out, const float* image, const float* no
 
 int gl_system_destroy(gl_system* s) {
   if (!s) return GL_OK;
+  // free on the system's own device, then give the caller's current device back
+  int cur = s->device;
+  cudaGetDevice(&cur);
+  if (cur != s->device) cudaSetDevice(s->device);
   cudaDeviceSynchronize();
   cudaFree(s->d_image);
   cudaFree(s->d_sigma2);
@@ -355,7 +381,9 @@ int gl_system_destroy(gl_system* s) {
   cudaFree(s->d_pimg);
   cudaFree(s->d_pfull);
   cudaFree(s->d_pamps);
+  const int dev = s->device;
   delete s;
+  if (cur != dev) cudaSetDevice(cur);
   return GL_OK;
 }
 
@@ -367,6 +395,8 @@ size_t gl_system_scratch_bytes(const gl_system* s, int B) {
   return sizeof(VecConst) * size_t(B) + sizeof(float) * size_t(B) * s->H * s->W + sizeof(double) * size_t(partial);
 }
 
+size_t gl_system_scratch_held(const gl_system* s) { return s ? gl_internal::scratch_held(s) : 0; }
+
 size_t gl_system_resident_bytes(const gl_system* s) {
   if (!s) return 0;
   return sizeof(float) * (2 * size_t(s->H) * s->W + size_t(s->K) * s->K);
@@ -375,6 +405,8 @@ size_t gl_system_resident_bytes(const gl_system* s) {
 int gl_system_reserve(gl_system* s, int B) {
   if (!s) return fail(GL_ERR_INVALID_ARG, "null gl_system");
   if (B < 0 || B > (1 << 24)) return fail(GL_ERR_INVALID_ARG, "B = %d", B);
+  int rc = check_device(s);
+  if (rc != GL_OK) return rc;
   // partial need is largest at small B (more tiles per vector); take the max over B' <= B
   long long need = 0;
   for (int b : {1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, B}) {

@@ -49,6 +49,11 @@ struct gl_batcher {
   size_t conv_smem[gl::N_CONV_CLASSES] = {0, 0, 0};
   int max_H = 0, max_W = 0, max_K = 0;
   cudaStream_t capture_stream = nullptr;
+  // the last run's graph and its stream: a run on another stream waits for
+  // it before it overwrites the device table and the arena that graph reads
+  cudaEvent_t done = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool ran = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   size_t table_bytes() const { return align256(sizeof(gl::TableHdr)) + sizeof(gl::Seg) * size_t(max_segments); }
@@ -62,6 +67,7 @@ int gl_batcher_destroy(gl_batcher* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  if (b->done) cudaEventDestroy(b->done);
   for (int i = 0; i < 2; ++i) {
     if (b->staged[i]) cudaEventDestroy(b->staged[i]);
     if (b->h_stage[i]) cudaFreeHost(b->h_stage[i]);
@@ -110,6 +116,7 @@ int gl_batcher_create(gl_batcher** out, int max_segments, size_t arena_bytes, in
       (e = cudaMallocHost(&b->h_stage[0], tb)) != cudaSuccess || (e = cudaMallocHost(&b->h_stage[1], tb)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&b->staged[0], cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&b->staged[1], cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) {
     gl_batcher_destroy(b);
     return gl_internal::cuda_error(e, "gl_batcher_create allocation");
@@ -153,11 +160,17 @@ int gl_batcher_run(gl_batcher* b, gl_system* const* systems, const float* const*
   if (n < 0 || n > b->max_segments) return gl_internal::set_error(GL_ERR_INVALID_ARG, "n outside [0, max_segments]");
   if (n > 0 && (!systems || !params || !B || !loglik_out || !grad_out))
     return gl_internal::set_error(GL_ERR_INVALID_ARG, "null array");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return gl_internal::cuda_error(e, "cudaGetDevice");
+  if (dev != b->device) return gl_internal::set_error(GL_ERR_INVALID_ARG, "the batcher lives on another device");
   std::vector<gl::Seg> by_class[gl::N_CONV_CLASSES];
   size_t used = 0;
   for (int i = 0; i < n; ++i) {
     if (!systems[i] || B[i] < 0 || B[i] > (1 << 24)) return gl_internal::set_error(GL_ERR_INVALID_ARG, "bad segment");
     if (B[i] == 0) continue;
+    const int rc = gl_internal::system_device_check(systems[i]);
+    if (rc != GL_OK) return rc;
     if (!params[i] || !loglik_out[i] || !grad_out[i])
       return gl_internal::set_error(GL_ERR_INVALID_ARG, "null params/loglik/grad of a segment");
     gl::Seg g = gl_internal::seg_without_scratch(systems[i], params[i], B[i]);
@@ -188,7 +201,7 @@ int gl_batcher_run(gl_batcher* b, gl_system* const* systems, const float* const*
   // stage the table (wait until the previous copy out of this staging buffer has run)
   const int s = b->slot;
   b->slot ^= 1;
-  cudaError_t e = cudaEventSynchronize(b->staged[s]);
+  e = cudaEventSynchronize(b->staged[s]);
   if (e != cudaSuccess) return gl_internal::cuda_error(e, "staging event");
   gl::TableHdr* hdr = reinterpret_cast<gl::TableHdr*>(b->h_stage[s]);
   gl::Seg* segs = reinterpret_cast<gl::Seg*>(b->h_stage[s] + align256(sizeof(gl::TableHdr)));
@@ -214,10 +227,15 @@ int gl_batcher_run(gl_batcher* b, gl_system* const* systems, const float* const*
   hdr->ray_total = rt;
   if (k == 0) return GL_OK;
   const size_t bytes = align256(sizeof(gl::TableHdr)) + sizeof(gl::Seg) * size_t(k);
+  if (b->ran && st != b->last_stream && (e = cudaStreamWaitEvent(st, b->done, 0)) != cudaSuccess)
+    return gl_internal::cuda_error(e, "wait for the previous run");
   if ((e = cudaMemcpyAsync(b->d_table, b->h_stage[s], bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return gl_internal::cuda_error(e, "table upload");
   if ((e = cudaEventRecord(b->staged[s], st)) != cudaSuccess) return gl_internal::cuda_error(e, "staging event");
   if ((e = cudaGraphLaunch(b->exec, st)) != cudaSuccess) return gl_internal::cuda_error(e, "graph launch");
+  if ((e = cudaEventRecord(b->done, st)) != cudaSuccess) return gl_internal::cuda_error(e, "run event");
+  b->last_stream = st;
+  b->ran = true;
   gl_internal::count_launches(gl::DEVTABLE_LAUNCHES);
   return GL_OK;
 }

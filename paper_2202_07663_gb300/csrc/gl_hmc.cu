@@ -16,11 +16,12 @@ namespace {
 
 // p += kick * eps * grad;  q += eps * M^-1 p;  q32 = float(q). One thread per component.
 // eps from *eps_dev when given (a value a replayed graph reads at run time).
-__global__ void k_hmc_leapfrog(int n, int d, double* __restrict__ q, double* __restrict__ p,
+__global__ void k_hmc_leapfrog(long long n, int d, double* __restrict__ q, double* __restrict__ p,
                                const double* __restrict__ grad, const double* __restrict__ inv_mass, double eps_arg,
                                const double* __restrict__ eps_dev, double kick, float* __restrict__ q32) {
   const double eps = eps_dev ? *eps_dev : eps_arg;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  // 64-bit index: B * d may exceed the int range
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double pi = p[i] + kick * eps * grad[i];
     const double qi = q[i] + eps * inv_mass[i % d] * pi;
     p[i] = pi;
@@ -208,7 +209,7 @@ int gl_hmc_leapfrog(int B, int d, double* q, double* p, const double* grad, cons
   gl::Hooks* h = gl_internal::hooks();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->before(GL_K_OTHER, st);
-  k_hmc_leapfrog<<<grid_for(n, 256), 256, 0, st>>>(int(n), d, q, p, grad, inv_mass, eps, nullptr, kick, q32_out);
+  k_hmc_leapfrog<<<grid_for(n, 256), 256, 0, st>>>(n, d, q, p, grad, inv_mass, eps, nullptr, kick, q32_out);
   cudaError_t e = h->after(GL_K_OTHER, st);
   return e == cudaSuccess ? GL_OK : gl_internal::cuda_error(e, "k_hmc_leapfrog");
 }
@@ -223,7 +224,7 @@ int gl_hmc_leapfrog_dev(int B, int d, double* q, double* p, const double* grad, 
   gl::Hooks* h = gl_internal::hooks();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   h->before(GL_K_OTHER, st);
-  k_hmc_leapfrog<<<grid_for(n, 256), 256, 0, st>>>(int(n), d, q, p, grad, inv_mass, 0.0, eps_dev, kick, q32_out);
+  k_hmc_leapfrog<<<grid_for(n, 256), 256, 0, st>>>(n, d, q, p, grad, inv_mass, 0.0, eps_dev, kick, q32_out);
   cudaError_t e = h->after(GL_K_OTHER, st);
   return e == cudaSuccess ? GL_OK : gl_internal::cuda_error(e, "k_hmc_leapfrog");
 }

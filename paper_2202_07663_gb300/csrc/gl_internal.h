@@ -10,6 +10,12 @@ struct gl_system;
 
 namespace gl_internal {
 
+// GL_OK if sys lives on the current device, else GL_ERR_INVALID_ARG (message set).
+int system_device_check(const gl_system* s);
+
+// Device bytes of likelihood scratch the system holds now (grown on demand).
+size_t scratch_held(const gl_system* s);
+
 // Segment of a call on sys (system data, tile plan) with null scratch pointers.
 gl::Seg seg_without_scratch(const gl_system* s, const float* params, int B);
 

@@ -12,7 +12,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
-#include <mutex>
 
 #include "gl_device.cuh"
 #include "gl_internal.h"
@@ -26,26 +25,17 @@ constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;   // 32 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
-
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
-// Device address of the array on the current device, resolved once per device.
+// Device address of the array on the current device. The host-side name of
+// the array is not a device address, so it is looked up with the device
+// current, on every call: the lookup allocates nothing, and no address is
+// kept that a reset of the device's context could leave stale.
 int scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return gl_internal::cuda_error(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return gl_internal::set_error(GL_ERR_UNSUPPORTED, "device ordinal out of range");
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return gl_internal::cuda_error(e, "cudaGetSymbolAddress(static scratch)");
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return gl_internal::cuda_error(e, "cudaGetSymbolAddress(static scratch)");
+  *out = p;
   return GL_OK;
 }
 
@@ -57,6 +47,8 @@ int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* l
                            double* grad_out, void* stream) {
   if (!sys) return gl_internal::set_error(GL_ERR_INVALID_ARG, "null gl_system");
   if (B < 0 || B > (1 << 24)) return gl_internal::set_error(GL_ERR_INVALID_ARG, "B outside [0, 2^24]");
+  int rc = gl_internal::system_device_check(sys);
+  if (rc != GL_OK) return rc;
   if (B == 0) return GL_OK;
   if (!params || !loglik_out || !grad_out)
     return gl_internal::set_error(GL_ERR_INVALID_ARG, "null params, loglik_out or grad_out");
@@ -72,7 +64,7 @@ int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* l
     return gl_internal::set_error(GL_ERR_INVALID_ARG, msg);
   }
   void* base = nullptr;
-  int rc = scratch_address(&base);
+  rc = scratch_address(&base);
   if (rc != GL_OK) return rc;
   unsigned char* p = static_cast<unsigned char*>(base);
   // Every element of these buffers is written before it is read within one

@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from paper_2202_07663_gb300 import inputs  # noqa: E402
-from gpu_common import assert_parity, make_system  # noqa: E402
+from gpu_common import assert_plain_parity, make_system  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -51,12 +51,17 @@ def test_noalloc_matches_allocating_entry_point_twice(abi):
     truth, image, psf = make_system(spec, 4242)
     sysm = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
     rng = np.random.default_rng(77)
+    assert sysm.scratch_held() == 0
     for call in range(2):   # two calls in a row: the second reuses the array the first left behind
         B = 64 if call == 0 else 37
         params = torch.from_numpy(inputs.draw_perturbed(rng, truth, B).astype(np.float32)).cuda()
         ll, c2, g = _noalloc(lib, sysm, params)
+        if call == 0:
+            # the system's own scratch is still unallocated: the call used the static array only
+            assert sysm.scratch_held() == 0
         rl, rg, rc2 = [t.cpu().numpy() for t in sysm.loglik_grad(params, chi2=True)]
-        assert_parity(ll, g, rl, rg, "no-alloc call %d" % call)
+        assert sysm.scratch_held() > 0
+        assert_plain_parity(ll, g, rl, rg, "no-alloc call %d" % call)
         np.testing.assert_allclose(c2, rc2, rtol=1e-4)
     sysm.close()
 
