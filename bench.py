@@ -83,10 +83,10 @@ def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
 
 
 MUFU_RAY_ADJ = 12   # ex2/lg2/rcp per ray in the adjoint (EPL power, two Sersic profiles)
-# DRAM bytes per launch of k_ray_adj from one ncu capture, valid only for the
-# kernel source it was taken on (sha256 prefix of gl_kernels.cu + gl_device.cuh);
-# any other source reports null traffic until it is captured again.
-TRAFFIC = {"484cf7d85eb9f23b": 64.712192e6}   # ncu dram read + write, one launch at B = 4096
+# DRAM bytes per launch of k_ray_adj from one ncu capture, keyed by workload
+# and the kernel source it was taken on (sha256 prefix of gl_kernels.cu +
+# gl_device.cuh); any other source reports null traffic until it is captured again.
+TRAFFIC = {}
 
 
 def kernel_source_hash() -> str:
@@ -156,9 +156,9 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def rank_param_seed(rank: int) -> int:
+def rank_param_seed(workload: str, rank: int) -> int:
     """Seed of rank r's parameter batch: every rank evaluates its own B vectors."""
-    return inputs.WORKLOADS[WORKLOAD]["seed"] + 17 + rank
+    return inputs.WORKLOADS[workload]["seed"] + 17 + rank
 
 
 def max_over_ranks(value: float, device, world: int) -> float:
@@ -176,99 +176,285 @@ def whole_job_rate(world: int, per_rank_units: int, seconds: float) -> float:
     return world * per_rank_units / seconds
 
 
-def make_workload(device, rank: int):
-    """Synthetic lens system (observed image from the GPU model + seeded noise) and B vectors."""
-    import torch
-    from paper_2202_07663_gb300 import abi
-    c = inputs.WORKLOADS[WORKLOAD]
-    spec, B = c["spec"], c["B"]
-    rng = inputs.rng_for(WORKLOAD, 0)
-    truth = inputs.draw_truth(rng)
-    psf = inputs.make_psf(spec).astype(np.float32)
-    blank = np.zeros((spec.H, spec.W), np.float32)
-    s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
-    model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
-    s0.close()
-    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
-    params = inputs.draw_box(np.random.default_rng(rank_param_seed(rank)), B).astype(np.float32)
-    return spec, B, truth, psf, image, params
+BENCH_INPUTS = os.path.join(ROOT, "tests", "golden", "bench_inputs")
 
 
-def synthetic_system(workload: str, device):
-    """(spec, truth, psf, image) of a workload: GPU model of a seeded truth + seeded noise."""
-    import torch
-    from paper_2202_07663_gb300 import abi
+def load_observed(workload: str):
+    """(spec, truth, psf, image) of a benchmark workload. The observed image
+    was written by the FP64 oracle (model of the seeded truth + seeded noise,
+    tests/golden/bench_inputs/make_bench_images.py), so both arms of the
+    benchmark and its error report use the same data, none of it from the
+    CUDA path."""
     spec = inputs.WORKLOADS[workload]["spec"]
-    rng = inputs.rng_for(workload, 0)
-    truth = inputs.draw_truth(rng)
+    image = np.load(os.path.join(BENCH_INPUTS, workload + ".image.npy"))
+    truth = np.load(os.path.join(BENCH_INPUTS, workload + ".truth.npy"))
+    if not np.array_equal(inputs.draw_truth(inputs.rng_for(workload, 0)), truth):
+        raise RuntimeError("stored benchmark input of %s does not match its seed" % workload)
     psf = inputs.make_psf(spec).astype(np.float32)
-    blank = np.zeros((spec.H, spec.W), np.float32)
-    s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
-    model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
-    s0.close()
-    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
-    return spec, truth, psf, image
+    return spec, truth, psf, image.astype(np.float32)
+
+
+def workload_params(workload: str, rank: int, truth: np.ndarray) -> np.ndarray:
+    c = inputs.WORKLOADS[workload]
+    rng = np.random.default_rng(rank_param_seed(workload, rank))
+    if c["draw"] == "box":
+        return inputs.draw_box(rng, c["B"]).astype(np.float32)
+    return inputs.draw_perturbed(rng, truth, c["B"]).astype(np.float32)
+
+
+def workload_config(workload: str) -> dict:
+    """The config object of a workload, the same in both arms of the benchmark."""
+    c = inputs.WORKLOADS[workload]
+    spec = c["spec"]
+    return {"workload": workload, "H": spec.H, "W": spec.W, "supersample": spec.k, "psf": spec.K,
+            "psf_kind": spec.psf, "pixel_scale": spec.pixel_scale, "sigma_bkg": spec.sigma_bkg,
+            "gain_exposure": spec.gain_exposure, "B_per_gpu": c["B"],
+            "params": "uniform over the prior box" if c["draw"] == "box" else "truth + N(0, 0.02 box width)",
+            "image": "oracle model of the seeded truth + seeded noise (stored input)",
+            "l2": "GPU arm: flushed by a 256 MB write between timed steps, outside the step events"}
+
+
+TOL_UNITS = ("multiples of the tolerance: log L |dl| / (1e-4 max(|l|, 1)); gradient "
+             "|dg_i| / (1e-3 (|g_i| + 1e-2 max_j |g_j|)), per component")
+
+
+def error_stats(ll, g, rl, rg) -> dict:
+    """Error of the GPU results against the FP64 oracle, per vector (log L)
+    and per component (gradient), in multiples of the stated tolerance."""
+    el = np.abs(ll - rl) / (1e-4 * np.maximum(np.abs(rl), 1.0))
+    eg = np.abs(g - rg) / (1e-3 * (np.abs(rg) + 1e-2 * np.max(np.abs(rg), axis=1, keepdims=True)))
+    per = eg.max(axis=0)
+    j = int(np.argmax(per))
+    return {"vectors": int(len(ll)), "unit": TOL_UNITS,
+            "loglik": {"max": float(el.max()), "p99": float(np.percentile(el, 99)),
+                       "frac_over_1": float(np.mean(el > 1))},
+            "grad": {"max": float(eg.max()), "p99": float(np.percentile(eg, 99)),
+                     "frac_over_1": float(np.mean(eg > 1)), "worst_param": inputs.PARAM_NAMES[j]}}
+
+
+def oracle_sample(spec, psf, image, params, budget_s: float, min_n: int = 8):
+    """The FP64 oracle (log L + gradient) on all host cores over a bounded,
+    evenly spread sample of a workload's vectors (first and last included):
+    (timing dict, sample indices, oracle log L, oracle gradient)."""
+    import oracle
+    oracle.build()
+    nt = oracle.max_threads()
+    args = (image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k, spec.gain_exposure)
+    B = len(params)
+
+    def pick(n):
+        return np.unique(np.linspace(0, B - 1, min(n, B)).round().astype(np.int64))
+
+    idx = pick(max(nt, min_n))
+    t = time.perf_counter()
+    oracle.loglik(params[idx].astype(np.float64), *args, grad=True, nthreads=nt)
+    dt = time.perf_counter() - t
+    if dt < budget_s / 3:
+        idx = pick(int(max(len(idx), math.floor(len(idx) * budget_s / max(dt, 1e-3)))))
+        t = time.perf_counter()
+    rl, _, rg = oracle.loglik(params[idx].astype(np.float64), *args, grad=True, nthreads=nt)
+    dt = time.perf_counter() - t
+    timing = {"value": len(idx) / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
+              "sample": "%d of the %d vectors, evenly spread, first and last included (log L + forward-mode "
+                        "gradient, FP64), %.1f s" % (len(idx), B, dt)}
+    return timing, idx, rl, rg
+
+
+def cpu_baseline(spec, psf, image, params, ll_gpu, g_gpu, budget_s: float = 12.0):
+    """The CPU-baseline leg: the FP64 oracle timed on a bounded sample of the
+    workload (all host cores, and one core on a smaller sample), and the error
+    of the GPU results on that sample against it."""
+    import oracle
+    timing, idx, rl, rg = oracle_sample(spec, psf, image, params, budget_s)
+    args = (image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k, spec.gain_exposure)
+    n1 = max(2, min(len(idx), int(len(idx) * 3.0 / budget_s / max(timing["cores"], 1)) + 1))
+    t = time.perf_counter()
+    oracle.loglik(params[idx[:n1]].astype(np.float64), *args, grad=True, nthreads=1)
+    dt1 = time.perf_counter() - t
+    timing.update(value_1core=n1 / dt1, sample_1core="%d vectors, %.1f s" % (n1, dt1))
+    err = error_stats(ll_gpu[idx], g_gpu[idx], rl, rg)
+    err["sample"] = "the CPU-baseline sample (%d vectors)" % len(idx)
+    return timing, err
+
+
+def measured_peaks():
+    """FP32 FMA and ex2 rates of this GPU from the library's probe kernels."""
+    from paper_2202_07663_gb300 import abi
+    return {"fp32_tflops": abi.gl_profile_peak(abi.GL_PEAK_FP32_FMA) / 1e12,
+            "mufu_ex2_gops": abi.gl_profile_peak(abi.GL_PEAK_MUFU_EX2) / 1e9}
+
+
+def measure(workload: str, device, rank: int, world: int, steps: int, warmup: int, cpu: bool, peaks: dict,
+            cpu_budget_s: float = 12.0) -> dict:
+    """One benchmark line for a workload: device-timed steps (inputs resident,
+    L2 flushed between steps, clocks sampled), the end-to-end rate through the
+    host-buffer entry point, the roofline of the dominant kernel against the
+    measured FP32 peak, kernel shares, and (rank 0, one GPU) the oracle
+    baseline with the per-result error."""
+    import torch
+    import torch.distributed as dist
+    from paper_2202_07663_gb300 import abi
+    spec, truth, psf, image = load_observed(workload)
+    B = inputs.WORKLOADS[workload]["B"]
+    params = workload_params(workload, rank, truth)
+    sysm = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    sysm.reserve(B)
+    p_dev = torch.from_numpy(params).to(device)
+    ll = torch.empty(B, dtype=torch.float64, device=device)
+    g = torch.empty(B, 22, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)   # > L2 (129 MB)
+
+    def step():
+        sysm.loglik_grad(p_dev, out=(ll, g, None))
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident in HBM; L2 flushed between steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    abi.gl_profile_reset()
+    abi.gl_profile_enable(True)
+    n0 = abi.gl_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    with Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
+        t0 = time.perf_counter()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    launches = abi.gl_launch_count() - n0
+    prof = abi.gl_profile_read()
+    abi.gl_profile_enable(False)
+    del flush
+    step_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, device, world)
+    value = whole_job_rate(world, B, step_ms * 1e-3)
+    ll_host, g_host = ll.cpu().numpy(), g.cpu().numpy()
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    hp = torch.from_numpy(params).pin_memory()
+    hl = torch.empty(B, dtype=torch.float64).pin_memory()
+    hg = torch.empty(B, 22, dtype=torch.float64).pin_memory()
+    hp_np, hl_np, hg_np = hp.numpy(), hl.numpy(), hg.numpy()
+    for _ in range(3):
+        sysm.loglik_grad_host(hp_np, hl_np, hg_np)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sysm.loglik_grad_host(hp_np, hl_np, hg_np)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / steps, device, world)
+    e2e_value = whole_job_rate(world, B, e2e_s)
+    sysm.close()
+
+    # ---- roofline of the dominant kernel (and the rates of the others), from the live event timings
+    rays = spec.H * spec.W * spec.k * spec.k
+    N_adj = series_terms(params, adjoint=True)
+    N_fwd = series_terms(params, adjoint=False)
+    work = {"k_ray_adj": float(rays * flops_ray_adj(N_adj).sum()),
+            "k_ray_fwd": float(rays * flops_ray_fwd(N_fwd).sum()),
+            "k_conv": float(B * spec.H * spec.W * flops_conv_pixel(spec.K, True))}
+    n_adj, ms_adj = prof["k_ray_adj"]
+    adj_s = (ms_adj / max(n_adj, 1)) * 1e-3
+    fp32_peak = peaks["fp32_tflops"]
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    nominal = read_peaks()[0]
+    fp32_nominal = sms * 128 * 2 * float(nominal.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = work["k_ray_adj"] / adj_s / 1e12
+    mufu_peak = peaks["mufu_ex2_gops"]
+    mufu_achieved = rays * B * MUFU_RAY_ADJ / adj_s / 1e9
+    th = kernel_source_hash()
+    traffic = TRAFFIC.get((workload, th))
+    tot = sum(v[1] for v in prof.values())
+    kern = {}
+    for k, (n, ms) in prof.items():
+        if n == 0:
+            continue
+        kern[k] = {"launches": n, "ms_total": round(ms, 4), "share": round(ms / tot, 4) if tot > 0 else None}
+        if k in work:
+            kern[k]["tflops"] = work[k] / (ms / n * 1e-3) / 1e12
+            kern[k]["frac_fp32_peak"] = kern[k]["tflops"] / fp32_peak
+    clocks = clk.summary()
+    cpu_base, err = None, None
+    if cpu and rank == 0 and world == 1:
+        cpu_base, err = cpu_baseline(spec, psf, image, params, ll_host, g_host, budget_s=cpu_budget_s)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f64 per-vector sums)", "data": "synthetic",
+        "config": dict(workload_config(workload),
+                       parallelism="replicas (B per GPU)" if world > 1 else "single GPU"),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 22 * 4,
+                "d2h_bytes_per_step": B * 8 + B * 22 * 8},
+        "roofline": {"bound": "alu", "kernel": "k_ray_adj", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                     "flops_per_launch": work["k_ray_adj"], "launch_ms": adj_s * 1e3,
+                     "peak_basis": "measured: packed-FMA probe kernel of this library (gl_profile_peak) on this "
+                                   "GPU before the timed steps, best of five launches",
+                     "peak_nominal": fp32_nominal, "frac_of_nominal": achieved / fp32_nominal,
+                     "nominal_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % (
+                         sms, float(nominal.get("sm_max_mhz", 2070.0))),
+                     "mufu": {"achieved": mufu_achieved, "peak": mufu_peak, "unit": "Gop/s",
+                              "frac": mufu_achieved / mufu_peak, "ops_per_ray": MUFU_RAY_ADJ,
+                              "peak_basis": "measured: ex2 probe kernel (gl_profile_peak)"},
+                     "mean_series_terms": float(N_adj.mean()), "kernel_source": th},
+        "kernels": kern,
+        "cpu_baseline": cpu_base,
+        "error": err,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "wall_s_timed": wall,
+    }
 
 
 def run_hmc_workload(device, iterations: int = 200, chains: int = 512, leapfrog: int = 8, cpu: bool = False):
-    """HMC through the adjoint, 100x100 pixels, k = 4, 21x21 Moffat PSF."""
+    """HMC through the adjoint (100x100 pixels, k = 4, 21x21 Moffat PSF): 512
+    chains x 8 leapfrog steps x 200 iterations, the log density and its
+    gradient through the torch.autograd.Function (LogLik + autograd.grad);
+    the same run through the library's direct call beside it, so that the
+    Function's overhead is measured. With cpu, the error of the gradient
+    evaluations against the FP64 oracle on a sample of the chains' start
+    points."""
     import torch
     from paper_2202_07663_gb300 import abi, hmc
-    spec, truth, psf, image = synthetic_system(inputs.HMC, device)
+    spec, truth, psf, image = load_observed(inputs.HMC)
     s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
     s.reserve(chains)
     q0 = torch.from_numpy(inputs.draw_perturbed(np.random.default_rng(3017), truth, chains, frac=0.002)).to(device)
     inv_mass = hmc.laplace_inv_mass(s, torch.from_numpy(truth).to(device))
-    sampler = hmc.HMC(q0, inv_mass, 0.05, leapfrog, system=s, seed=3)
-    eps = sampler.tune_step_size(rounds=5, iters=2)
-    st = sampler.run(iterations)
-    s.close()
-    out = {"workload": "hmc-100x100-k4-moffat21", "chains": chains, "leapfrog": leapfrog,
-           "iterations": iterations, "grad_evals": st.grad_evals, "seconds": st.seconds,
-           "evals_per_s": st.evals_per_s, "acceptance": st.acceptance, "step_size": eps,
+    out = {"workload": "hmc-100x100-k4-moffat21", "chains": chains, "leapfrog": leapfrog, "iterations": iterations,
            "mass": "diagonal, 1/|d2 logL/dq2| at the truth (Laplace)",
            "log_density": "log L (flat prior), physical parameters"}
+    eps = None
+    for name, target in (("autograd", hmc.AutogradTarget(s)), ("direct", hmc.LensTarget(s))):
+        sampler = hmc.HMC(q0, inv_mass, 0.05, leapfrog, target=target, seed=3)
+        if eps is None:
+            eps = sampler.tune_step_size(rounds=5, iters=2)
+        else:
+            sampler.eps = eps
+        st = sampler.run(iterations)
+        out[name] = {"grad_evals": st.grad_evals, "seconds": st.seconds, "evals_per_s": st.evals_per_s,
+                     "acceptance": st.acceptance}
+    out.update(step_size=eps, grad_evals=out["autograd"]["grad_evals"], seconds=out["autograd"]["seconds"],
+               evals_per_s=out["autograd"]["evals_per_s"], acceptance=out["autograd"]["acceptance"],
+               autograd_over_direct_time=out["autograd"]["seconds"] / out["direct"]["seconds"])
     if cpu:
-        out["cpu_oracle"] = oracle_sample(spec, psf, image, q0.cpu().numpy().astype(np.float32))
-    return out
-
-
-def run_stress_workload(device, steps: int = 3, cpu: bool = False):
-    """The stress workload: 200x200 pixels, k = 4, 21x21 PSF, B = 16384 vectors per call."""
-    import torch
-    from paper_2202_07663_gb300 import abi
-    spec, truth, psf, image = synthetic_system(inputs.STRESS, device)
-    B = inputs.WORKLOADS[inputs.STRESS]["B"]
-    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
-    s.reserve(B)
-    params = inputs.draw_box(np.random.default_rng(5017), B).astype(np.float32)
-    p = torch.from_numpy(params).to(device)
-    ll = torch.empty(B, dtype=torch.float64, device=device)
-    g = torch.empty(B, 22, dtype=torch.float64, device=device)
-    s.loglik_grad(p, out=(ll, g, None))
-    torch.cuda.synchronize()
-    abi.gl_profile_reset()
-    abi.gl_profile_enable(True)
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(steps):
-        s.loglik_grad(p, out=(ll, g, None))
-    e.record()
-    torch.cuda.synchronize()
-    prof = abi.gl_profile_read()
-    abi.gl_profile_enable(False)
-    ms = a.elapsed_time(e) / steps
-    n_adj, ms_adj = prof["k_ray_adj"]
-    N = series_terms(params, adjoint=True)
-    rays = spec.H * spec.W * spec.k * spec.k
-    adj_tflops = rays * float(flops_ray_adj(N).sum()) / (ms_adj / n_adj * 1e-3) / 1e12
+        q = q0.to(torch.float32).contiguous()
+        ll, g = s.loglik_grad(q)
+        timing, idx, rl, rg = oracle_sample(spec, psf, image, q.cpu().numpy(), budget_s=4.0, min_n=16)
+        out["cpu_oracle"] = timing
+        out["error"] = dict(error_stats(ll.cpu().numpy()[idx], g.cpu().numpy()[idx], rl, rg),
+                            sample="%d of the chains' start points" % len(idx))
     s.close()
-    out = {"workload": "stress-200x200-k4-psf21-B16384", "B": B, "steps": steps, "ms_per_step": ms,
-           "evals_per_s": B / (ms * 1e-3), "k_ray_adj_tflops": adj_tflops,
-           "kernel_ms_per_step": {k: v[1] / steps for k, v in prof.items() if v[0] > 0},
-           "finite": bool(torch.isfinite(ll).all().item() and torch.isfinite(g).all().item())}
-    if cpu:
-        out["cpu_oracle"] = oracle_sample(spec, psf, image, params)
     return out
 
 
@@ -468,68 +654,22 @@ def run_pipeline_workload(device):
     return out
 
 
-def cpu_baseline(spec, psf, image, params, budget_s: float = 12.0):
-    """The FP64 oracle (log L + gradient) on a bounded sample of the same workload."""
-    import oracle
-    oracle.build()
-    nt = oracle.max_threads()
-    args = (image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k, spec.gain_exposure)
-    n0 = min(len(params), max(nt, 8))
-    t = time.perf_counter()
-    oracle.loglik(params[:n0].astype(np.float64), *args, grad=True, nthreads=nt)
-    dt = time.perf_counter() - t
-    n = int(min(len(params), max(n0, math.floor(n0 * budget_s / max(dt, 1e-3)))))
-    t = time.perf_counter()
-    oracle.loglik(params[:n].astype(np.float64), *args, grad=True, nthreads=nt)
-    dt = time.perf_counter() - t
-    # the same on one core, on a smaller sample
-    n1 = max(2, min(len(params), int(n * 4.0 / budget_s / max(nt, 1)) + 1))
-    t = time.perf_counter()
-    oracle.loglik(params[:n1].astype(np.float64), *args, grad=True, nthreads=1)
-    dt1 = time.perf_counter() - t
-    return {"value": n / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
-            "sample": "%d of the %d vectors (log L + forward-mode gradient, FP64), %.1f s" % (n, len(params), dt),
-            "value_1core": n1 / dt1, "sample_1core": "%d vectors, %.1f s" % (n1, dt1)}
-
-
-def oracle_sample(spec, psf, image, params, budget_s: float = 4.0):
-    """The FP64 oracle (log L + gradient) on all host cores over a bounded
-    sample of a workload's vectors (one per core first, then more if that
-    took well under the budget): evals/s and what the sample was."""
-    import oracle
-    oracle.build()
-    nt = oracle.max_threads()
-    args = (image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k, spec.gain_exposure)
-    n = min(len(params), nt)
-    t = time.perf_counter()
-    oracle.loglik(params[:n].astype(np.float64), *args, grad=True, nthreads=nt)
-    dt = time.perf_counter() - t
-    if dt < budget_s / 3:
-        n = int(min(len(params), max(n, math.floor(n * budget_s / max(dt, 1e-3)))))
-        t = time.perf_counter()
-        oracle.loglik(params[:n].astype(np.float64), *args, grad=True, nthreads=nt)
-        dt = time.perf_counter() - t
-    return {"evals_per_s": n / dt, "cores": nt, "kind": "oracle",
-            "sample": "%d of the workload's vectors (log L + forward-mode gradient, FP64), %.1f s" % (n, dt)}
-
-
 def run_reference(args):
+    """The reference arm: the FP64 oracle timed on the host cores on the same
+    workload (same stored observed image, same parameter vectors, same config
+    object), each step a bounded sample of the vectors."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
     oracle.build()
-    c = inputs.WORKLOADS[WORKLOAD]
-    spec, B = c["spec"], c["B"]
-    rng = inputs.rng_for(WORKLOAD, 0)
-    truth = inputs.draw_truth(rng)
-    psf = inputs.make_psf(spec).astype(np.float32)
-    model = oracle.simulate(truth, spec.H, spec.W, psf, spec.pixel_scale, spec.k)[0]
-    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
-    params = inputs.draw_box(np.random.default_rng(rank_param_seed(0)), B).astype(np.float32)
+    workload = args.workload
+    spec, truth, psf, image = load_observed(workload)
+    params = workload_params(workload, 0, truth)
+    B = len(params)
     nt = oracle.max_threads()
     a = (image, np.float32(spec.sigma_bkg), psf, spec.pixel_scale, spec.k, spec.gain_exposure)
-    per_step = max(nt * 2, 32)
+    per_step = max(nt * 2, 32) if spec.H * spec.W * spec.k ** 2 <= 40000 else nt
     for w in range(args.warmup):
         oracle.loglik(params[:nt].astype(np.float64), *a, grad=True, nthreads=nt)
     times = []
@@ -544,10 +684,11 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "H": spec.H, "W": spec.W, "supersample": spec.k, "psf": spec.K, "B": B,
-                   "step_sample": per_step},
+        "config": dict(workload_config(workload), parallelism="single GPU" if args.gpus <= 1 else
+                       "replicas (B per GPU)"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
-                         "sample": "%d vectors per step of the %d-vector workload" % (per_step, B)},
+                         "sample": "%d vectors per step of the %d-vector workload (log L + forward-mode gradient, "
+                                   "FP64)" % (per_step, B)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -597,17 +738,22 @@ def run_small_batch(args, B: int = 50):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 400 for the 60x60 workload, 20 for the 200x200 stress workload)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[inputs.MULTISTART, inputs.STRESS],
+                    help="the metric's workload (default) or the 200x200, k = 4, B = 16384 stress workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-workloads", action="store_true",
-                    help="skip the HMC (100x100, k=4), stress (200x200, B=16384) and serving runs reported beside the metric")
+                    help="skip the workloads reported beside the metric (stress, HMC, serving, MAP, ...)")
     ap.add_argument("--small-batch", action="store_true",
                     help="only the sampler-sized call: B = 50 vectors of an 80x80, k = 2, 11x11-PSF system")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.steps is None:
+        args.steps = 20 if args.workload == inputs.STRESS else 400
     if args.impl == "reference":
         return run_reference(args)
     if args.small_batch:
@@ -615,7 +761,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2202_07663_gb300 import abi, build
+    from paper_2202_07663_gb300 import build
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -628,129 +774,21 @@ def main():
         build.build()
     if world > 1:
         dist.barrier()
-
-    spec, B, truth, psf, image, params = make_workload(device, rank)
-    sysm = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
-    sysm.reserve(B)
-    p_dev = torch.from_numpy(params).to(device)
-    ll = torch.empty(B, dtype=torch.float64, device=device)
-    g = torch.empty(B, 22, dtype=torch.float64, device=device)
-    stream = torch.cuda.current_stream(device)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)   # > L2 (129 MB)
-
-    def step():
-        sysm.loglik_grad(p_dev, out=(ll, g, None))
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    # ---- device-timed steps (inputs resident in HBM; L2 flushed between steps)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    abi.gl_profile_reset()
-    abi.gl_profile_enable(True)
-    n0 = abi.gl_launch_count()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
-        t0 = time.perf_counter()
-        for a, b in ev:
-            flush.zero_()
-            a.record(stream)
-            step()
-            b.record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    if world > 1:
-        dist.barrier()
-    launches = abi.gl_launch_count() - n0
-    prof = abi.gl_profile_read()
-    abi.gl_profile_enable(False)
-    step_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / args.steps, device, world)
-    value = whole_job_rate(world, B, step_ms * 1e-3)
-
-    # ---- end to end through the host-buffer entry point (pinned host memory)
-    hp = torch.from_numpy(params).pin_memory()
-    hl = torch.empty(B, dtype=torch.float64).pin_memory()
-    hg = torch.empty(B, 22, dtype=torch.float64).pin_memory()
-    hp_np, hl_np, hg_np = hp.numpy(), hl.numpy(), hg.numpy()
-    for _ in range(3):
-        sysm.loglik_grad_host(hp_np, hl_np, hg_np)
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sysm.loglik_grad_host(hp_np, hl_np, hg_np)
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, device, world)
-    e2e_value = whole_job_rate(world, B, e2e_s)
-
-    # ---- roofline of the dominant kernel, from the live event timings
-    n_adj, ms_adj = prof["k_ray_adj"]
-    N = series_terms(params, adjoint=True)
-    rays = spec.H * spec.W * spec.k * spec.k
-    flop_adj = float(rays * flops_ray_adj(N).sum())
-    adj_s = (ms_adj / max(n_adj, 1)) * 1e-3
-    peaks, peak_src = read_peaks()
-    sms = torch.cuda.get_device_properties(device).multi_processor_count
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = flop_adj / adj_s / 1e12
-    # special-function unit: 12 MUFU ops per ray in the adjoint; 32 per clock per SM
-    # (own ex2.approx throughput probe on this GPU)
-    mufu_peak = sms * 32 * sm_mhz * 1e6 / 1e9
-    mufu_achieved = rays * B * MUFU_RAY_ADJ / adj_s / 1e9
-    th = kernel_source_hash()
-    traffic = TRAFFIC.get(th)
-    if traffic is not None:
-        traffic = traffic * B / 4096.0   # captured at B = 4096; DRAM bytes scale with the vectors of a launch
-    kern = {k: {"launches": v[0], "ms_total": round(v[1], 4)} for k, v in prof.items() if v[0] > 0}
-    tot = sum(v[1] for v in prof.values())
-    for k in kern:
-        kern[k]["share"] = round(prof[k][1] / tot, 4) if tot > 0 else None
-    clocks = clk.summary()
-
+    peaks = measured_peaks()
+    cpu = not args.no_cpu_baseline
+    out = measure(args.workload, device, rank, world, args.steps, args.warmup, cpu, peaks)
     if world > 1:
         dist.barrier()
     if rank != 0:
         dist.destroy_process_group()
         return 0
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(spec, psf, image, params)
-    workloads = None
-    if world == 1 and not args.no_workloads:
-        cpu_w = not args.no_cpu_baseline
-        workloads = {"hmc": run_hmc_workload(device, cpu=cpu_w), "stress": run_stress_workload(device, cpu=cpu_w),
-                     "serving": run_serving_workload(device), "map": run_map_workload(device),
-                     "hmc_paper": run_hmc_paper_workload(device), "variant": run_variant_workload(device),
-                     "pipeline": run_pipeline_workload(device)}
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (f64 per-vector sums)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "H": spec.H, "W": spec.W, "supersample": spec.k, "psf": spec.K,
-                   "pixel_scale": spec.pixel_scale, "B_per_gpu": B, "params": "uniform over the prior box",
-                   "l2": "flushed (256 MB write) between timed steps, flush outside the step events",
-                   "parallelism": "replicas (B per GPU)" if world > 1 else "single GPU"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 22 * 4,
-                "d2h_bytes_per_step": B * 8 + B * 22 * 8},
-        "roofline": {"bound": "alu", "kernel": "k_ray_adj", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                     "flops_per_launch": flop_adj, "launch_ms": adj_s * 1e3,
-                     "peak_basis": "FP32 FMA: %d SMs x 128 lanes x 2 x %.0f MHz (max SM clock, %s peaks file)" % (
-                         sms, sm_mhz, peak_src),
-                     "mufu": {"achieved": mufu_achieved, "peak": mufu_peak, "unit": "Gop/s",
-                              "frac": mufu_achieved / mufu_peak, "ops_per_ray": MUFU_RAY_ADJ,
-                              "peak_basis": "%d SMs x 32 MUFU/clk (measured ex2 probe) x %.0f MHz" % (sms, sm_mhz)},
-                     "mean_series_terms": float(N.mean()), "kernel_source": th},
-        "kernels": kern,
-        "cpu_baseline": cpu,
-        "workloads": workloads,
-        "clocks": clocks,
-        "gpu_launches": int(launches),
-        "wall_s_timed": wall,
-    }
+    if world == 1 and not args.no_workloads and args.workload == WORKLOAD:
+        out["workloads"] = {
+            "stress": measure(inputs.STRESS, device, 0, 1, 20, 3, cpu, peaks),
+            "hmc": run_hmc_workload(device, cpu=cpu), "serving": run_serving_workload(device),
+            "map": run_map_workload(device), "hmc_paper": run_hmc_paper_workload(device),
+            "variant": run_variant_workload(device), "pipeline": run_pipeline_workload(device)}
+    out["peaks"] = peaks
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

@@ -29,6 +29,12 @@
  *    its log-likelihood, chi^2 and gradient come back as NaN.
  *  - Calls on one gl_system share its scratch memory: issue them on one
  *    stream (or serialise them). Different systems are independent.
+ *  - A gl_system lives on the device that was current when it was created.
+ *    Every call that takes one must be made with that device current (the
+ *    stream and the buffers belong to it too); otherwise the call returns
+ *    GL_ERR_INVALID_ARG before anything is launched. The library never
+ *    switches the current device for a call, except that gl_system_destroy
+ *    frees on the system's own device and then restores the caller's.
  */
 #ifndef GIGALENS_H_
 #define GIGALENS_H_
@@ -47,7 +53,7 @@ enum gl_status {
   GL_ERR_INVALID_ARG = -1, /* bad pointer, size or value; nothing was launched */
   GL_ERR_OOM = -2,         /* device or pinned allocation failed */
   GL_ERR_CUDA = -3,        /* a CUDA runtime call failed; see gl_last_error_message */
-  GL_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up */
+  GL_ERR_TIMEOUT = -4,     /* reserved: no call returns it (no kernel of the library waits on a flag) */
   GL_ERR_BUDGET = -5,      /* request exceeds the caller's memory budget */
   GL_ERR_UNSUPPORTED = -6  /* shape outside what the kernels support (e.g. image too large) */
 };
@@ -117,6 +123,12 @@ size_t gl_system_scratch_bytes(const gl_system* sys, int B);
 
 /* Device bytes held by the resident data (image, variance, PSF). */
 size_t gl_system_resident_bytes(const gl_system* sys);
+
+/* Device bytes of scratch (per-vector constants, image work buffer, tile
+ * partials) the system holds now: 0 after creation, grown by calls that
+ * need more and by gl_system_reserve; gl_loglik_grad_noalloc never grows it.
+ * NULL gives 0. */
+size_t gl_system_scratch_held(const gl_system* sys);
 
 /*
  * gl_loglik - log-likelihood of B parameter vectors (Sec. 2.1.2, Eq.
@@ -195,12 +207,13 @@ int gl_loglik_grad_grouped(gl_system* const* systems, const float* const* params
  * 2,000 vectors of a 60 x 60 image; scratch per vector is roughly
  * 4*H*W + 800 bytes).
  *
- * The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call shares the one array and leaves its
- * contents behind; nothing in it has to start at zero. Calls whose kernels
- * overlap on the GPU (two streams, or two host threads) race on the array:
- * issue them on one stream.
+ * Every call looks up the array's device address (cudaGetSymbolAddress)
+ * with the system's device current; the lookup allocates nothing. The first
+ * call on a device may also load the library's device code there, so make
+ * it before any stream capture. Every call shares the one array and leaves
+ * its contents behind; nothing in it has to start at zero. Calls whose
+ * kernels overlap on the GPU (two streams, or two host threads) race on the
+ * array: issue them on one stream.
  */
 int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* loglik_out, double* chi2_out,
                            double* grad_out, void* stream);
@@ -225,8 +238,10 @@ int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* l
  *   [B[s], 22], loglik_out[s] device float64 [B[s]], grad_out[s] device
  *   float64 [B[s], 22], chi2_out NULL or per segment NULL / [B[s]]. A system
  *   may appear in several segments. Host arrays are read before return; the
- *   work is asynchronous on stream. All runs of one batcher must be issued on
- *   one stream (they share the arena and the device table). The call blocks
+ *   work is asynchronous on stream. Runs of one batcher share its arena and
+ *   device table, so they execute one after another: a run issued on another
+ *   stream than the previous run's first waits (on the device) for that run
+ *   to finish. Make the calls from one host thread at a time. The call blocks
  *   only if the staging buffer it reuses is still being copied (two batches
  *   back). Errors: GL_ERR_BUDGET if the segments' scratch exceeds the arena,
  *   GL_ERR_UNSUPPORTED for a segment beyond max_H/max_W/max_K.
@@ -527,6 +542,22 @@ int gl_profile_reset(void);
 int gl_profile_read(long long* launches, double* total_ms);
 const char* gl_kernel_name(int kind);
 long long gl_launch_count(void);
+
+/*
+ * gl_profile_peak - measured throughput of one pipe of the current device,
+ * the denominator of the likelihood kernels' roofline (they are bound by
+ * FP32 arithmetic and the special-function unit, not by memory):
+ *   GL_PEAK_FP32_FMA  FP32 flop/s of packed fused multiply-adds (FMA = 2 flops)
+ *   GL_PEAK_MUFU_EX2  ex2.approx results/s of the special-function unit
+ * Each is the best of five timed launches of a kernel of independent
+ * dependency chains over every SM, at the clock the GPU runs at. rate_out is
+ * a HOST double. Blocking (synchronises the launches on the legacy default
+ * stream); allocates and frees a small device buffer. Errors:
+ * GL_ERR_INVALID_ARG for a NULL rate_out or an unknown kind; GL_ERR_CUDA.
+ */
+#define GL_PEAK_FP32_FMA 0
+#define GL_PEAK_MUFU_EX2 1
+int gl_profile_peak(int kind, double* rate_out);
 
 #ifdef __cplusplus
 }

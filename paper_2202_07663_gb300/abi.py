@@ -41,6 +41,7 @@ SIGNATURES = {
     "gl_system_reserve": ([_vp, _i], _i),
     "gl_system_scratch_bytes": ([_vp, _i], ctypes.c_size_t),
     "gl_system_resident_bytes": ([_vp], ctypes.c_size_t),
+    "gl_system_scratch_held": ([_vp], ctypes.c_size_t),
     "gl_loglik": ([_vp, _vp, _i, _vp, _vp, _vp], _i),
     "gl_loglik_grad": ([_vp, _vp, _i, _vp, _vp, _vp, _vp], _i),
     "gl_loglik_grad_host": ([_vp, _vp, _i, _vp, _vp, _vp, _vp], _i),
@@ -79,6 +80,7 @@ SIGNATURES = {
     "gl_profile_read": ([_vp, _vp], _i),
     "gl_kernel_name": ([_i], ctypes.c_char_p),
     "gl_launch_count": ([], ctypes.c_longlong),
+    "gl_profile_peak": ([_i, _vp], _i),
 }
 
 
@@ -235,6 +237,17 @@ def gl_launch_count() -> int:
     return int(lib_handle().gl_launch_count())
 
 
+GL_PEAK_FP32_FMA, GL_PEAK_MUFU_EX2 = 0, 1
+
+
+def gl_profile_peak(kind: int) -> float:
+    """Measured rate of a pipe of the current device: FP32 flop/s
+    (GL_PEAK_FP32_FMA) or ex2 results/s (GL_PEAK_MUFU_EX2)."""
+    r = ctypes.c_double()
+    _check(lib_handle().gl_profile_peak(kind, ctypes.addressof(r)), "gl_profile_peak")
+    return float(r.value)
+
+
 # ------------------------------------------------------------ objects -------
 
 class GLSystem:
@@ -280,6 +293,10 @@ class GLSystem:
 
     def resident_bytes(self) -> int:
         return int(lib_handle().gl_system_resident_bytes(self._h))
+
+    def scratch_held(self) -> int:
+        """Device bytes of scratch the system holds now (0 until a call needs some)."""
+        return int(lib_handle().gl_system_scratch_held(self._h))
 
     def _params(self, params):
         import torch

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(CSRC, "libgigalens.so")
 BUILD_DIR = os.path.join(CSRC, "_build")
-SOURCES = ["gl_kernels.cu", "gl_abi.cu", "gl_noalloc.cu", "gl_hmc.cu", "gl_batch.cu", "gl_map.cu", "gl_vi.cu", "gl_variant.cu"]
+SOURCES = ["gl_kernels.cu", "gl_abi.cu", "gl_noalloc.cu", "gl_hmc.cu", "gl_batch.cu", "gl_map.cu", "gl_vi.cu", "gl_variant.cu", "gl_probe.cu"]
 HEADERS = ["gl_device.cuh", "gl_launch.h", "gl_internal.h", "gl_prior.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

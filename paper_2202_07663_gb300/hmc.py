@@ -12,6 +12,7 @@ uniforms) come from a seeded torch generator and are passed in. The mass
 matrix is diagonal. Targets:
 
 - ``LensTarget``: log L in the physical parameters (the HMC throughput workload);
+- ``AutogradTarget``: the same log L through ``LogLik`` and ``torch.autograd``;
 - ``PosteriorTarget``: the posterior of the unconstrained parameters,
   log p~(z) = log L(g(z)) + log p(g(z)) + log|J| (Eq. reparam-post), through
   ``gl_map_transform`` and ``gl_posterior_grad`` — the paper's sampler;
@@ -74,6 +75,27 @@ class LensTarget:
 
     def __call__(self, q64, q32, lp_out, g_out):
         self.system.loglik_grad(q32, out=(lp_out, g_out, None))
+
+
+class AutogradTarget:
+    """log L in the physical parameters through ``LogLik`` and
+    ``torch.autograd.grad``: the chain's FP64 positions are the leaf, the
+    Function's forward runs the likelihood and the adjoint, its backward
+    scales the stashed gradient. The same numbers as ``LensTarget`` (which
+    calls the library directly), plus autograd's bookkeeping."""
+    needs_q32 = False
+
+    def __init__(self, system):
+        self.system = system
+
+    def __call__(self, q64, q32, lp_out, g_out):
+        q = q64.detach().requires_grad_(g_out is not None)
+        with torch.enable_grad():
+            ll = LogLik.apply(q, self.system)
+            if g_out is not None:
+                (g,) = torch.autograd.grad(ll.sum(), q)
+                g_out.copy_(g)
+        lp_out.copy_(ll.detach())
 
 
 class PosteriorTarget:

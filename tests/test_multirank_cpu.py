@@ -28,7 +28,7 @@ def _worker(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        seed = bench.rank_param_seed(rank)
+        seed = bench.rank_param_seed(bench.WORKLOAD, rank)
         p = inputs.draw_box(np.random.default_rng(seed), 8)
         t = 1.0 + rank  # rank 1 is the slow one
         tmax = bench.max_over_ranks(t, torch.device("cpu"), world)
