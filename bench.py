@@ -86,7 +86,7 @@ MUFU_RAY_ADJ = 12   # ex2/lg2/rcp per ray in the adjoint (EPL power, two Sersic 
 # DRAM bytes per launch of k_ray_adj from one ncu capture, keyed by workload
 # and the kernel source it was taken on (sha256 prefix of gl_kernels.cu +
 # gl_device.cuh); any other source reports null traffic until it is captured again.
-TRAFFIC = {}
+TRAFFIC = {("multistart-60x60-k2-psf11-B4096", "be933c83770bac56"): 64.532e6}
 
 
 def kernel_source_hash() -> str:

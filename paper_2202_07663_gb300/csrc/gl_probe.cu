@@ -11,7 +11,7 @@
 
 namespace {
 
-constexpr int kChains = 8;          // independent dependency chains per thread
+constexpr int kChains = 16;         // independent dependency chains per thread
 constexpr int kThreads = 256;
 constexpr int kBlocksPerSM = 4;
 
@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(kThreads) k_peak_ffma2(int iters, float* out) 
   const float2 m = make_float2(0.9999999f, 0.9999998f), c = make_float2(1e-7f, 2e-7f);
 #pragma unroll
   for (int j = 0; j < kChains; ++j) a[j] = make_float2(threadIdx.x * 1e-3f + j, 0.5f * j);
+#pragma unroll 4
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int j = 0; j < kChains; ++j) a[j] = __ffma2_rn(a[j], m, c);
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_peak_ex2(int iters, float* out) {
   float a[kChains];
 #pragma unroll
   for (int j = 0; j < kChains; ++j) a[j] = 0.1f * (j + 1) + threadIdx.x * 1e-6f;
+#pragma unroll 4
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int j = 0; j < kChains; ++j) a[j] = gl::ex2(-a[j]);
@@ -57,7 +59,7 @@ extern "C" int gl_profile_peak(int kind, double* rate_out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return gl_internal::cuda_error(e, "device query");
   const int grid = sms * kBlocksPerSM;
-  const int iters = kind == GL_PEAK_FP32_FMA ? 8192 : 2048;
+  const int iters = kind == GL_PEAK_FP32_FMA ? 4096 : 1024;   // a multiple of the unroll
   float* out = nullptr;
   cudaEvent_t a = nullptr, b = nullptr;
   if ((e = cudaMalloc(&out, sizeof(float) * size_t(grid) * kThreads)) != cudaSuccess)

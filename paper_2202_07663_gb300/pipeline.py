@@ -9,8 +9,12 @@
    first 80% of n_burn = 250, then n_sample = 750.
 
 ``preconditioner="laplace"`` replaces the VI covariance (for HMC's mass and
-the chains' start) by the Laplace covariance of log p~(z) at the MAP point
-(see ``hmc.laplace_covariance``); VI still runs and is timed.
+the chains' start) by the Laplace covariance of log p~(z) at the VI mean
+(see ``hmc.laplace_covariance``). It is taken at the VI mean, not at the MAP
+point: when the best start ends at a local mode (the paper's 300 iterations
+do not always reach the global one), the Hessian there describes the wrong
+basin and the chains stay in it, while VI has already moved its mean toward
+the posterior mass.
 Every stage runs in the library's kernels; this module only sequences them.
 
 With a process group (one GPU per process, ``distributed``) the starts, the
@@ -78,7 +82,7 @@ def model_system(system: abi.GLSystem, theta_starts: torch.Tensor, prior=None, m
     if preconditioner == "vi":
         mu, cov = r.mu, r.cov
     else:
-        mu, cov = z_map, hmc.laplace_covariance(post, z_map)
+        mu, cov = r.mu, hmc.laplace_covariance(post, r.mu)
         evals["laplace"] = 2 * NPARAM
     torch.cuda.synchronize(dev)
     t3 = time.perf_counter()
