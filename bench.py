@@ -480,41 +480,54 @@ def run_serving_workload(device, n_latency: int = 200, n_capacity: int = 1000):
             "speedup_lenses_per_s": cap.lenses_per_s / base_cap.lenses_per_s}
 
 
-def run_map_workload(device, n_starts: int = 300, steps=(300, 1000, 3000)):
-    """Sec. 2.3 / Table 1: multi-start MAP, 300 starts drawn from the prior, on
-    a system drawn from the paper's simulation distribution (80x80, k = 2,
-    sigma_bkg = 0.2, t_exp = 100 s, G = 1). Reports time, the fraction of
-    starts that end at reduced chi^2 <= 1.01 (the paper's marker of runs that
-    reached the global mode, Sec. 2.3) and the fraction whose objective ends
-    within 1 of the best start's (the same optimum)."""
+def run_map_workload(device, n_starts: int = 300, steps=(300, 1000, 3000), seeds=(202, 303, 404, 505, 606, 707)):
+    """Sec. 2.3 / Table 1: multi-start MAP, 300 starts drawn from the prior,
+    on six systems drawn from the paper's simulation distribution (80x80,
+    k = 2, sigma_bkg = 0.2, t_exp = 100 s, G = 1), for 300, 1000 and 3000
+    Adam iterations (10^-2 -> 10^-3 linearly over the run). Per system and
+    iteration count: time, the best start's distance to the global optimum in
+    objective (df = f - f_opt, f the negative log posterior; f_opt the lowest
+    value over every run, including 16 starts near the truth run for 3000
+    iterations), the fractions of starts with df <= 1 and <= 5, and with
+    reduced chi^2 <= 1.01 (the paper's marker, Sec. 2.3)."""
     import torch
     from paper_2202_07663_gb300 import abi, map as gmap
     spec = inputs.PAPER_SAMPLE_SPEC
-    rng = np.random.default_rng(202)
-    truth = inputs.draw_table(rng, inputs.PAPER_SIM, 1)[0]
     psf = inputs.make_psf(spec).astype(np.float32)
-    blank = np.zeros((spec.H, spec.W), np.float32)
-    s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
-    model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
-    s0.close()
-    image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
-    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
-    s.reserve(n_starts)
+    dof = spec.H * spec.W - 22
     th0 = torch.from_numpy(inputs.draw_table(np.random.default_rng(13), inputs.PAPER_PRIOR_DRAW,
                                              n_starts).astype(np.float32)).to(device)
-    out = {"workload": "map-multistart-80x80-k2-psf11-paper-noise", "starts": n_starts, "runs": []}
-    for k in steps:
+    out = {"workload": "map-multistart-80x80-k2-psf11-paper-noise", "starts": n_starts, "systems": []}
+    for seed in seeds:
+        rng = np.random.default_rng(seed)
+        truth = inputs.draw_table(rng, inputs.PAPER_SIM, 1)[0]
+        blank = np.zeros((spec.H, spec.W), np.float32)
+        s0 = abi.GLSystem(blank, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+        model = s0.simulate(torch.from_numpy(truth.astype(np.float32)[None]).to(device)).cpu().numpy()[0]
+        s0.close()
+        image = inputs.add_noise(rng, model, spec.sigma_bkg, spec.gain_exposure).astype(np.float32)
+        s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+        s.reserve(n_starts)
+        near = torch.from_numpy(inputs.draw_perturbed(np.random.default_rng(seed + 1), truth, 16, frac=0.005)
+                                .astype(np.float32)).to(device)
         gmap.MultiStartMAP(s, steps=5).run(th0[:8])   # warm-up
-        r = gmap.MultiStartMAP(s, steps=k).run(th0)
-        _, c2 = s.loglik(r.theta, chi2=True)
-        chi2nu = c2.cpu().numpy() / (spec.H * spec.W - 22)
-        f = r.objective.cpu().numpy()
-        fbest = float(np.nanmin(f))
-        out["runs"].append({"iterations": k, "seconds": r.seconds, "evals_per_s": r.grad_evals / r.seconds,
-                            "fraction_chi2nu_le_1.01": float(np.mean(chi2nu <= 1.01)),
-                            "fraction_at_best_objective": float(np.mean(f <= fbest + 1.0)),
-                            "best_objective": fbest, "best_chi2nu": float(chi2nu[int(np.nanargmin(f))])})
-    s.close()
+        f_near = gmap.MultiStartMAP(s, steps=max(steps)).run(near).objective.cpu().numpy()
+        runs = []
+        for k in steps:
+            r = gmap.MultiStartMAP(s, steps=k).run(th0)
+            _, c2 = s.loglik(r.theta, chi2=True)
+            runs.append((k, r, r.objective.cpu().numpy(), c2.cpu().numpy() / dof))
+        f_opt = float(min(np.nanmin(f_near), *(np.nanmin(f) for _, _, f, _ in runs)))
+        rec = {"seed": seed, "f_opt": f_opt, "runs": []}
+        for k, r, f, chi2nu in runs:
+            df = f - f_opt
+            b = int(np.nanargmin(f))
+            rec["runs"].append({"iterations": k, "seconds": r.seconds, "evals_per_s": r.grad_evals / r.seconds,
+                                "best_df": float(df[b]), "best_chi2nu": float(chi2nu[b]),
+                                "fraction_df_le_1": float(np.mean(df <= 1)), "fraction_df_le_5": float(np.mean(df <= 5)),
+                                "fraction_chi2nu_le_1.01": float(np.mean(chi2nu <= 1.01))})
+        out["systems"].append(rec)
+        s.close()
     return out
 
 

@@ -166,6 +166,21 @@ __device__ __forceinline__ float grid_coord(int n, float hh, float hl) {
   return fmaf(f, hh, f * hl);
 }
 
+// ------------------------------------------- programmatic dependent launch ---
+// The likelihood kernels of a call are launched with programmatic stream
+// serialization. A kernel's blocks wait on the device for the previous grid
+// to complete and its writes to be visible before they read anything (the
+// constructor), and signal, when they are done, that the next grid may be
+// scheduled (the destructor, on every exit path); the next grid is then
+// launched while this one's last blocks drain. (Signalling at the start of
+// a block instead let the next grid's blocks be placed on the SMs while this
+// one still held them, and measured slower.) Without the launch attribute
+// both instructions do nothing.
+struct PdlScope {
+  __device__ __forceinline__ PdlScope() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+  __device__ __forceinline__ ~PdlScope() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+};
+
 // --------------------------------------------------------- packed pairs ---
 // Two rays of one parameter vector evaluated in lockstep with Blackwell's
 // packed FP32 instructions (one f32x2 FMA/MUL/ADD does the arithmetic of two
@@ -215,6 +230,11 @@ __device__ __forceinline__ float lg2c(float x) {
 __device__ __forceinline__ float lg2cT(float a) { return lg2c(a); }
 __device__ __forceinline__ F2 lg2cT(F2 a) { return {make_float2(lg2c(a.v.x), lg2c(a.v.y))}; }
 
+// The same for a packed pair of grid indices n already in float (exact: |n|
+// is far below 2^24), so that the inner subpixel loops step n by exact float
+// adds instead of converting an integer per ray.
+__device__ __forceinline__ F2 grid_coord2(F2 n, float hh, float hl) { return fmaT(n, sp<F2>(hh), n * sp<F2>(hl)); }
+
 // Elliptical Sersic at (px, py), generic in the ray type; the forward model,
 // so its log2 is the unbiased one (log L sums the model over every pixel).
 template <class T>
@@ -236,9 +256,9 @@ __device__ __forceinline__ void epl_fwd_T(const VecConst& V, const float* an, T 
   const T wi = fmaT(sp<T>(V.e1), dy, fmaT(sp<T>(-V.e2), dx, dy));
   const T w2 = fmaT(wr, wr, wi * wi);
   const T keep = geT(w2, sp<T>(V.w2min));
-  const T lw = lg2T(maxT(w2, sp<T>(V.w2min)));
-  const T S = keep * ex2T(fmaT(sp<T>(V.t), fmaT(sp<T>(-0.5f), lw, sp<T>(V.lc)), sp<T>(V.tlc_lo)));
-  const T iw2 = rcpT(maxT(w2, sp<T>(1e-30f)));
+  const T w2c = maxT(w2, sp<T>(V.w2min));   // > 0; where it clamps, keep = 0 zeroes the deflection
+  const T S = keep * ex2T(fmaT(sp<T>(V.t), fmaT(sp<T>(-0.5f), lg2T(w2c), sp<T>(V.lc)), sp<T>(V.tlc_lo)));
+  const T iw2 = rcpT(w2c);
   const T nwi = -wi;
   const T vr = fmaT(wr, wr, nwi * wi) * iw2;
   const T vi = sp<T>(2.f) * wr * wi * iw2;

@@ -271,6 +271,7 @@ __device__ __forceinline__ void series_coeffs(int lane, float t, VecConst* V) {
 // phases write disjoint fields of VecConst.
 template <class Src>
 __global__ void k_setup(const __grid_constant__ Src src) {
+  const PdlScope pdl;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const int nvec = src.nvec();
@@ -343,6 +344,7 @@ template <class Src>
 __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd(const __grid_constant__ Src src) {
   __shared__ VecConst sv;
   __shared__ Seg ss;
+  const PdlScope pdl;
   for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
     int local;
     const Seg* segp = src.ray_seg(item, local);
@@ -367,10 +369,15 @@ __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd(const __gr
       const int iq = qq / W, jq = qq - iq * W;
       F2 acc = sp<F2>(0.f);
       if (valid) {
-        for (int a = 0; a < k; ++a) {
-          const F2 y = {make_float2(grid_coord(2 * (ip * k + a) + ss.ny0, ss.hh, ss.hl), grid_coord(2 * (iq * k + a) + ss.ny0, ss.hh, ss.hl))};
-          for (int c = 0; c < k; ++c) {
-            const F2 x = {make_float2(grid_coord(2 * (jp * k + c) + ss.nx0, ss.hh, ss.hl), grid_coord(2 * (jq * k + c) + ss.nx0, ss.hh, ss.hl))};
+        // grid indices of the pixels' first subpixels; a subpixel step adds 2
+        const F2 ny0 = {make_float2(float(2 * ip * k + ss.ny0), float(2 * iq * k + ss.ny0))};
+        const F2 nx0 = {make_float2(float(2 * jp * k + ss.nx0), float(2 * jq * k + ss.nx0))};
+        F2 ny = ny0;
+        for (int a = 0; a < k; ++a, ny = ny + sp<F2>(2.f)) {
+          const F2 y = grid_coord2(ny, ss.hh, ss.hl);
+          F2 nx = nx0;
+          for (int c = 0; c < k; ++c, nx = nx + sp<F2>(2.f)) {
+            const F2 x = grid_coord2(nx, ss.hh, ss.hl);
             acc = acc + ray_intensity_T(sv, sv.an, x, y);
           }
         }
@@ -394,6 +401,7 @@ template <class Src>
 __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd_basis(const __grid_constant__ Src src) {
   __shared__ VecConst sv;
   __shared__ Seg ss;
+  const PdlScope pdl;
   for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
     int local;
     const Seg* segp = src.ray_seg(item, local);
@@ -423,10 +431,14 @@ __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd_basis(cons
       const int iq = qq / W, jq = qq - iq * W;
       F2 acc_l = sp<F2>(0.f), acc_s = sp<F2>(0.f);
       if (valid) {
-        for (int a = 0; a < k; ++a) {
-          const F2 y = {make_float2(grid_coord(2 * (ip * k + a) + ss.ny0, ss.hh, ss.hl), grid_coord(2 * (iq * k + a) + ss.ny0, ss.hh, ss.hl))};
-          for (int c = 0; c < k; ++c) {
-            const F2 x = {make_float2(grid_coord(2 * (jp * k + c) + ss.nx0, ss.hh, ss.hl), grid_coord(2 * (jq * k + c) + ss.nx0, ss.hh, ss.hl))};
+        const F2 ny0 = {make_float2(float(2 * ip * k + ss.ny0), float(2 * iq * k + ss.ny0))};
+        const F2 nx0 = {make_float2(float(2 * jp * k + ss.nx0), float(2 * jq * k + ss.nx0))};
+        F2 ny = ny0;
+        for (int a = 0; a < k; ++a, ny = ny + sp<F2>(2.f)) {
+          const F2 y = grid_coord2(ny, ss.hh, ss.hl);
+          F2 nx = nx0;
+          for (int c = 0; c < k; ++c, nx = nx + sp<F2>(2.f)) {
+            const F2 x = grid_coord2(nx, ss.hh, ss.hl);
             F2 ax, ay;
             epl_fwd_T(sv, sv.an, x, y, ax, ay);
             const F2 bx = x - ax - fmaT(sp<F2>(sv.g1), x, sp<F2>(sv.g2) * y);
@@ -499,9 +511,10 @@ __device__ __forceinline__ void ray_adj(const VecConst& V, const float* an, cons
   const T wi = fmaT(sp<T>(V.e1), dy, fmaT(sp<T>(-V.e2), dx, dy));
   const T w2 = fmaT(wr, wr, wi * wi);
   const T keep = geT(w2, sp<T>(V.w2min));
-  const T lrho = fmaT(sp<T>(-0.5f), lg2T(maxT(w2, sp<T>(V.w2min))), sp<T>(V.lc));  // log2(thetaE / rho)
+  const T w2c = maxT(w2, sp<T>(V.w2min));   // > 0; where it clamps, S = 0 zeroes every EPL term
+  const T lrho = fmaT(sp<T>(-0.5f), lg2T(w2c), sp<T>(V.lc));  // log2(thetaE / rho)
   const T S = keep * ex2T(fmaT(sp<T>(V.t), lrho, sp<T>(V.tlc_lo)));
-  const T iw2 = rcpT(maxT(w2, sp<T>(1e-30f)));
+  const T iw2 = rcpT(w2c);
   const T nwi = -wi;
   const T vr = fmaT(wr, wr, nwi * wi) * iw2;
   const T vi = sp<T>(2.f) * wr * wi * iw2;
@@ -601,6 +614,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, MINB) k_ray_adj(const __grid_cons
   __shared__ VecConst sv;
   __shared__ Seg ss;
   __shared__ double red[ADJ_THREADS / 32][NACC];
+  const PdlScope pdl;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int item = blockIdx.x; item < src.nray(); item += gridDim.x) {
     int local;
@@ -628,10 +642,14 @@ __global__ void __launch_bounds__(ADJ_THREADS, MINB) k_ray_adj(const __grid_cons
           const int ip = p / W, jp = p - ip * W;
           const int iq = q / W, jq = q - iq * W;
           const F2 g = {make_float2(gpre[p], gpre[q])};
+          // (indices converted per ray here: float-stepped indices, as in the
+          // forward kernel, cost this register-bound kernel spills and time)
           for (int a = 0; a < k; ++a) {
-            const F2 y = {make_float2(grid_coord(2 * (ip * k + a) + ss.ny0, ss.hh, ss.hl), grid_coord(2 * (iq * k + a) + ss.ny0, ss.hh, ss.hl))};
+            const F2 y = {make_float2(grid_coord(2 * (ip * k + a) + ss.ny0, ss.hh, ss.hl),
+                                      grid_coord(2 * (iq * k + a) + ss.ny0, ss.hh, ss.hl))};
             for (int c = 0; c < k; ++c) {
-              const F2 x = {make_float2(grid_coord(2 * (jp * k + c) + ss.nx0, ss.hh, ss.hl), grid_coord(2 * (jq * k + c) + ss.nx0, ss.hh, ss.hl))};
+              const F2 x = {make_float2(grid_coord(2 * (jp * k + c) + ss.nx0, ss.hh, ss.hl),
+                                        grid_coord(2 * (jq * k + c) + ss.nx0, ss.hh, ss.hl))};
               ray_adj(sv, sv.an, sv.ant, x, y, g, acc);
             }
           }
@@ -1082,6 +1100,7 @@ __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src s
   float* smem = reinterpret_cast<float*>(smem4);
   __shared__ double red2[2 * (NT / 32)];
   __shared__ Seg ss;
+  const PdlScope pdl;
   for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x) {
     int b;
     const Seg* segp = src.conv_seg(item, b);
@@ -1124,6 +1143,7 @@ __global__ void __launch_bounds__(BAND_THREADS) k_conv_bands(const __grid_consta
   float* smem = reinterpret_cast<float*>(smem4);
   __shared__ double red2[2 * (BAND_THREADS / 32)];
   __shared__ double band_sum[2];
+  const PdlScope pdl;
   constexpr int S = 16, KP = (K + 3) & ~3, c = (K - 1) / 2;
   const Seg& s = src.s;
   const int nb = int(cluster.num_blocks()), rank = int(cluster.block_rank());
@@ -1277,6 +1297,7 @@ __device__ __forceinline__ double chain_rule(int j, const double* a, const float
 // One thread per vector (calls whose vectors have one ray tile each).
 template <class Src>
 __global__ void k_final(const __grid_constant__ Src src) {
+  const PdlScope pdl;
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < src.nvec(); item += gridDim.x * blockDim.x) {
     int b;
     const Seg* s = src.vec_seg(item, b);
@@ -1302,6 +1323,7 @@ __global__ void k_final(const __grid_constant__ Src src) {
 template <class Src>
 __global__ void k_final_warp(const __grid_constant__ Src src) {
   __shared__ double sa[FINAL_THREADS / 32][NACC];
+  const PdlScope pdl;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   for (int item = blockIdx.x * wpb + w; item < src.nvec(); item += gridDim.x * wpb) {
     int b;
@@ -1378,18 +1400,72 @@ size_t conv_smem_bytes(int H, int W, int K, bool two_buf) {
 
 bool conv_two_buf(int H, int W, int K) { return conv_smem_bytes(H, W, K, true) <= CONV_TWO_BUF_MAX_SMEM; }
 
-void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix) {
+// Ray tiles of at most this many rays take the three-blocks-per-SM adjoint.
+constexpr long long ADJ_SHORT_TILE_RAYS = 32768;
+
+// Resident blocks per SM of the forward ray kernel (occupancy query, cached;
+// its launch bound if the query fails, e.g. without a GPU).
+static int fwd_blocks_per_sm() {
+  static std::atomic<int> cached{0};
+  int n = cached.load(std::memory_order_relaxed);
+  if (n == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ray_fwd<OneSeg>, FWD_THREADS, 0) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = GL_FWD_MINB;
+    }
+    cached.store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
+// Tiling of a B-vector call's rays: the tile count that minimises a model of
+// the two ray kernels' time, waves x (pixels per tile + a fixed per-tile
+// cost of 64 pixels), the forward kernel at its resident blocks per SM and
+// the adjoint, 2.4 times the forward's cost per ray (measured at 60 x 60,
+// k = 2), at two or three blocks per SM (a three-block wave takes 3/2.054 of
+// a two-block wave: a block's time grows with the blocks sharing its SM, and
+// three share 1.027x the work of two; three only for tiles of at most
+// ADJ_SHORT_TILE_RAYS rays, whose spills cost little). Tiles keep at least
+// 8 rays per thread of a 256-thread block; ties go to fewer tiles. Small
+// batches are where the waves matter: 50 vectors of 80 x 80, k = 2, take 9
+// tiles (one adjoint wave) instead of 13 (1.4 waves).
+struct TilePlan {
+  int ntiles, tile_pix;
+  bool adj3;
+};
+
+static TilePlan plan_rays(int B, int H, int W, int k) {
   const int HW = H * W;
+  TilePlan best{1, HW, false};
+  if (B <= 0 || HW <= 0) return best;
   const long long rays = (long long)HW * k * k;
-  const int target = num_sms() * 8;
-  long long nt = B > 0 ? (target + B - 1) / B : 1;
-  const long long by_work = (rays + RAY_THREADS * 8 - 1) / (RAY_THREADS * 8);  // >= 8 rays per thread
-  if (nt > by_work) nt = by_work;
-  if (nt < 1) nt = 1;
-  if (nt > HW) nt = HW;
-  int tp = int((HW + nt - 1) / nt);
-  *tile_pix = tp;
-  *ntiles = (HW + tp - 1) / tp;
+  long long max_nt = (rays + RAY_THREADS * 8 - 1) / (RAY_THREADS * 8);
+  if (max_nt > HW) max_nt = HW;
+  if (max_nt < 1) max_nt = 1;
+  const double sms = num_sms(), fwd_slots = sms * fwd_blocks_per_sm();
+  double best_cost = 0.0;
+  for (long long nt = 1; nt <= max_nt; ++nt) {
+    const int tp = int((HW + nt - 1) / nt);
+    const int ntt = (HW + tp - 1) / tp;
+    if (ntt != nt) continue;   // the same tiling as a smaller count
+    const double items = double(B) * ntt, px = tp + 64.0;
+    const double fwd = std::ceil(items / fwd_slots) * px;
+    const double adj2 = std::ceil(items / (2 * sms)) * px;
+    const bool short_tile = (long long)tp * k * k <= ADJ_SHORT_TILE_RAYS;
+    const double adj3 = short_tile ? std::ceil(items / (3 * sms)) * px * (3.0 / 2.054) : 1e300;
+    const double cost = fwd + 2.4 * (adj3 < adj2 ? adj3 : adj2);
+    if (nt == 1 || cost < best_cost * (1.0 - 1e-9)) {
+      best_cost = cost;
+      best = TilePlan{ntt, tp, adj3 < adj2};
+    }
+  }
+  return best;
+}
+
+void plan_tiles(int B, int H, int W, int k, int* ntiles, int* tile_pix) {
+  const TilePlan p = plan_rays(B, H, W, k);
+  *ntiles = p.ntiles;
+  *tile_pix = p.tile_pix;
 }
 
 // Blocks of a convolution kernel resident on the whole GPU at a dynamic
@@ -1408,6 +1484,24 @@ static cudaError_t conv_resident(size_t smem, int* resident) {
   }
   *resident = num_sms() * it->second;
   return cudaSuccess;
+}
+
+// Launch with programmatic stream serialization (see pdl_begin): the kernel
+// may be scheduled while its predecessor in the stream drains.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 template <int K, int R, int NT, int MINB, class Src>
@@ -1432,8 +1526,7 @@ static cudaError_t launch_conv(const Src& src, int nitems, size_t smem, int mode
     if (e != cudaSuccess) return e;
     grid = grid < resident ? grid : resident;
   }
-  k_conv<K, R, NT, MINB, Src><<<grid, NT, smem, st>>>(src, mode);
-  return cudaSuccess;
+  return launch_pdl(k_conv<K, R, NT, MINB, Src>, unsigned(grid), NT, smem, st, src, mode);
 }
 
 // wide: 512-thread blocks for calls with fewer vectors than SMs (one vector's
@@ -1456,12 +1549,12 @@ static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t
 }
 
 // Row bands for the cluster convolution of a B-vector call (0: one block per
-// vector instead). Bands only below half as many vectors as SMs, at most 8 per
-// vector (a portable cluster), each at least max(16, (K - 1) / 2) rows and
-// within CONV_TWO_BUF_MAX_SMEM of shared memory.
+// vector instead). Bands only below half as many vectors as SMs: up to two
+// blocks per SM, at most 8 per vector (a portable cluster), each at least
+// max(16, (K - 1) / 2) rows and within CONV_TWO_BUF_MAX_SMEM of shared memory.
 static int conv_bands(int B, int H, int W, int K) {
   if ((K != 11 && K != 21) || B < 1 || 2 * B > num_sms()) return 0;
-  int nb = num_sms() / B;
+  int nb = 2 * num_sms() / B;
   if (nb > 8) nb = 8;
   const int min_rows = (K - 1) / 2 > 16 ? (K - 1) / 2 : 16;
   while (nb > 1 && (H + nb - 1) / nb < min_rows) --nb;
@@ -1487,18 +1580,17 @@ static cudaError_t launch_conv_bands(const OneSeg& src, int nb, int mode, cudaSt
   cfg.blockDim = dim3(BAND_THREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = unsigned(nb);
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_conv_bands<K>, src, mode, rows);
 }
-
-// Ray tiles of at most this many rays take the three-blocks-per-SM adjoint.
-constexpr long long ADJ_SHORT_TILE_RAYS = 32768;
 
 template <class Src>
 static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj_final, cudaStream_t st,
@@ -1519,26 +1611,30 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
   }
   if (fwd) {
     hooks->before(GL_K_SETUP, st);
-    k_setup<Src><<<sgrid, vthreads, 0, st>>>(src);
-    if ((e = hooks->after(GL_K_SETUP, st)) != cudaSuccess) return e;
+    e = launch_pdl(k_setup<Src>, unsigned(sgrid), vthreads, 0, st, src);
+    cudaError_t h = hooks->after(GL_K_SETUP, st);
+    if (e != cudaSuccess || (e = h) != cudaSuccess) return e;
     if (!fwd_rays) return cudaSuccess;   // setup only (the correlation-only gradient)
     hooks->before(GL_K_RAY_FWD, st);
-    k_ray_fwd<Src><<<rgrid, FWD_THREADS, 0, st>>>(src);
-    return hooks->after(GL_K_RAY_FWD, st);
+    e = launch_pdl(k_ray_fwd<Src>, unsigned(rgrid), FWD_THREADS, 0, st, src);
+    h = hooks->after(GL_K_RAY_FWD, st);
+    return e != cudaSuccess ? e : h;
   }
   if (adj_final) {
     hooks->before(GL_K_RAY_ADJ, st);
     if (short_tiles)
-      k_ray_adj<Src, 3><<<rgrid, ADJ_THREADS, 0, st>>>(src);
+      e = launch_pdl(k_ray_adj<Src, 3>, unsigned(rgrid), ADJ_THREADS, 0, st, src);
     else
-      k_ray_adj<Src><<<rgrid, ADJ_THREADS, 0, st>>>(src);
-    if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
+      e = launch_pdl(k_ray_adj<Src>, unsigned(rgrid), ADJ_THREADS, 0, st, src);
+    cudaError_t h = hooks->after(GL_K_RAY_ADJ, st);
+    if (e != cudaSuccess || (e = h) != cudaSuccess) return e;
     hooks->before(GL_K_FINAL, st);
     if (one_tile)
-      k_final<Src><<<fgrid, FINAL_THREADS, 0, st>>>(src);
+      e = launch_pdl(k_final<Src>, unsigned(fgrid), FINAL_THREADS, 0, st, src);
     else
-      k_final_warp<Src><<<wgrid, FINAL_THREADS, 0, st>>>(src);
-    return hooks->after(GL_K_FINAL, st);
+      e = launch_pdl(k_final_warp<Src>, unsigned(wgrid), FINAL_THREADS, 0, st, src);
+    h = hooks->after(GL_K_FINAL, st);
+    return e != cudaSuccess ? e : h;
   }
   return cudaSuccess;
 }
@@ -1559,14 +1655,10 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD && mode != MODE_CORR) return cudaSuccess;
-  // three blocks per SM for short tiles when the waves favour it: a block's
-  // time grows with the blocks sharing its SM, three share 1.027x the work of
-  // two, so three win when 3 w3 < 2.054 w2 (w_m = tiles / (SMs m), rounded up;
-  // B = 300 on 80x80: 4 waves against 5, two blocks win, as measured)
-  const long long items = (long long)s.B * s.ntiles, sms = num_sms();
-  const long long w2 = (items + 2 * sms - 1) / (2 * sms), w3 = (items + 3 * sms - 1) / (3 * sms);
-  const bool short_tiles = (long long)s.tile_pix * s.k * s.k <= ADJ_SHORT_TILE_RAYS && 3000 * w3 < 2054 * w2;
-  return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false, s.ntiles == 1, true, short_tiles);
+  // the adjoint's blocks per SM as the tile plan chose them (plan_rays)
+  const TilePlan tp = plan_rays(s.B, s.H, s.W, s.k);
+  const bool three = tp.adj3 && tp.ntiles == s.ntiles && tp.tile_pix == s.tile_pix;
+  return run_rays(src, s.B, s.B * s.ntiles, false, true, st, hooks, false, s.ntiles == 1, true, three);
 }
 
 cudaError_t launch_basis(const Seg& s, cudaStream_t st, Hooks* hooks) {
@@ -1575,7 +1667,8 @@ cudaError_t launch_basis(const Seg& s, cudaStream_t st, Hooks* hooks) {
   cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false, false);   // setup
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_RAY_FWD, st);
-  k_ray_fwd_basis<OneSeg><<<s.B * s.ntiles, FWD_THREADS, 0, st>>>(src);
+  if ((e = launch_pdl(k_ray_fwd_basis<OneSeg>, unsigned(s.B * s.ntiles), FWD_THREADS, 0, st, src)) != cudaSuccess)
+    return e;
   if ((e = hooks->after(GL_K_RAY_FWD, st)) != cudaSuccess) return e;
   Seg c = s;
   c.B = 2 * s.B;   // the convolution takes the two images of every vector as vectors of their own
@@ -1640,10 +1733,11 @@ cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size
   cudaError_t e;
   DevTable src{d_hdr, d_segs, 0};
   hooks->before(GL_K_SETUP, st);
-  k_setup<DevTable><<<sms * 2, 256, 0, st>>>(src);
+  if ((e = launch_pdl(k_setup<DevTable>, unsigned(sms * 2), 256, 0, st, src)) != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_SETUP, st)) != cudaSuccess) return e;
   hooks->before(GL_K_RAY_FWD, st);
-  k_ray_fwd<DevTable><<<sms * GL_FWD_MINB, FWD_THREADS, 0, st>>>(src);
+  if ((e = launch_pdl(k_ray_fwd<DevTable>, unsigned(sms * GL_FWD_MINB), FWD_THREADS, 0, st, src)) != cudaSuccess)
+    return e;
   if ((e = hooks->after(GL_K_RAY_FWD, st)) != cudaSuccess) return e;
   for (int c = 0; c < N_CONV_CLASSES; ++c) {
     DevTable cs{d_hdr, d_segs, c};
@@ -1653,10 +1747,11 @@ cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size
     if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   }
   hooks->before(GL_K_RAY_ADJ, st);
-  k_ray_adj<DevTable><<<sms * GL_ADJ_MINB, ADJ_THREADS, 0, st>>>(src);
+  if ((e = launch_pdl(k_ray_adj<DevTable>, unsigned(sms * GL_ADJ_MINB), ADJ_THREADS, 0, st, src)) != cudaSuccess)
+    return e;
   if ((e = hooks->after(GL_K_RAY_ADJ, st)) != cudaSuccess) return e;
   hooks->before(GL_K_FINAL, st);
-  k_final_warp<DevTable><<<sms * 4, FINAL_THREADS, 0, st>>>(src);
+  if ((e = launch_pdl(k_final_warp<DevTable>, unsigned(sms * 4), FINAL_THREADS, 0, st, src)) != cudaSuccess) return e;
   return hooks->after(GL_K_FINAL, st);
 }
 

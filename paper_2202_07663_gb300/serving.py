@@ -68,9 +68,16 @@ class Scheduler:
             raise ValueError("request %d needs %d bytes, more than the whole budget" % (job.index, job.bytes))
         self.waiting.append(job)
 
-    def admit(self, now: float) -> List[Job]:
+    def admit(self, now: float, max_ready: Optional[int] = None) -> List[Job]:
+        """Admit waiting jobs FIFO while the budget allows and, with max_ready,
+        while fewer than max_ready admitted jobs still have vectors to schedule
+        (uploading a system blocks the host, so it is done as the batches need
+        it, while the GPU works on the batches already queued)."""
         out = []
-        while self.waiting and self.used + self.waiting[0].bytes <= self.budget:
+        ready = sum(1 for j in self.active if j.remaining > 0)
+        while self.waiting and self.used + self.waiting[0].bytes <= self.budget and (
+                max_ready is None or ready < max_ready):
+            ready += 1
             j = self.waiting.popleft()
             j.admitted_s = now
             self.used += j.bytes
@@ -218,7 +225,7 @@ class LensServer:
                 r = pending.popleft()
                 resident = 4 * (2 * r.spec.H * r.spec.W + r.spec.K * r.spec.K)
                 sched.arrive(Job(r.index, r.arrival_s if realtime else 0.0, r.params.shape[0], resident))
-            for j in sched.admit(now):
+            for j in sched.admit(now, max_ready=2 * self.max_segments):
                 r = by_index[j.index]
                 with torch.cuda.stream(self.upload):
                     sysm = abi.GLSystem(r.image, r.psf, r.spec.pixel_scale, r.spec.k, r.spec.gain_exposure,

@@ -74,3 +74,21 @@ def test_arena_limit_halves_a_chunk():
     s.admit(0.0)
     segs = s.next_batch()
     assert segs[0][2] == 32 and seg_bytes(None, 32) <= 40_000
+
+
+def test_admission_limited_to_what_the_next_batches_need():
+    """With max_ready, no more than that many admitted jobs wait with vectors
+    still to schedule; a job whose vectors are all scheduled frees its slot
+    (its budget stays held until it completes)."""
+    s = Scheduler(budget_bytes=10 ** 12, arena_bytes=10 ** 9, max_segments=2, chunk=1000, segment_bytes=seg_bytes)
+    for i in range(6):
+        s.arrive(Job(i, 0.0, 50, 1000))
+    assert [j.index for j in s.admit(0.0, max_ready=3)] == [0, 1, 2]
+    assert [j.index for j in s.admit(0.0, max_ready=3)] == []
+    segs = s.next_batch()                   # jobs 0 and 1, all their vectors
+    assert [j.index for j, _, _ in segs] == [0, 1] and all(c == 50 for _, _, c in segs)
+    assert [j.index for j in s.admit(0.0, max_ready=3)] == [3, 4]
+    assert [j.index for j in s.waiting] == [5]
+    used = s.used
+    s.complete(segs[0][0], 1.0)
+    assert s.used == used - segs[0][0].bytes
