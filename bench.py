@@ -468,6 +468,9 @@ def run_serving_workload(device, n_latency: int = 200, n_capacity: int = 1000):
     stream = inputs.serving_stream(n=n_capacity)
     reqs = serving.make_requests(stream, device)
     srv = serving.LensServer(budget_bytes=16 << 30, arena_bytes=4 << 30, max_segments=64, chunk=2048)
+    # warm-up of both forms (first launches of each kernel variant load its code)
+    srv.serve(reqs[:40], realtime=False)
+    serving.serve_one_call_per_lens(reqs[:40], realtime=False)
     lat, _ = srv.serve(reqs[:n_latency], realtime=True)
     cap, _ = srv.serve(reqs, realtime=False)
     srv.close()

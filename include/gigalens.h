@@ -241,7 +241,10 @@ int gl_loglik_grad_noalloc(gl_system* sys, const float* params, int B, double* l
  *   work is asynchronous on stream. Runs of one batcher share its arena and
  *   device table, so they execute one after another: a run issued on another
  *   stream than the previous run's first waits (on the device) for that run
- *   to finish. Make the calls from one host thread at a time. The call blocks
+ *   to finish. Make the calls from one host thread at a time. A batch of one
+ *   non-empty segment runs the launch sequence of a single-system call
+ *   (gl_loglik_grad's, with its share of the arena as scratch) instead of the
+ *   graph, so its results are those of gl_loglik_grad, bit for bit. The call blocks
  *   only if the staging buffer it reuses is still being copied (two batches
  *   back). Errors: GL_ERR_BUDGET if the segments' scratch exceeds the arena,
  *   GL_ERR_UNSUPPORTED for a segment beyond max_H/max_W/max_K.

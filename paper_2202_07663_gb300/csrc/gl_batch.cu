@@ -198,6 +198,26 @@ int gl_batcher_run(gl_batcher* b, gl_system* const* systems, const float* const*
     by_class[c].push_back(g);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int nonempty = 0;
+  for (int c = 0; c < gl::N_CONV_CLASSES; ++c) nonempty += int(by_class[c].size());
+  if (nonempty == 1) {
+    // One segment (the common case of a lightly loaded server): the launch
+    // sequence of a single-system call, tuned for its batch size (tile plan,
+    // adjoint blocks per SM, small-batch convolution), on its share of the
+    // arena; no table, no graph.
+    gl::Seg g;
+    for (int c = 0; c < gl::N_CONV_CLASSES; ++c)
+      if (!by_class[c].empty()) g = by_class[c][0];
+    g.conv_two_buf = gl::conv_two_buf(g.H, g.W, g.K) ? 1 : 0;
+    if (b->ran && st != b->last_stream && (e = cudaStreamWaitEvent(st, b->done, 0)) != cudaSuccess)
+      return gl_internal::cuda_error(e, "wait for the previous run");
+    if ((e = gl::launch_one(g, gl::MODE_GRAD, st, gl_internal::hooks())) != cudaSuccess)
+      return gl_internal::cuda_error(e, "kernel launch");
+    if ((e = cudaEventRecord(b->done, st)) != cudaSuccess) return gl_internal::cuda_error(e, "run event");
+    b->last_stream = st;
+    b->ran = true;
+    return GL_OK;
+  }
   // stage the table (wait until the previous copy out of this staging buffer has run)
   const int s = b->slot;
   b->slot ^= 1;

@@ -1718,6 +1718,7 @@ static cudaError_t set_devtable_attr(size_t smem) {
 
 cudaError_t prepare_devtable(const size_t* conv_smem) {
   cudaError_t e;
+  (void)fwd_blocks_per_sm();   // the occupancy query before any capture
   e = conv_smem[0] > CONV_WIDE_MIN_SMEM ? set_devtable_attr<11, 16, 512, 1>(conv_smem[0])
                                         : set_devtable_attr<11, 16, 256, 3>(conv_smem[0]);
   if (e != cudaSuccess) return e;
@@ -1736,7 +1737,8 @@ cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size
   if ((e = launch_pdl(k_setup<DevTable>, unsigned(sms * 2), 256, 0, st, src)) != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_SETUP, st)) != cudaSuccess) return e;
   hooks->before(GL_K_RAY_FWD, st);
-  if ((e = launch_pdl(k_ray_fwd<DevTable>, unsigned(sms * GL_FWD_MINB), FWD_THREADS, 0, st, src)) != cudaSuccess)
+  if ((e = launch_pdl(k_ray_fwd<DevTable>, unsigned(sms * fwd_blocks_per_sm()), FWD_THREADS, 0, st, src)) !=
+      cudaSuccess)
     return e;
   if ((e = hooks->after(GL_K_RAY_FWD, st)) != cudaSuccess) return e;
   for (int c = 0; c < N_CONV_CLASSES; ++c) {

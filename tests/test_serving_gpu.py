@@ -65,6 +65,32 @@ def test_batcher_matches_single_calls(mods):
     small.close()
 
 
+def test_single_segment_batch_is_the_single_call(mods):
+    """A batch of one segment takes the launch sequence of a single-system
+    call (on the batcher's arena): the same bits as gl_loglik_grad, twice in
+    a row, and on a second stream after the first."""
+    abi, serving = mods
+    dev = torch.device("cuda")
+    reqs = serving.make_requests([inputs.LensRequest(0, 0.0, inputs.SystemSpec(80, 80, 2, 11), 50, 901),
+                                  inputs.LensRequest(1, 0.0, inputs.SystemSpec(100, 100, 4, 21), 300, 902)], dev)
+    b = abi.Batcher(8, 256 << 20, 128, 128, 21)
+    other = torch.cuda.Stream()
+    for r in reqs:
+        s = abi.GLSystem(r.image, r.psf, r.spec.pixel_scale, r.spec.k, r.spec.gain_exposure, sigma_bkg=r.spec.sigma_bkg)
+        p = torch.from_numpy(r.params).to(dev)
+        rl, rg = [t.cpu().numpy() for t in s.loglik_grad(p)]
+        for stream in (None, None, other.cuda_stream):
+            ll = torch.full((p.shape[0],), float("nan"), dtype=torch.float64, device=dev)
+            g = torch.full((p.shape[0], 22), float("nan"), dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            b.run([s], [p.data_ptr()], [p.shape[0]], [ll.data_ptr()], [g.data_ptr()], stream=stream)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(ll.cpu().numpy(), rl)
+            np.testing.assert_array_equal(g.cpu().numpy(), rg)
+        s.close()
+    b.close()
+
+
 def test_each_result_is_the_same_alone_and_in_the_mix(mods):
     abi, serving = mods
     dev = torch.device("cuda")
