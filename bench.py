@@ -9,7 +9,7 @@ likelihood + pixel adjoint, recomputed-ray adjoint, gradient reduction.
 Prints ONE JSON line (rank 0). Keys beyond the metric:
   e2e          same metric through the host-buffer C-ABI entry point
                (pinned params in, log L + gradient out, copies timed)
-  roofline     dominant kernel (k_ray_adj) against the FP32 ALU peak
+  roofline     dominant kernel (k_ray_adj) against the measured FP32 peak
   cpu_baseline the FP64 oracle on the host cores, bounded sample
   clocks       nvidia-smi SM clocks and throttle reasons during the timed region
   gpu_launches kernels this library launched in the timed region
@@ -50,6 +50,7 @@ def flops_ray_adj(N):
     return 331 + 14 * N
 
 
+
 def flops_conv_pixel(K, grad):
     return (4 if grad else 2) * K * K + 25
 
@@ -82,7 +83,7 @@ def series_terms(params: np.ndarray, adjoint: bool) -> np.ndarray:
     return first.astype(np.int64)
 
 
-MUFU_RAY_ADJ = 12   # ex2/lg2/rcp per ray in the adjoint (EPL power, two Sersic profiles)
+MUFU_RAY_ADJ = 13   # ex2/lg2/rcp per ray in the adjoint: EPL 5 (lg2, ex2, three rcp), each Sersic profile 4
 # DRAM bytes per launch of k_ray_adj from one ncu capture, keyed by workload
 # and the kernel source it was taken on (sha256 prefix of gl_kernels.cu +
 # gl_device.cuh); any other source reports null traffic until it is captured again.
