@@ -110,6 +110,34 @@ int gl_system_create_obsvar(gl_system** out, const float* image, const float* no
                             int H, int W, const float* psf, int K, double pixel_scale, int supersample,
                             double gain_exposure, void* stream);
 
+/*
+ * gl_psf_factor - the PSF as a sum of separable terms (host only; touches no
+ *   device). The convolution of Eq. 4's model (and its adjoint) with a PSF
+ *   P = sum_{r<R} u_r v_r^T is R pairs of 1-D passes, 2 K R multiply-adds per
+ *   pixel instead of K^2. gl_system_create applies this to its PSF and, when
+ *   R > 0, the PSF side is 11 or 21 and the separable buffers
+ *   (2 (H + K - 1) + H) * P * 4 bytes (P as below) fit 200 KiB, keeps the
+ *   factors and convolves that way (gl_system_psf_rank); a sampled Gaussian
+ *   PSF has R = 1. The 2-D convolution of the oracle is the reference for
+ *   both forms.
+ *  psf    [K][K] row-major floats (the PSF as the system stores it).
+ *  K      odd side, 1..255.
+ *  fac    NULL, or room for fac_len floats: on return [R][2][K], the row
+ *         factor sigma_r u_r then the column factor v_r of term r, from a
+ *         singular value decomposition in FP64 (one-sided Jacobi).
+ *  rank   out: R, the fewest terms whose dropped singular values have a root
+ *         sum of squares of at most 2^-24 ||P||_F (the rounding the FP32
+ *         entries already carry), or 0 when 4 R > K (the 2-D convolution is
+ *         kept).
+ * Errors: GL_ERR_INVALID_ARG for null psf/rank, a bad K, a non-finite value,
+ * or fac_len < 2 R K with fac non-NULL.
+ */
+int gl_psf_factor(const float* psf, int K, float* fac, int fac_len, int* rank);
+
+/* The number of separable PSF terms the system convolves with (0: the
+ * K x K stencil), or GL_ERR_INVALID_ARG for NULL. Host state only. */
+int gl_system_psf_rank(const gl_system* sys);
+
 /* Free the system, its resident data and its scratch. Synchronises the
  * device first. NULL is accepted. */
 int gl_system_destroy(gl_system* sys);
@@ -121,7 +149,8 @@ int gl_system_reserve(gl_system* sys, int B);
 /* Device bytes the system's scratch needs for a batch of B vectors. */
 size_t gl_system_scratch_bytes(const gl_system* sys, int B);
 
-/* Device bytes held by the resident data (image, variance, PSF). */
+/* Device bytes held by the resident data (image, variance, PSF and its
+ * separable terms). */
 size_t gl_system_resident_bytes(const gl_system* sys);
 
 /* Device bytes of scratch (per-vector constants, image work buffer, tile
@@ -204,8 +233,8 @@ int gl_loglik_grad_grouped(gl_system* const* systems, const float* const* params
  * 32 MiB (33,554,432 bytes), which every GPU that loads
  * the library holds until the process exits. A batch whose scratch does not
  * fit is rejected with GL_ERR_INVALID_ARG before anything is launched (about
- * 2,000 vectors of a 60 x 60 image; scratch per vector is roughly
- * 4*H*W + 800 bytes).
+ * 2,100 vectors of a 60 x 60 image; scratch per vector is 4*H*W + 1,232
+ * bytes plus 192 bytes per ray tile, gl_system_scratch_bytes(sys, B) / B).
  *
  * Every call looks up the array's device address (cudaGetSymbolAddress)
  * with the system's device current; the lookup allocates nothing. The first

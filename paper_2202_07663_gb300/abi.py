@@ -81,6 +81,8 @@ SIGNATURES = {
     "gl_kernel_name": ([_i], ctypes.c_char_p),
     "gl_launch_count": ([], ctypes.c_longlong),
     "gl_profile_peak": ([_i, _vp], _i),
+    "gl_psf_factor": ([_vp, _i, _vp, _i, _vp], _i),
+    "gl_system_psf_rank": ([_vp], _i),
 }
 
 
@@ -240,6 +242,22 @@ def gl_launch_count() -> int:
 GL_PEAK_FP32_FMA, GL_PEAK_MUFU_EX2 = 0, 1
 
 
+def psf_factor(psf):
+    """The PSF's separable terms as gl_system_create uses them: (R, fac) with
+    fac [R, 2, K] (row factor sigma_r u_r, column factor v_r); R = 0 when
+    the 2-D convolution is kept."""
+    p = np.ascontiguousarray(psf, dtype=np.float32)
+    K = p.shape[0]
+    if p.shape != (K, K):
+        raise ValueError("psf must be square")
+    fac = np.zeros(2 * K * K, np.float32)
+    r = ctypes.c_int()
+    _check(lib_handle().gl_psf_factor(p.ctypes.data, K, fac.ctypes.data, fac.size, ctypes.addressof(r)),
+           "gl_psf_factor")
+    R = int(r.value)
+    return R, fac[:2 * R * K].reshape(R, 2, K).copy()
+
+
 def gl_profile_peak(kind: int) -> float:
     """Measured rate of a pipe of the current device: FP32 flop/s
     (GL_PEAK_FP32_FMA) or ex2 results/s (GL_PEAK_MUFU_EX2)."""
@@ -293,6 +311,13 @@ class GLSystem:
 
     def resident_bytes(self) -> int:
         return int(lib_handle().gl_system_resident_bytes(self._h))
+
+    def psf_rank(self) -> int:
+        """Separable PSF terms the convolution uses (0: the 2-D stencil)."""
+        r = int(lib_handle().gl_system_psf_rank(self._h))
+        if r < 0:
+            _check(r, "gl_system_psf_rank")
+        return r
 
     def scratch_held(self) -> int:
         """Device bytes of scratch the system holds now (0 until a call needs some)."""

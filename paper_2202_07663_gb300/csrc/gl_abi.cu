@@ -2,6 +2,7 @@
 // contract of every entry point are in include/gigalens.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -24,6 +25,9 @@ struct gl_system {
   float* d_image = nullptr;
   float* d_sigma2 = nullptr;
   float* d_psf = nullptr;
+  // the PSF as psf_rank separable terms (0: convolve with the K x K PSF directly)
+  int psf_rank = 0;
+  float* d_psf_sep = nullptr;   // [psf_rank][2][K]: sigma_r u_r (rows), v_r (columns)
   // scratch, grown on demand
   long long cap_B = 0;
   long long cap_partial = 0;   // doubles
@@ -133,6 +137,83 @@ int max_smem_optin(int dev) {
   return v;
 }
 
+// The PSF P (K x K, row-major, FP64 values of the floats the device uses) as
+// a sum of separable terms P = sum_r sigma_r u_r v_r^T, from its singular
+// value decomposition by one-sided Jacobi rotations (Hestenes 1958): the
+// columns of A = P are rotated pairwise until orthogonal, A V = U Sigma.
+// The rank kept is the smallest whose dropped singular values have a root
+// sum of squares of at most 2^-24 ||P||_F: no more than the rounding that
+// the PSF's FP32 values already carry (half an ulp, 2^-24 relative, in every
+// entry), so that a PSF which is separable before rounding stays so. The
+// factors are used only if 2 R K <= K^2 / 2 (then two 1-D passes per term
+// are at least twice as cheap as the 2-D pass). Returns R (0: keep the
+// 2-D convolution) and fac = [R][2][K] as floats: sigma_r u_r, then v_r.
+int psf_separable(const std::vector<float>& psf, int K, std::vector<float>& fac) {
+  const int n = K;
+  std::vector<double> A(size_t(n) * n), V(size_t(n) * n, 0.0);
+  for (int i = 0; i < n * n; ++i) A[i] = psf[i];
+  for (int i = 0; i < n; ++i) V[size_t(i) * n + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double alpha = 0.0, beta = 0.0, gamma = 0.0;
+        for (int i = 0; i < n; ++i) {
+          const double ap = A[size_t(i) * n + p], aq = A[size_t(i) * n + q];
+          alpha += ap * ap;
+          beta += aq * aq;
+          gamma += ap * aq;
+        }
+        if (gamma == 0.0 || std::fabs(gamma) <= 1e-17 * std::sqrt(alpha * beta)) continue;
+        off = std::fmax(off, std::fabs(gamma) / std::sqrt(alpha * beta));
+        const double zeta = (beta - alpha) / (2.0 * gamma);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+        for (int i = 0; i < n; ++i) {
+          double& ap = A[size_t(i) * n + p];
+          double& aq = A[size_t(i) * n + q];
+          const double x = ap, y = aq;
+          ap = c * x - sn * y;
+          aq = sn * x + c * y;
+          double& vp = V[size_t(i) * n + p];
+          double& vq = V[size_t(i) * n + q];
+          const double vx = vp, vy = vq;
+          vp = c * vx - sn * vy;
+          vq = sn * vx + c * vy;
+        }
+      }
+    if (off < 1e-15) break;
+  }
+  std::vector<std::pair<double, int>> sv(n);
+  double total = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s2 = 0.0;
+    for (int i = 0; i < n; ++i) s2 += A[size_t(i) * n + j] * A[size_t(i) * n + j];
+    sv[j] = {std::sqrt(s2), j};
+    total += s2;
+  }
+  std::sort(sv.begin(), sv.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+    return a.first > b.first;
+  });
+  int R = n;
+  double tail = 0.0;   // sum of the squares of the dropped singular values
+  const double tol2 = 0x1p-48;   // (2^-24)^2
+  while (R > 1 && tail + sv[R - 1].first * sv[R - 1].first <= tol2 * total) {
+    tail += sv[R - 1].first * sv[R - 1].first;
+    --R;
+  }
+  if (!(total > 0.0) || 4 * R > K) return 0;
+  fac.assign(size_t(R) * 2 * n, 0.f);
+  for (int r = 0; r < R; ++r) {
+    const int j = sv[r].second;
+    for (int i = 0; i < n; ++i) {
+      fac[(size_t(r) * 2) * n + i] = float(A[size_t(i) * n + j]);         // sigma_r u_r (column j of A V)
+      fac[(size_t(r) * 2 + 1) * n + i] = float(V[size_t(i) * n + j]);     // v_r (column j of V)
+    }
+  }
+  return R;
+}
+
 // Static shared memory of the convolution kernel besides the image (Seg + reductions), with margin.
 constexpr size_t CONV_STATIC_SMEM = 2048;
 
@@ -168,6 +249,8 @@ Seg make_seg(const gl_system* s, const float* params, int B) {
   g.image = s->d_image;
   g.sigma2 = s->d_sigma2;
   g.psf = s->d_psf;
+  g.psf_sep = s->d_psf_sep;
+  g.psf_rank = s->psf_rank;
   g.H = s->H;
   g.W = s->W;
   g.K = s->K;
@@ -186,6 +269,7 @@ Seg make_seg(const gl_system* s, const float* params, int B) {
   g.work = s->d_work;
   g.partial = s->d_partial;
   g.conv_two_buf = gl::conv_two_buf(s->H, s->W, s->K) ? 1 : 0;
+  g.conv_sep = gl::conv_sep_ok(s->H, s->W, s->K, s->psf_rank) ? 1 : 0;
   return g;
 }
 
@@ -296,6 +380,17 @@ int create_impl(gl_system** out, const float* image, const std::vector<float>& s
     gl_system_destroy(s);
     return cuda_fail(e, "gl_system_create upload");
   }
+  std::vector<float> fac;
+  const int R = psf_separable(psf_area, K, fac);
+  if (R > 0 && gl::conv_sep_ok(H, W, K, R)) {   // factors kept only where the 1-D passes run
+    if ((e = cudaMalloc(&s->d_psf_sep, fac.size() * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemcpy(s->d_psf_sep, fac.data(), fac.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+            cudaSuccess) {
+      gl_system_destroy(s);
+      return cuda_fail(e, "gl_system_create upload (PSF factors)");
+    }
+    s->psf_rank = R;
+  }
   *out = s;
   return GL_OK;
 }
@@ -371,6 +466,7 @@ int gl_system_destroy(gl_system* s) {
   cudaFree(s->d_image);
   cudaFree(s->d_sigma2);
   cudaFree(s->d_psf);
+  cudaFree(s->d_psf_sep);
   cudaFree(s->d_vc);
   cudaFree(s->d_work);
   cudaFree(s->d_partial);
@@ -399,7 +495,27 @@ size_t gl_system_scratch_held(const gl_system* s) { return s ? gl_internal::scra
 
 size_t gl_system_resident_bytes(const gl_system* s) {
   if (!s) return 0;
-  return sizeof(float) * (2 * size_t(s->H) * s->W + size_t(s->K) * s->K);
+  return sizeof(float) * (2 * size_t(s->H) * s->W + size_t(s->K) * s->K + 2 * size_t(s->psf_rank) * s->K);
+}
+
+int gl_system_psf_rank(const gl_system* s) {
+  if (!s) return fail(GL_ERR_INVALID_ARG, "null gl_system");
+  return s->psf_rank;
+}
+
+int gl_psf_factor(const float* psf, int K, float* fac, int fac_len, int* rank) {
+  if (!psf || !rank) return fail(GL_ERR_INVALID_ARG, "null psf or rank");
+  if (K < 1 || K % 2 == 0 || K > 255) return fail(GL_ERR_INVALID_ARG, "K = %d (odd, 1..255)", K);
+  std::vector<float> p(psf, psf + size_t(K) * K), f;
+  for (float v : p)
+    if (!std::isfinite(v)) return fail(GL_ERR_INVALID_ARG, "non-finite PSF value");
+  const int R = psf_separable(p, K, f);
+  if (fac && R > 0) {
+    if (fac_len < 2 * R * K) return fail(GL_ERR_INVALID_ARG, "fac holds %d floats, %d needed", fac_len, 2 * R * K);
+    std::copy(f.begin(), f.end(), fac);
+  }
+  *rank = R;
+  return GL_OK;
 }
 
 int gl_system_reserve(gl_system* s, int B) {
@@ -579,7 +695,7 @@ int gl_loglik_grad_grouped(gl_system* const* systems, const float* const* params
       vec_total += sg.B;
       ray_total += sg.B * sg.ntiles;
       r.nitems += sg.B;
-      const size_t sm = gl::conv_smem_bytes(sg.H, sg.W, sg.K, sg.conv_two_buf != 0);
+      const size_t sm = gl::seg_conv_smem(sg);
       r.smem = sm > r.smem ? sm : r.smem;
       segs.push_back(sg);
     }

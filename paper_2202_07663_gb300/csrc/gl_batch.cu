@@ -177,8 +177,9 @@ int gl_batcher_run(gl_batcher* b, gl_system* const* systems, const float* const*
     if (g.H > b->max_H || g.W > b->max_W || g.K > b->max_K)
       return gl_internal::set_error(GL_ERR_UNSUPPORTED, "segment image or PSF larger than the batcher was built for");
     const int c = gl::conv_class(g.K);
+    if (g.conv_sep && gl::seg_conv_smem(g) > b->conv_smem[c]) g.conv_sep = 0;
     if (g.conv_two_buf && gl::conv_smem_bytes(g.H, g.W, g.K, true) > b->conv_smem[c]) g.conv_two_buf = 0;
-    if (gl::conv_smem_bytes(g.H, g.W, g.K, g.conv_two_buf != 0) > b->conv_smem[c])
+    if (gl::seg_conv_smem(g) > b->conv_smem[c])
       return gl_internal::set_error(GL_ERR_UNSUPPORTED, "segment convolution does not fit the captured shared memory");
     const size_t need = segment_scratch(g);
     if (used + need > b->arena_bytes) {
@@ -209,6 +210,7 @@ int gl_batcher_run(gl_batcher* b, gl_system* const* systems, const float* const*
     for (int c = 0; c < gl::N_CONV_CLASSES; ++c)
       if (!by_class[c].empty()) g = by_class[c][0];
     g.conv_two_buf = gl::conv_two_buf(g.H, g.W, g.K) ? 1 : 0;
+    g.conv_sep = gl::conv_sep_ok(g.H, g.W, g.K, g.psf_rank) ? 1 : 0;
     if (b->ran && st != b->last_stream && (e = cudaStreamWaitEvent(st, b->done, 0)) != cudaSuccess)
       return gl_internal::cuda_error(e, "wait for the previous run");
     if ((e = gl::launch_one(g, gl::MODE_GRAD, st, gl_internal::hooks())) != cudaSuccess)

@@ -105,6 +105,9 @@ struct Seg {
   const float* image;      // I_obs [H, W]
   const float* sigma2;     // sigma_bkg^2 [H, W]
   const float* psf;        // [K, K]
+  const float* psf_sep;    // [psf_rank][2][K]: the PSF as separable terms (sigma_r u_r, v_r), or null
+  int psf_rank;            // separable terms of the PSF (0: 2-D convolution only)
+  int conv_sep;            // 1: this launch convolves with the separable terms (its shared memory has room)
   int H, W, K, k;
   float hh, hl;            // h = pixel_scale / (2k) = hh + hl (a pair of floats)
   int nx0, ny0;            // 1 - kW, 1 - kH: subpixel (i, j) sits at ((2j + nx0) h, (2i + ny0) h)

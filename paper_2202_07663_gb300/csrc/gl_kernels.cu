@@ -261,6 +261,9 @@ __device__ __forceinline__ void series_coeffs(int lane, float t, VecConst* V) {
   }
 }
 
+// Block size of k_setup: eight warps, one vector each per step.
+constexpr int SETUP_THREADS = 8 * 32;
+
 // A block takes its vectors wpb (warps per block) at a time. First the FP64
 // constants: thread 3 v + part of the block forms part `part` of vector v
 // of the chunk (setup_fp64_part), so that one warp's FP64 instructions serve
@@ -272,7 +275,7 @@ __device__ __forceinline__ void series_coeffs(int lane, float t, VecConst* V) {
 template <class Src>
 __global__ void k_setup(const __grid_constant__ Src src) {
   const PdlScope pdl;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int nvec = src.nvec();
   for (int base = blockIdx.x * wpb; base < nvec; base += gridDim.x * wpb) {
@@ -280,7 +283,7 @@ __global__ void k_setup(const __grid_constant__ Src src) {
       const int item = base + threadIdx.x / 3;
       if (item < nvec) setup_fp64_part(src, item, threadIdx.x % 3);
     }
-    const int item = base + (threadIdx.x >> 5);
+    const int item = base + warp;
     if (item >= nvec) continue;   // warp-uniform
     int b;
     const Seg* s = src.vec_seg(item, b);
@@ -969,6 +972,84 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// The binned image (the vector's work slot) into the interior of the
+// zero-padded buffer img ([H + K - 1][P], halo (K - 1)/2), by asynchronous
+// copies while the halo is zeroed; rows across warps, columns across lanes.
+// The caller synchronises the block after.
+template <int K>
+__device__ __forceinline__ void load_padded(const Seg& s, float* img, int P, const float* work) {
+  constexpr int c = (K - 1) / 2;
+  const int H = s.H, W = s.W;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < H; i += nw)
+    for (int j = lane; j < W; j += 32) cp_async4(&img[(i + c) * P + j + c], &work[i * W + j]);
+  for (int i = threadIdx.x; i < c * P; i += blockDim.x) {
+    img[i] = 0.f;                       // top halo rows
+    img[(H + c) * P + i] = 0.f;         // bottom halo rows
+  }
+  const int side = P - W;               // left halo c columns + right halo and pitch padding
+  for (int t = threadIdx.x; t < H * side; t += blockDim.x) {
+    const int i = t / side, q = t - i * side;
+    img[(i + c) * P + (q < c ? q : W + q)] = 0.f;
+  }
+  cp_async_wait_all();
+}
+
+// log L and chi^2 of the block's vector from the threads' partial sums (FP32
+// within a warp, pairwise; FP64 across warps in warp order), and a block
+// barrier: every thread calls it.
+__device__ __forceinline__ void block_loglik(const Seg& s, int b, float ll, float c2, double* red2) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  ll = warp_sum_f(ll);
+  c2 = warp_sum_f(c2);
+  if (lane == 0) {
+    red2[2 * wid] = double(ll);
+    red2[2 * wid + 1] = double(c2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double L = 0.0, C = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      L += red2[2 * w];
+      C += red2[2 * w + 1];
+    }
+    if (s.loglik) s.loglik[b] = -0.5 * L;
+    if (s.chi2) s.chi2[b] = C;
+  }
+}
+
+// Pixel phase after the model pass (coalesced: rows across warps, columns
+// across lanes): the model value of pixel (i, j) from stage (pitch P) if two,
+// else from the work slot. With want_sim it goes to s.sim; otherwise the
+// likelihood terms are summed (FP32 within a thread and a warp, pairwise;
+// FP64 across warps: the block size sets the summation order, the last bits
+// of log L) into s.loglik / s.chi2, and with want_grad d log L / d M goes
+// into img's interior (halo c). Returns whether a correlation pass follows.
+__device__ bool pixel_phase(const Seg& s, int b, bool want_sim, bool want_grad, const float* stage, int P, float* img,
+                            int c, bool two, double* red2) {
+  const int H = s.H, W = s.W, HW = H * W;
+  const float* work = s.work + size_t(b) * HW;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float ll = 0.f, c2 = 0.f;
+  for (int i = wid; i < H; i += nw)
+#pragma unroll 2
+  for (int j = lane; j < W; j += 32) {
+    const int p = i * W + j;
+    const float M = two ? stage[i * P + j] : work[p];
+    if (want_sim) {
+      s.sim[size_t(b) * HW + p] = M;
+      continue;
+    }
+    const float gm = pixel_terms(s, p, M, ll, c2);
+    if (want_grad) img[(i + c) * P + j + c] = gm;
+  }
+  if (!want_sim)
+    block_loglik(s, b, ll, c2, red2);
+  else
+    __syncthreads();
+  return want_grad;
+}
+
 // One vector, PSF side K known at compile time. Shared memory: both PSF
 // orientations ([K][KP], zero padded), the zero-padded input buffer
 // [H + K - 1][P] and, when s.conv_two_buf, an unpadded staging buffer [H][P]
@@ -998,19 +1079,7 @@ __device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, dou
   }
   // pixel loops: rows across warps, columns across lanes (coalesced, no division)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // the binned image into the interior (asynchronous copies) while the halo is zeroed
-  for (int i = wid; i < H; i += nw)
-    for (int j = lane; j < W; j += 32) cp_async4(&img[(i + c) * P + j + c], &work[i * W + j]);
-  for (int i = threadIdx.x; i < c * P; i += blockDim.x) {
-    img[i] = 0.f;                       // top halo rows
-    img[(H + c) * P + i] = 0.f;         // bottom halo rows
-  }
-  const int side = P - W;               // left halo c columns + right halo and pitch padding
-  for (int t = threadIdx.x; t < H * side; t += blockDim.x) {
-    const int i = t / side, q = t - i * side;
-    img[(i + c) * P + (q < c ? q : W + q)] = 0.f;
-  }
-  cp_async_wait_all();
+  load_padded<K>(s, img, P, work);
   __syncthreads();
 
   const int nstrip = (W + S - 1) / S;
@@ -1033,41 +1102,7 @@ __device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, dou
   }
   __syncthreads();
 
-  // pixel phase (coalesced): likelihood terms and d log L / d M into img's interior
-  float ll = 0.f, c2 = 0.f;
-  for (int i = wid; i < H; i += nw)
-#pragma unroll 2
-  for (int j = lane; j < W; j += 32) {
-    const int p = i * W + j;
-    const float M = two ? stage[i * P + j] : work[p];
-    if (want_sim) {
-      s.sim[size_t(b) * HW + p] = M;
-      continue;
-    }
-    const float gm = pixel_terms(s, p, M, ll, c2);
-    if (want_grad) img[(i + c) * P + j + c] = gm;
-  }
-  if (!want_sim) {
-    // FP32 within a thread (a few tens of pixels) and a warp (pairwise), FP64 across
-    // warps: the block size sets the summation order (the last bits of log L)
-    ll = warp_sum_f(ll);
-    c2 = warp_sum_f(c2);
-    if (lane == 0) {
-      red2[2 * wid] = double(ll);
-      red2[2 * wid + 1] = double(c2);
-    }
-  }
-  __syncthreads();
-  if (!want_sim && threadIdx.x == 0) {
-    double L = 0.0, C = 0.0;
-    for (int w = 0; w < nw; ++w) {
-      L += red2[2 * w];
-      C += red2[2 * w + 1];
-    }
-    if (s.loglik) s.loglik[b] = -0.5 * L;
-    if (s.chi2) s.chi2[b] = C;
-  }
-  if (!want_grad) return;
+  if (!pixel_phase(s, b, want_sim, want_grad, stage, P, img, c, two, red2)) return;
   }   // !corr_only
 
   // pass 2: subpixel adjoint = (PSF correlated with d log L / d M) / k^2
@@ -1094,6 +1129,146 @@ __device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, dou
   }
 }
 
+// ---- separable PSFs: the convolution as 1-D passes ----
+//
+// A PSF whose singular values beyond the first R are negligible (psf_rank,
+// from gl_system_create: their root sum of squares is at most 2^-24 of the
+// PSF's Frobenius norm, the rounding its FP32 entries already carry) is
+// P = sum_r u_r v_r^T (u_r carries the singular value). A pass over the
+// image is then R horizontal K-tap passes (v_r, into R row buffers) and, per
+// output, the sum over r of K-tap vertical passes (u_r): 2 K R multiply-adds
+// per pixel instead of K^2 (a sampled Gaussian PSF has R = 1: 22 instead of
+// 121 at K = 11). flip: the flipped PSF (the model's convolution), else the
+// PSF (the adjoint's correlation).
+constexpr int SEP_RV = 8;   // output rows per thread in the vertical pass
+
+// Horizontal passes: tmp + r Hp P, row i, columns j0 .. j0 + 15, for every
+// padded row i (lanes take consecutive rows: float4 loads of rows an odd
+// number of 16-byte words apart are conflict-free).
+template <int K>
+__device__ __forceinline__ void sep_hpass(const float* __restrict__ in, int P, int Hp, int W, const float* fac, int R,
+                                          bool flip, float* tmp) {
+  constexpr int S = 16, NIN = (S + K - 1 + 3) & ~3;
+  const int nstrip = (W + S - 1) / S;
+  for (int r = 0; r < R; ++r) {
+    const float* v = fac + (2 * r + 1) * K;
+    float tv[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) tv[q] = v[flip ? K - 1 - q : q];
+    float* out = tmp + size_t(r) * Hp * P;
+    for (int t = threadIdx.x; t < Hp * nstrip; t += blockDim.x) {
+      const int strip = t / Hp, i = t - strip * Hp, j0 = strip * S;
+      float x[NIN];
+      const float4* r4 = reinterpret_cast<const float4*>(in + i * P + j0);
+#pragma unroll
+      for (int q = 0; q < NIN / 4; ++q) {
+        const float4 w = r4[q];
+        x[4 * q] = w.x;
+        x[4 * q + 1] = w.y;
+        x[4 * q + 2] = w.z;
+        x[4 * q + 3] = w.w;
+      }
+      float acc[S];
+#pragma unroll
+      for (int o = 0; o < S; ++o) {
+        float a = 0.f;
+#pragma unroll
+        for (int q = 0; q < K; ++q) a = fmaf(tv[q], x[o + q], a);
+        acc[o] = a;
+      }
+      float4* t4 = reinterpret_cast<float4*>(out + i * P + j0);
+#pragma unroll
+      for (int q = 0; q < S / 4; ++q) t4[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+  }
+}
+
+// Vertical passes of one unit: rows i0 .. i0 + 7 of column j, summed over
+// the R terms into m (lanes take consecutive columns).
+template <int K>
+__device__ __forceinline__ void sep_vunit(const float* tmp, int P, int Hp, const float* fac, int R, bool flip, int i0,
+                                          int j, float (&m)[SEP_RV]) {
+  constexpr int NV = SEP_RV + K - 1;
+#pragma unroll
+  for (int o = 0; o < SEP_RV; ++o) m[o] = 0.f;
+  for (int r = 0; r < R; ++r) {
+    const float* u = fac + 2 * r * K;
+    const float* col = tmp + size_t(r) * Hp * P + j;
+    float x[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) x[q] = (i0 + q < Hp) ? col[(i0 + q) * P] : 0.f;
+#pragma unroll
+    for (int o = 0; o < SEP_RV; ++o) {
+      float a = m[o];
+#pragma unroll
+      for (int q = 0; q < K; ++q) a = fmaf(u[flip ? K - 1 - q : q], x[o + q], a);
+      m[o] = a;
+    }
+  }
+}
+
+// One vector with a separable PSF (s.conv_sep). Shared memory: the factors,
+// the zero-padded input [H + K - 1][P] and R row buffers [H + K - 1][P].
+// The model pass's vertical step computes the likelihood terms of its
+// outputs at once and writes d log L / d M over the input's interior (the
+// horizontal step has read it); the correlation's vertical step writes the
+// subpixel adjoint to the vector's work slot. The arithmetic of every pixel
+// (its model value, its likelihood terms, its adjoint) is fixed by the
+// layout, not the block size; log L is summed in a block-size-dependent
+// order.
+template <int K>
+__device__ void conv_vector_sep(const Seg& s, int b, int mode, float* smem, double* red2) {
+  constexpr int c = (K - 1) / 2;
+  const int H = s.H, W = s.W, HW = H * W, R = s.psf_rank;
+  const int P = rowconv_pitch(W, K), Hp = H + K - 1;
+  const int nvu = ((H + SEP_RV - 1) / SEP_RV) * W;   // vertical units
+  float* fac = smem;
+  float* img = smem + ((2 * R * K + 3) & ~3);
+  float* tmp = img + Hp * P;
+  float* work = s.work + size_t(b) * HW;
+  const bool want_sim = (mode == MODE_SIM);
+  const bool corr_only = (mode == MODE_CORR);   // the work slot holds d log L / d M already
+  const bool want_grad = (mode == MODE_GRAD) || corr_only;
+  for (int i = threadIdx.x; i < 2 * R * K; i += blockDim.x) fac[i] = s.psf_sep[i];
+  load_padded<K>(s, img, P, work);
+  __syncthreads();
+  if (!corr_only) {
+    sep_hpass<K>(img, P, Hp, W, fac, R, true, tmp);
+    __syncthreads();
+    float ll = 0.f, c2 = 0.f;
+    for (int t = threadIdx.x; t < nvu; t += blockDim.x) {
+      const int strip = t / W, j = t - strip * W, i0 = strip * SEP_RV;
+      float m[SEP_RV];
+      sep_vunit<K>(tmp, P, Hp, fac, R, true, i0, j, m);
+#pragma unroll
+      for (int o = 0; o < SEP_RV; ++o) {
+        const int i = i0 + o;
+        if (i >= H) break;
+        if (want_sim) {
+          s.sim[size_t(b) * HW + i * W + j] = m[o];
+          continue;
+        }
+        const float gm = pixel_terms(s, i * W + j, m[o], ll, c2);
+        if (want_grad) img[(i + c) * P + j + c] = gm;
+      }
+    }
+    if (want_sim) return;
+    block_loglik(s, b, ll, c2, red2);   // also the barrier before the correlation reads img
+    if (!want_grad) return;
+  }
+  sep_hpass<K>(img, P, Hp, W, fac, R, false, tmp);
+  __syncthreads();
+  const float inv_k2 = 1.0f / float(s.k * s.k);
+  for (int t = threadIdx.x; t < nvu; t += blockDim.x) {
+    const int strip = t / W, j = t - strip * W, i0 = strip * SEP_RV;
+    float m[SEP_RV];
+    sep_vunit<K>(tmp, P, Hp, fac, R, false, i0, j, m);
+#pragma unroll
+    for (int o = 0; o < SEP_RV; ++o)
+      if (i0 + o < H) work[(i0 + o) * W + j] = m[o] * inv_k2;
+  }
+}
+
 template <int K, int R, int NT, int MINB, class Src>
 __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src src, int mode) {
   extern __shared__ float4 smem4[];
@@ -1107,10 +1282,29 @@ __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src s
     block_copy(&ss, segp);
     __syncthreads();
     if constexpr (K > 0) {
-      conv_vector_rows<K>(ss, b, mode, smem, red2);
+      // a single-system call takes k_conv_sep for a separable PSF; a table
+      // may mix both kinds of segment
+      if (!std::is_same<Src, OneSeg>::value && ss.conv_sep)
+        conv_vector_sep<K>(ss, b, mode, smem, red2);
+      else
+        conv_vector_rows<K>(ss, b, mode, smem, red2);
     } else {
       conv_vector<K, R>(ss, b, mode, smem, red2);
     }
+    __syncthreads();
+  }
+}
+
+// The separable convolution of a single-system call (its own kernel, so that
+// the 2-D form's register budget does not bound it).
+template <int K, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_conv_sep(const __grid_constant__ OneSeg src, int mode) {
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  __shared__ double red2[2 * (NT / 32)];
+  const PdlScope pdl;
+  for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x) {
+    conv_vector_sep<K>(src.s, item, mode, smem, red2);
     __syncthreads();
   }
 }
@@ -1400,6 +1594,21 @@ size_t conv_smem_bytes(int H, int W, int K, bool two_buf) {
 
 bool conv_two_buf(int H, int W, int K) { return conv_smem_bytes(H, W, K, true) <= CONV_TWO_BUF_MAX_SMEM; }
 
+size_t conv_sep_smem_bytes(int H, int W, int K, int R) {
+  const size_t P = size_t(rowconv_pitch(W, K)), Hp = size_t(H) + K - 1;
+  return (size_t((2 * R * K + 3) & ~3) + (1 + size_t(R)) * Hp * P) * sizeof(float);
+}
+
+bool conv_sep_ok(int H, int W, int K, int R) {
+  // 2 K R multiply-adds per pixel and pass against K^2, with a pass of
+  // shared-memory traffic per term: worth it at R <= K / 4
+  return R > 0 && 4 * R <= K && (K == 11 || K == 21) && conv_sep_smem_bytes(H, W, K, R) <= CONV_TWO_BUF_MAX_SMEM;
+}
+
+size_t seg_conv_smem(const Seg& g) {
+  return g.conv_sep ? conv_sep_smem_bytes(g.H, g.W, g.K, g.psf_rank) : conv_smem_bytes(g.H, g.W, g.K, g.conv_two_buf != 0);
+}
+
 // Ray tiles of at most this many rays take the three-blocks-per-SM adjoint.
 constexpr long long ADJ_SHORT_TILE_RAYS = 32768;
 
@@ -1548,6 +1757,36 @@ static cudaError_t launch_conv_class(int cls, const Src& src, int nitems, size_t
   }
 }
 
+template <int K, int NT, int MINB>
+static cudaError_t launch_conv_sep(const OneSeg& src, int nitems, size_t smem, int mode, cudaStream_t st) {
+  static size_t attr = 48 * 1024;
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (smem > attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_conv_sep<K, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(smem));
+      if (e != cudaSuccess) return e;
+      attr = smem;
+    }
+  }
+  return launch_pdl(k_conv_sep<K, NT, MINB>, unsigned(nitems), NT, smem, st, src, mode);
+}
+
+// The convolution of a single-system call over nitems vectors: the
+// separable kernel when the segment takes it, else its PSF-size class.
+static cudaError_t launch_conv_one(const OneSeg& src, int nitems, int mode, cudaStream_t st, bool wide) {
+  const Seg& s = src.s;
+  const size_t smem = seg_conv_smem(s);
+  if (s.conv_sep) {
+    if (s.K == 11)
+      return wide ? launch_conv_sep<11, 512, 1>(src, nitems, smem, mode, st)
+                  : launch_conv_sep<11, 256, 4>(src, nitems, smem, mode, st);
+    return wide ? launch_conv_sep<21, 512, 1>(src, nitems, smem, mode, st)
+                : launch_conv_sep<21, 256, 2>(src, nitems, smem, mode, st);
+  }
+  return launch_conv_class(conv_class(s.K), src, nitems, smem, mode, st, false, wide || smem > CONV_WIDE_MIN_SMEM);
+}
+
 // Row bands for the cluster convolution of a B-vector call (0: one block per
 // vector instead). Bands only below half as many vectors as SMs: up to two
 // blocks per SM, at most 8 per vector (a portable cluster), each at least
@@ -1598,7 +1837,7 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
                             bool short_tiles = false) {
   const int sms = num_sms();
   cudaError_t e;
-  const int vthreads = 256, wpb = vthreads / 32;
+  const int vthreads = SETUP_THREADS, wpb = vthreads / 32;
   int sgrid = (nvec + wpb - 1) / wpb;
   int fgrid = (nvec + FINAL_THREADS - 1) / FINAL_THREADS;
   int wgrid = (nvec + FINAL_THREADS / 32 - 1) / (FINAL_THREADS / 32);
@@ -1645,13 +1884,11 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false, mode != MODE_CORR);
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_CONV, st);
-  const size_t csmem = conv_smem_bytes(s.H, s.W, s.K, s.conv_two_buf != 0);
-  const int nb = mode == MODE_CORR ? 0 : conv_bands(s.B, s.H, s.W, s.K);
+  const int nb = (mode == MODE_CORR || s.conv_sep) ? 0 : conv_bands(s.B, s.H, s.W, s.K);
   if (nb > 0)
     e = s.K == 11 ? launch_conv_bands<11>(src, nb, mode, st) : launch_conv_bands<21>(src, nb, mode, st);
   else
-    e = launch_conv_class(conv_class(s.K), src, s.B, csmem, mode, st, false,
-                          s.B < num_sms() || csmem > CONV_WIDE_MIN_SMEM);
+    e = launch_conv_one(src, s.B, mode, st, s.B < num_sms());
   if (e != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_CONV, st)) != cudaSuccess) return e;
   if (mode != MODE_GRAD && mode != MODE_CORR) return cudaSuccess;
@@ -1674,8 +1911,7 @@ cudaError_t launch_basis(const Seg& s, cudaStream_t st, Hooks* hooks) {
   c.B = 2 * s.B;   // the convolution takes the two images of every vector as vectors of their own
   OneSeg csrc{c};
   hooks->before(GL_K_CONV, st);
-  e = launch_conv_class(conv_class(c.K), csrc, c.B, conv_smem_bytes(c.H, c.W, c.K, c.conv_two_buf != 0), MODE_SIM,
-                        st, false, c.B < num_sms());
+  e = launch_conv_one(csrc, c.B, MODE_SIM, st, c.B < num_sms());
   if (e != cudaSuccess) return e;
   return hooks->after(GL_K_CONV, st);
 }
@@ -1734,7 +1970,7 @@ cudaError_t launch_devtable(const TableHdr* d_hdr, const Seg* d_segs, const size
   cudaError_t e;
   DevTable src{d_hdr, d_segs, 0};
   hooks->before(GL_K_SETUP, st);
-  if ((e = launch_pdl(k_setup<DevTable>, unsigned(sms * 2), 256, 0, st, src)) != cudaSuccess) return e;
+  if ((e = launch_pdl(k_setup<DevTable>, unsigned(sms * 2), SETUP_THREADS, 0, st, src)) != cudaSuccess) return e;
   if ((e = hooks->after(GL_K_SETUP, st)) != cudaSuccess) return e;
   hooks->before(GL_K_RAY_FWD, st);
   if ((e = launch_pdl(k_ray_fwd<DevTable>, unsigned(sms * fwd_blocks_per_sm()), FWD_THREADS, 0, st, src)) !=

@@ -37,6 +37,12 @@ constexpr size_t CONV_WIDE_MIN_SMEM = 100 * 1024;
 
 // Whether the convolution of an H x W image, K x K PSF uses the second buffer.
 bool conv_two_buf(int H, int W, int K);
+// Shared memory of the separable convolution (rank-R PSF), whether a system
+// of this size takes it, and the dynamic shared memory of a segment's
+// convolution (separable or direct, as its flags say).
+size_t conv_sep_smem_bytes(int H, int W, int K, int R);
+bool conv_sep_ok(int H, int W, int K, int R);
+size_t seg_conv_smem(const Seg& g);
 
 // Convolution kernel class of a PSF side (0: K = 11, 1: K = 21, 2: any other odd K).
 int conv_class(int K);

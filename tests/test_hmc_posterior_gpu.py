@@ -143,7 +143,10 @@ def test_posterior_hmc_on_a_lens_system(mods):
     sampler = hmc.HMC(x0, torch.ones(d, dtype=torch.float64, device="cuda"), 0.3, 5, target=target, seed=6,
                       graphs=True)
     assert torch.isfinite(sampler.logp).all()
-    run = sampler.run_adaptive(n_burn=150, n_samples=200, adapt_trajectory=True, max_leapfrog=64)
+    # 200 + 400 iterations: with 150 + 200 one of four sampler seeds left two
+    # parameters at R-hat 1.16 (slow chains on a non-Gaussian posterior);
+    # at this length seeds 6-9 gave R-hat max 1.003-1.021
+    run = sampler.run_adaptive(n_burn=200, n_samples=400, adapt_trajectory=True, max_leapfrog=64)
     s.close()
     assert torch.isfinite(sampler.logp).all()
     assert 0.55 < run.accept_samples < 0.92, run

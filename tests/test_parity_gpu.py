@@ -250,8 +250,10 @@ def _sample_indices(B, nsample, seed):
 # ray's large gradient term by ~1e-5 of itself.
 FULL_SIZE_EXCEPTIONS = {
     # measured: gamma_epl 2.54 (vector 0: a source-plane ray 3.2 mas from the
-    # source centre, n_s = 3.9), x_epl 1.78
-    inputs.MULTISTART: {"gamma_epl": 3.0, "x_epl": 2.5},
+    # source centre, n_s = 3.9), x_epl 1.78 (vector 608: 1.5 mas, n_s = 3.5),
+    # gamma_ext1 1.002 (vector 2046: 4.1 mas, n_s = 3.3; 1.000 with the 2-D
+    # convolution, 1.002 with the separable one)
+    inputs.MULTISTART: {"gamma_epl": 3.0, "x_epl": 2.5, "gamma_ext1": 1.5},
 }
 
 
@@ -366,8 +368,8 @@ def test_banded_convolution_equals_one_block(abi, H, W, k, K, B):
     on a cluster of row bands (halo rows through distributed shared memory);
     a grouped call convolves it in one block. Per pixel the arithmetic is the
     same, so the gradients must be the same bits (log L only sums in another
-    order)."""
-    spec = inputs.SystemSpec(H, W, k, K, "gaussian")
+    order). A Moffat PSF: a separable one takes the 1-D passes instead."""
+    spec = inputs.SystemSpec(H, W, k, K, "moffat")
     truth, image, psf = make_system(spec, 500 + H * W + K)
     params = inputs.draw_perturbed(np.random.default_rng(H * W), truth, B).astype(np.float32)
     s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
@@ -379,3 +381,39 @@ def test_banded_convolution_equals_one_block(abi, H, W, k, K, B):
     np.testing.assert_array_equal(grads[0].cpu().numpy(), g1)
     np.testing.assert_allclose(lls[0].cpu().numpy(), ll1, rtol=1e-6, atol=0)
     assert np.all(np.isfinite(sim1))
+
+
+def _two_gaussians(K):
+    x = np.arange(K) - (K - 1) / 2.0
+    g1, g2 = np.exp(-0.5 * (x / 1.1) ** 2), np.exp(-0.5 * ((x - 1.0) / 2.3) ** 2)
+    psf = (np.outer(g1, g1) + 0.25 * np.outer(g2, g2[::-1])).astype(np.float32)
+    return psf / psf.sum()
+
+
+@pytest.mark.parametrize("H,W,k,K,B,rank", [(61, 59, 2, 11, 7, 1), (33, 70, 1, 21, 300, 1), (40, 47, 2, 11, 200, 2),
+                                            (90, 100, 1, 21, 3, 2)])
+def test_separable_psf_convolution(abi, H, W, k, K, B, rank):
+    """A PSF of rank 1 (sampled Gaussian) or 2 (two Gaussians, one of them
+    mirrored) is convolved as 1-D passes (the system stores its 2 R K
+    factors). Model images and the likelihood with its gradient match the
+    oracle's 2-D convolution, and the grouped launch gives the same bits."""
+    spec = inputs.SystemSpec(H, W, k, K, "gaussian")
+    psf = inputs.gaussian_psf(K).astype(np.float32) if rank == 1 else _two_gaussians(K)
+    assert abi.psf_factor(psf)[0] == rank
+    truth, image, psf = make_system(spec, 700 + H + K + rank, psf=psf)
+    params = inputs.draw_perturbed(np.random.default_rng(H * K), truth, B).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    assert s.psf_rank() == rank and s.resident_bytes() == 4 * (2 * H * W + K * K + 2 * rank * K)
+    p = torch.from_numpy(params).cuda()
+    ll, g = (t.cpu().numpy() for t in s.loglik_grad(p))
+    sim = s.simulate(p[:3]).cpu().numpy()
+    lls, grads, _ = abi.loglik_grad_grouped([s], [p])
+    s.close()
+    np.testing.assert_array_equal(grads[0].cpu().numpy(), g)
+    np.testing.assert_allclose(lls[0].cpu().numpy(), ll, rtol=1e-6, atol=0)
+    ref_sim = oracle.simulate(params[:3].astype(np.float64), H, W, psf, spec.pixel_scale, k)
+    tol = 1e-4 * np.abs(ref_sim) + 1e-5 * np.abs(ref_sim).max()
+    assert np.all(np.abs(sim - ref_sim) <= tol), np.max(np.abs(sim - ref_sim) / tol)
+    idx = _sample_indices(B, min(B, 24), H + W)
+    rl, _, rg = oracle_eval(spec, image, psf, params[idx])
+    assert_plain_parity(ll[idx], g[idx], rl, rg, "separable PSF rank %d %dx%d K=%d" % (rank, H, W, K))
