@@ -1140,34 +1140,95 @@ __device__ void conv_vector_rows(const Seg& s, int b, int mode, float* smem, dou
 // per pixel instead of K^2 (a sampled Gaussian PSF has R = 1: 22 instead of
 // 121 at K = 11). flip: the flipped PSF (the model's convolution), else the
 // PSF (the adjoint's correlation).
-constexpr int SEP_RV = 8;   // output rows per thread in the vertical pass
+constexpr int SEP_RV = 8;   // output rows per unit of the vertical pass
 
-// Horizontal passes: tmp + r Hp P, row i, columns j0 .. j0 + 15, for every
-// padded row i (lanes take consecutive rows: float4 loads of rows an odd
-// number of 16-byte words apart are conflict-free).
+// Shared memory of the separable form: the factors [R][2][K] (u_r, v_r), the
+// u_r taps again as duplicated pairs [R][K] (for packed FMAs), the
+// zero-padded input [Ht][P] and R row buffers [Ht][P]; Ht = H rounded up to
+// whole vertical units, plus K - 1 halo rows, so that no vertical unit reads
+// past a buffer. The same formula sizes the launch (conv_sep_smem_bytes).
+struct SepLayout {
+  int P, Ht, nvs;
+  float* fac;
+  float2* tapu;
+  float* img;
+  float* tmp;
+};
+
+__host__ __device__ inline int sep_rows(int H, int K) { return (H + SEP_RV - 1) / SEP_RV * SEP_RV + K - 1; }
+
+__device__ __forceinline__ SepLayout sep_layout(const Seg& s, float* smem) {
+  SepLayout L;
+  L.P = rowconv_pitch(s.W, s.K);
+  L.Ht = sep_rows(s.H, s.K);
+  L.nvs = (s.H + SEP_RV - 1) / SEP_RV;
+  const int nf = (2 * s.psf_rank * s.K + 3) & ~3;
+  L.fac = smem;
+  L.tapu = reinterpret_cast<float2*>(smem + nf);
+  L.img = smem + 2 * nf;
+  L.tmp = L.img + L.Ht * L.P;
+  return L;
+}
+
+// The factors into shared memory and the input buffer's halo (everything
+// outside rows c .. c + H - 1, columns c .. c + W - 1) zeroed; rows across
+// warps, columns across lanes. The caller synchronises the block before
+// the factors are read.
 template <int K>
-__device__ __forceinline__ void sep_hpass(const float* __restrict__ in, int P, int Hp, int W, const float* fac, int R,
-                                          bool flip, float* tmp) {
+__device__ __forceinline__ void sep_prepare(const Seg& s, const SepLayout& L) {
+  constexpr int c = (K - 1) / 2;
+  const int R = s.psf_rank;
+  for (int i = threadIdx.x; i < 2 * R * K; i += blockDim.x) L.fac[i] = s.psf_sep[i];
+  for (int i = threadIdx.x; i < R * K; i += blockDim.x) {
+    const float u = s.psf_sep[(i / K) * 2 * K + i % K];
+    L.tapu[i] = make_float2(u, u);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < L.Ht; i += nw) {
+    const bool inner = i >= c && i < c + s.H;
+    for (int q = lane; q < L.P; q += 32)
+      if (!inner || q < c || q >= c + s.W) L.img[i * L.P + q] = 0.f;
+  }
+}
+
+// The binned image (the vector's work slot) into the input's interior by
+// asynchronous copies; the caller synchronises the block after.
+template <int K>
+__device__ __forceinline__ void sep_load(const Seg& s, const SepLayout& L, const float* work) {
+  constexpr int c = (K - 1) / 2;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < s.H; i += nw)
+    for (int j = lane; j < s.W; j += 32) cp_async4(&L.img[(i + c) * L.P + j + c], &work[i * s.W + j]);
+  cp_async_wait_all();
+}
+
+// Horizontal passes: row buffer r, row i, columns j0 .. j0 + 15, for the Ht
+// rows. A warp takes 32 consecutive rows of one strip (float4 loads of rows
+// an odd number of 16-byte words apart are conflict-free); each unit loads
+// its input span once for the R terms.
+template <int K>
+__device__ __forceinline__ void sep_hpass(const float* __restrict__ in, const SepLayout& L, int W, int R, bool flip) {
   constexpr int S = 16, NIN = (S + K - 1 + 3) & ~3;
-  const int nstrip = (W + S - 1) / S;
-  for (int r = 0; r < R; ++r) {
-    const float* v = fac + (2 * r + 1) * K;
-    float tv[K];
+  const int P = L.P, Ht = L.Ht, nstrip = (W + S - 1) / S, rg = (Ht + 31) >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int w = wid; w < nstrip * rg; w += nw) {
+    const int strip = w / rg, i = (w - strip * rg) * 32 + lane, j0 = strip * S;   // warp-uniform division
+    if (i >= Ht) continue;
+    float x[NIN];
+    const float4* r4 = reinterpret_cast<const float4*>(in + i * P + j0);
 #pragma unroll
-    for (int q = 0; q < K; ++q) tv[q] = v[flip ? K - 1 - q : q];
-    float* out = tmp + size_t(r) * Hp * P;
-    for (int t = threadIdx.x; t < Hp * nstrip; t += blockDim.x) {
-      const int strip = t / Hp, i = t - strip * Hp, j0 = strip * S;
-      float x[NIN];
-      const float4* r4 = reinterpret_cast<const float4*>(in + i * P + j0);
+    for (int q = 0; q < NIN / 4; ++q) {
+      const float4 v = r4[q];
+      x[4 * q] = v.x;
+      x[4 * q + 1] = v.y;
+      x[4 * q + 2] = v.z;
+      x[4 * q + 3] = v.w;
+    }
+    for (int r = 0; r < R; ++r) {
+      const float* v = L.fac + (2 * r + 1) * K;
+      float tv[K];
 #pragma unroll
-      for (int q = 0; q < NIN / 4; ++q) {
-        const float4 w = r4[q];
-        x[4 * q] = w.x;
-        x[4 * q + 1] = w.y;
-        x[4 * q + 2] = w.z;
-        x[4 * q + 3] = w.w;
-      }
+      for (int q = 0; q < K; ++q) tv[q] = v[flip ? K - 1 - q : q];
       float acc[S];
 #pragma unroll
       for (int o = 0; o < S; ++o) {
@@ -1176,96 +1237,104 @@ __device__ __forceinline__ void sep_hpass(const float* __restrict__ in, int P, i
         for (int q = 0; q < K; ++q) a = fmaf(tv[q], x[o + q], a);
         acc[o] = a;
       }
-      float4* t4 = reinterpret_cast<float4*>(out + i * P + j0);
+      float4* t4 = reinterpret_cast<float4*>(L.tmp + size_t(r) * Ht * P + i * P + j0);
 #pragma unroll
       for (int q = 0; q < S / 4; ++q) t4[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
     }
   }
 }
 
-// Vertical passes of one unit: rows i0 .. i0 + 7 of column j, summed over
-// the R terms into m (lanes take consecutive columns).
+// Vertical passes of one unit: rows i0 .. i0 + 7 of columns j, j + 1 (j
+// even) in packed pairs, summed over the R terms (per lane the FMAs of the
+// scalar form, in the same order).
 template <int K>
-__device__ __forceinline__ void sep_vunit(const float* tmp, int P, int Hp, const float* fac, int R, bool flip, int i0,
-                                          int j, float (&m)[SEP_RV]) {
+__device__ __forceinline__ void sep_vunit(const SepLayout& L, int R, bool flip, int i0, int j, float2 (&m)[SEP_RV]) {
   constexpr int NV = SEP_RV + K - 1;
 #pragma unroll
-  for (int o = 0; o < SEP_RV; ++o) m[o] = 0.f;
+  for (int o = 0; o < SEP_RV; ++o) m[o] = make_float2(0.f, 0.f);
   for (int r = 0; r < R; ++r) {
-    const float* u = fac + 2 * r * K;
-    const float* col = tmp + size_t(r) * Hp * P + j;
-    float x[NV];
+    const float2* tap = L.tapu + r * K;
+    const float* col = L.tmp + size_t(r) * L.Ht * L.P + i0 * L.P + j;
+    float2 x[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) x[q] = (i0 + q < Hp) ? col[(i0 + q) * P] : 0.f;
+    for (int q = 0; q < NV; ++q) x[q] = *reinterpret_cast<const float2*>(col + q * L.P);
 #pragma unroll
     for (int o = 0; o < SEP_RV; ++o) {
-      float a = m[o];
+      float2 a = m[o];
 #pragma unroll
-      for (int q = 0; q < K; ++q) a = fmaf(u[flip ? K - 1 - q : q], x[o + q], a);
+      for (int q = 0; q < K; ++q) a = __ffma2_rn(tap[flip ? K - 1 - q : q], x[o + q], a);
       m[o] = a;
     }
   }
 }
 
-// One vector with a separable PSF (s.conv_sep). Shared memory: the factors,
-// the zero-padded input [H + K - 1][P] and R row buffers [H + K - 1][P].
-// The model pass's vertical step computes the likelihood terms of its
-// outputs at once and writes d log L / d M over the input's interior (the
-// horizontal step has read it); the correlation's vertical step writes the
-// subpixel adjoint to the vector's work slot. The arithmetic of every pixel
-// (its model value, its likelihood terms, its adjoint) is fixed by the
-// layout, not the block size; log L is summed in a block-size-dependent
-// order.
+// One vector with a separable PSF (s.conv_sep), its halo and factors in
+// place when prepared (a single-system kernel prepares once per block), else
+// set up here. The model pass's vertical step computes the likelihood terms
+// of its outputs at once and writes d log L / d M over the input's interior
+// (the horizontal step has read it); the correlation's vertical step writes
+// the subpixel adjoint to the vector's work slot. Every pixel's model value,
+// likelihood terms and adjoint are fixed by the layout, not the block size;
+// log L is summed in a block-size-dependent order. Vertical units (8 rows
+// of a column pair) go to consecutive threads along the row.
 template <int K>
-__device__ void conv_vector_sep(const Seg& s, int b, int mode, float* smem, double* red2) {
+__device__ void conv_vector_sep(const Seg& s, int b, int mode, float* smem, double* red2, bool prepared) {
   constexpr int c = (K - 1) / 2;
   const int H = s.H, W = s.W, HW = H * W, R = s.psf_rank;
-  const int P = rowconv_pitch(W, K), Hp = H + K - 1;
-  const int nvu = ((H + SEP_RV - 1) / SEP_RV) * W;   // vertical units
-  float* fac = smem;
-  float* img = smem + ((2 * R * K + 3) & ~3);
-  float* tmp = img + Hp * P;
+  const SepLayout L = sep_layout(s, smem);
   float* work = s.work + size_t(b) * HW;
   const bool want_sim = (mode == MODE_SIM);
   const bool corr_only = (mode == MODE_CORR);   // the work slot holds d log L / d M already
   const bool want_grad = (mode == MODE_GRAD) || corr_only;
-  for (int i = threadIdx.x; i < 2 * R * K; i += blockDim.x) fac[i] = s.psf_sep[i];
-  load_padded<K>(s, img, P, work);
+  const int Wp2 = (W + 1) >> 1, nvu = L.nvs * Wp2;   // vertical units: 8 rows x a column pair
+  if (!prepared) sep_prepare<K>(s, L);
+  sep_load<K>(s, L, work);
   __syncthreads();
   if (!corr_only) {
-    sep_hpass<K>(img, P, Hp, W, fac, R, true, tmp);
+    sep_hpass<K>(L.img, L, W, R, true);
     __syncthreads();
     float ll = 0.f, c2 = 0.f;
-    for (int t = threadIdx.x; t < nvu; t += blockDim.x) {
-      const int strip = t / W, j = t - strip * W, i0 = strip * SEP_RV;
-      float m[SEP_RV];
-      sep_vunit<K>(tmp, P, Hp, fac, R, true, i0, j, m);
+    for (int u = threadIdx.x; u < nvu; u += blockDim.x) {
+      const int strip = u / Wp2, j = 2 * (u - strip * Wp2), i0 = strip * SEP_RV;
+      const bool two = j + 1 < W;
+      float2 m[SEP_RV];
+      sep_vunit<K>(L, R, true, i0, j, m);
 #pragma unroll
       for (int o = 0; o < SEP_RV; ++o) {
         const int i = i0 + o;
         if (i >= H) break;
+        const int p = i * W + j;
         if (want_sim) {
-          s.sim[size_t(b) * HW + i * W + j] = m[o];
+          s.sim[size_t(b) * HW + p] = m[o].x;
+          if (two) s.sim[size_t(b) * HW + p + 1] = m[o].y;
           continue;
         }
-        const float gm = pixel_terms(s, i * W + j, m[o], ll, c2);
-        if (want_grad) img[(i + c) * P + j + c] = gm;
+        const float g0 = pixel_terms(s, p, m[o].x, ll, c2);
+        if (want_grad) L.img[(i + c) * L.P + j + c] = g0;
+        if (two) {
+          const float g1 = pixel_terms(s, p + 1, m[o].y, ll, c2);
+          if (want_grad) L.img[(i + c) * L.P + j + 1 + c] = g1;
+        }
       }
     }
     if (want_sim) return;
     block_loglik(s, b, ll, c2, red2);   // also the barrier before the correlation reads img
     if (!want_grad) return;
   }
-  sep_hpass<K>(img, P, Hp, W, fac, R, false, tmp);
+  sep_hpass<K>(L.img, L, W, R, false);
   __syncthreads();
   const float inv_k2 = 1.0f / float(s.k * s.k);
-  for (int t = threadIdx.x; t < nvu; t += blockDim.x) {
-    const int strip = t / W, j = t - strip * W, i0 = strip * SEP_RV;
-    float m[SEP_RV];
-    sep_vunit<K>(tmp, P, Hp, fac, R, false, i0, j, m);
+  for (int u = threadIdx.x; u < nvu; u += blockDim.x) {
+    const int strip = u / Wp2, j = 2 * (u - strip * Wp2), i0 = strip * SEP_RV;
+    float2 m[SEP_RV];
+    sep_vunit<K>(L, R, false, i0, j, m);
 #pragma unroll
-    for (int o = 0; o < SEP_RV; ++o)
-      if (i0 + o < H) work[(i0 + o) * W + j] = m[o] * inv_k2;
+    for (int o = 0; o < SEP_RV; ++o) {
+      const int i = i0 + o;
+      if (i >= H) break;
+      work[i * W + j] = m[o].x * inv_k2;
+      if (j + 1 < W) work[i * W + j + 1] = m[o].y * inv_k2;
+    }
   }
 }
 
@@ -1285,7 +1354,7 @@ __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src s
       // a single-system call takes k_conv_sep for a separable PSF; a table
       // may mix both kinds of segment
       if (!std::is_same<Src, OneSeg>::value && ss.conv_sep)
-        conv_vector_sep<K>(ss, b, mode, smem, red2);
+        conv_vector_sep<K>(ss, b, mode, smem, red2, false);
       else
         conv_vector_rows<K>(ss, b, mode, smem, red2);
     } else {
@@ -1303,10 +1372,12 @@ __global__ void __launch_bounds__(NT, MINB) k_conv_sep(const __grid_constant__ O
   float* smem = reinterpret_cast<float*>(smem4);
   __shared__ double red2[2 * (NT / 32)];
   const PdlScope pdl;
-  for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x) {
-    conv_vector_sep<K>(src.s, item, mode, smem, red2);
-    __syncthreads();
-  }
+  // the factors and the zero halo stay in place for all of the block's
+  // vectors; each vector's steps end with the vertical pass, which reads only
+  // the row buffers, and the next vector's horizontal pass comes after the
+  // barrier that follows its image load
+  sep_prepare<K>(src.s, sep_layout(src.s, smem));
+  for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x) conv_vector_sep<K>(src.s, item, mode, smem, red2, true);
 }
 
 // ---- small batches: one vector's convolution over a cluster of row bands ----
@@ -1595,8 +1666,8 @@ size_t conv_smem_bytes(int H, int W, int K, bool two_buf) {
 bool conv_two_buf(int H, int W, int K) { return conv_smem_bytes(H, W, K, true) <= CONV_TWO_BUF_MAX_SMEM; }
 
 size_t conv_sep_smem_bytes(int H, int W, int K, int R) {
-  const size_t P = size_t(rowconv_pitch(W, K)), Hp = size_t(H) + K - 1;
-  return (size_t((2 * R * K + 3) & ~3) + (1 + size_t(R)) * Hp * P) * sizeof(float);
+  const size_t P = size_t(rowconv_pitch(W, K)), Ht = size_t(sep_rows(H, K));
+  return (2 * size_t((2 * R * K + 3) & ~3) + (1 + size_t(R)) * Ht * P) * sizeof(float);
 }
 
 bool conv_sep_ok(int H, int W, int K, int R) {
@@ -1769,7 +1840,23 @@ static cudaError_t launch_conv_sep(const OneSeg& src, int nitems, size_t smem, i
       attr = smem;
     }
   }
-  return launch_pdl(k_conv_sep<K, NT, MINB>, unsigned(nitems), NT, smem, st, src, mode);
+  // at most the blocks resident at once: each prepares its factors and halo
+  // once and then takes every gridDim-th vector
+  static std::map<size_t, int> per_sm;   // by dynamic shared memory
+  int resident;
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    auto it = per_sm.find(smem);
+    if (it == per_sm.end()) {
+      int n = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_conv_sep<K, NT, MINB>, NT, smem);
+      if (e != cudaSuccess) return e;
+      it = per_sm.emplace(smem, n > 0 ? n : 1).first;
+    }
+    resident = num_sms() * it->second;
+  }
+  const int grid = nitems < resident ? nitems : resident;
+  return launch_pdl(k_conv_sep<K, NT, MINB>, unsigned(grid), NT, smem, st, src, mode);
 }
 
 // The convolution of a single-system call over nitems vectors: the
@@ -1782,7 +1869,7 @@ static cudaError_t launch_conv_one(const OneSeg& src, int nitems, int mode, cuda
       return wide ? launch_conv_sep<11, 512, 1>(src, nitems, smem, mode, st)
                   : launch_conv_sep<11, 256, 4>(src, nitems, smem, mode, st);
     return wide ? launch_conv_sep<21, 512, 1>(src, nitems, smem, mode, st)
-                : launch_conv_sep<21, 256, 2>(src, nitems, smem, mode, st);
+                : launch_conv_sep<21, 256, 3>(src, nitems, smem, mode, st);
   }
   return launch_conv_class(conv_class(s.K), src, nitems, smem, mode, st, false, wide || smem > CONV_WIDE_MIN_SMEM);
 }

@@ -143,3 +143,15 @@ def assert_plain_parity(ll, g, rl, rg, what="", grad_exceptions=None, ll_extra=N
     assert not over.any(), "%s grad: %d entries over the plain tolerance; worst %.3g x at vector %d param %s " \
         "(gpu %r ref %r)" % (what, int(over.sum()), e2[i, j], i, inputs.PARAM_NAMES[j], g[i, j], rg[i, j])
     return rep
+
+
+def assert_sum_order_close(ll, ref, what=""):
+    """log L of the same per-pixel terms summed in another order (the FP32
+    sums within a warp depend on the block size and on which thread holds
+    which pixel): the difference is rounding of the partial sums, whose size
+    the batch's largest |log L| sets, not each vector's own |log L| (a sum of
+    terms of both signs can be near zero)."""
+    ll, ref = np.asarray(ll), np.asarray(ref)
+    d = np.max(np.abs(ll - ref))
+    assert d <= 2e-6 * np.max(np.abs(ref)), "%s: log L differs by %.3g (batch max |log L| %.3g)" % (
+        what, d, np.max(np.abs(ref)))

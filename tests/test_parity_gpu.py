@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from paper_2202_07663_gb300 import inputs  # noqa: E402
-from gpu_common import assert_plain_parity, ll_bound, make_system, oracle_eval  # noqa: E402
+from gpu_common import assert_plain_parity, assert_sum_order_close, ll_bound, make_system, oracle_eval  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -217,11 +217,11 @@ def test_grouped_launch_equals_single_calls(abi):
     # gradients are the same bits; a single call this small runs the
     # convolution in wider blocks, which sums log L in another order
     for (sl, sg), ll, g in zip(singles, lls, grads):
-        np.testing.assert_allclose(ll.cpu().numpy(), sl, rtol=1e-6, atol=0)
+        assert_sum_order_close(ll.cpu().numpy(), sl, "grouped vs single")
         np.testing.assert_array_equal(g.cpu().numpy(), sg)
     lls2, grads2, _ = abi.loglik_grad_grouped(systems, params, grad=False)
     for (sl, _), ll, l1 in zip(singles, lls2, lls):
-        np.testing.assert_allclose(ll.cpu().numpy(), sl, rtol=1e-6, atol=0)
+        assert_sum_order_close(ll.cpu().numpy(), sl, "grouped vs single")
         np.testing.assert_array_equal(ll.cpu().numpy(), l1.cpu().numpy())
     for s in systems:
         s.close()
@@ -379,7 +379,7 @@ def test_banded_convolution_equals_one_block(abi, H, W, k, K, B):
     sim1 = s.simulate(p).cpu().numpy()
     s.close()
     np.testing.assert_array_equal(grads[0].cpu().numpy(), g1)
-    np.testing.assert_allclose(lls[0].cpu().numpy(), ll1, rtol=1e-6, atol=0)
+    assert_sum_order_close(lls[0].cpu().numpy(), ll1, "one block vs bands")
     assert np.all(np.isfinite(sim1))
 
 
@@ -410,7 +410,7 @@ def test_separable_psf_convolution(abi, H, W, k, K, B, rank):
     lls, grads, _ = abi.loglik_grad_grouped([s], [p])
     s.close()
     np.testing.assert_array_equal(grads[0].cpu().numpy(), g)
-    np.testing.assert_allclose(lls[0].cpu().numpy(), ll, rtol=1e-6, atol=0)
+    assert_sum_order_close(lls[0].cpu().numpy(), ll, "grouped vs single")
     ref_sim = oracle.simulate(params[:3].astype(np.float64), H, W, psf, spec.pixel_scale, k)
     tol = 1e-4 * np.abs(ref_sim) + 1e-5 * np.abs(ref_sim).max()
     assert np.all(np.abs(sim - ref_sim) <= tol), np.max(np.abs(sim - ref_sim) / tol)
