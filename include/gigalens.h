@@ -114,12 +114,16 @@ int gl_system_create_obsvar(gl_system** out, const float* image, const float* no
  * gl_psf_factor - the PSF as a sum of separable terms (host only; touches no
  *   device). The convolution of Eq. 4's model (and its adjoint) with a PSF
  *   P = sum_{r<R} u_r v_r^T is R pairs of 1-D passes, 2 K R multiply-adds per
- *   pixel instead of K^2. gl_system_create applies this to its PSF and, when
- *   R > 0, the PSF side is 11 or 21 and the separable buffers
- *   (2 (H + K - 1) + H) * P * 4 bytes (P as below) fit 200 KiB, keeps the
- *   factors and convolves that way (gl_system_psf_rank); a sampled Gaussian
- *   PSF has R = 1. The 2-D convolution of the oracle is the reference for
- *   both forms.
+ *   pixel instead of K^2. gl_system_create applies this to its PSF: when
+ *   R > 0 and the PSF side is 11 or 21 it keeps the factors
+ *   (gl_system_psf_rank) and convolves that way, the whole image in one
+ *   block when its R + 1 padded buffers fit 200 KiB of shared memory
+ *   ((R + 1) * (ceil(H/8)*8 + K - 1) * P * 4 bytes, P as below), else (and
+ *   for batches below half as many vectors as SMs) in row bands over a
+ *   thread-block cluster. Grouped and batched calls use the factors where
+ *   the whole image fits and the K x K stencil otherwise. A sampled
+ *   Gaussian PSF has R = 1. The oracle's 2-D convolution is the reference
+ *   for every form.
  *  psf    [K][K] row-major floats (the PSF as the system stores it).
  *  K      odd side, 1..255.
  *  fac    NULL, or room for fac_len floats: on return [R][2][K], the row
@@ -134,8 +138,9 @@ int gl_system_create_obsvar(gl_system** out, const float* image, const float* no
  */
 int gl_psf_factor(const float* psf, int K, float* fac, int fac_len, int* rank);
 
-/* The number of separable PSF terms the system convolves with (0: the
- * K x K stencil), or GL_ERR_INVALID_ARG for NULL. Host state only. */
+/* The number of separable PSF terms the system's single calls convolve
+ * with (0: the K x K stencil), or GL_ERR_INVALID_ARG for NULL. Host state
+ * only. */
 int gl_system_psf_rank(const gl_system* sys);
 
 /* Free the system, its resident data and its scratch. Synchronises the

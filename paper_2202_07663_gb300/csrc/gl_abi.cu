@@ -382,7 +382,7 @@ int create_impl(gl_system** out, const float* image, const std::vector<float>& s
   }
   std::vector<float> fac;
   const int R = psf_separable(psf_area, K, fac);
-  if (R > 0 && gl::conv_sep_ok(H, W, K, R)) {   // factors kept only where the 1-D passes run
+  if (R > 0 && gl::conv_sep_any(H, W, K, R)) {   // factors kept only where the 1-D passes run
     if ((e = cudaMalloc(&s->d_psf_sep, fac.size() * sizeof(float))) != cudaSuccess ||
         (e = cudaMemcpy(s->d_psf_sep, fac.data(), fac.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
             cudaSuccess) {

@@ -1157,11 +1157,12 @@ struct SepLayout {
 
 __host__ __device__ inline int sep_rows(int H, int K) { return (H + SEP_RV - 1) / SEP_RV * SEP_RV + K - 1; }
 
-__device__ __forceinline__ SepLayout sep_layout(const Seg& s, float* smem) {
+// rows: the output rows a block covers (the image, or a band of it)
+__device__ __forceinline__ SepLayout sep_layout(const Seg& s, float* smem, int rows) {
   SepLayout L;
   L.P = rowconv_pitch(s.W, s.K);
-  L.Ht = sep_rows(s.H, s.K);
-  L.nvs = (s.H + SEP_RV - 1) / SEP_RV;
+  L.Ht = sep_rows(rows, s.K);
+  L.nvs = (rows + SEP_RV - 1) / SEP_RV;
   const int nf = (2 * s.psf_rank * s.K + 3) & ~3;
   L.fac = smem;
   L.tapu = reinterpret_cast<float2*>(smem + nf);
@@ -1281,7 +1282,7 @@ template <int K>
 __device__ void conv_vector_sep(const Seg& s, int b, int mode, float* smem, double* red2, bool prepared) {
   constexpr int c = (K - 1) / 2;
   const int H = s.H, W = s.W, HW = H * W, R = s.psf_rank;
-  const SepLayout L = sep_layout(s, smem);
+  const SepLayout L = sep_layout(s, smem, H);
   float* work = s.work + size_t(b) * HW;
   const bool want_sim = (mode == MODE_SIM);
   const bool corr_only = (mode == MODE_CORR);   // the work slot holds d log L / d M already
@@ -1376,7 +1377,7 @@ __global__ void __launch_bounds__(NT, MINB) k_conv_sep(const __grid_constant__ O
   // vectors; each vector's steps end with the vertical pass, which reads only
   // the row buffers, and the next vector's horizontal pass comes after the
   // barrier that follows its image load
-  sep_prepare<K>(src.s, sep_layout(src.s, smem));
+  sep_prepare<K>(src.s, sep_layout(src.s, smem, src.s.H));
   for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x) conv_vector_sep<K>(src.s, item, mode, smem, red2, true);
 }
 
@@ -1529,18 +1530,171 @@ __global__ void __launch_bounds__(BAND_THREADS) k_conv_bands(const __grid_consta
     for (int j = lane; j < W; j += 32) work[(r0 + li) * W + j] = stage[li * P + j];
 }
 
+// ---- separable PSFs over a cluster of row bands ----
+//
+// The separable form for a vector whose whole-image buffers do not fit one
+// block's shared memory (200 x 200, K = 21), and for small batches (below
+// half as many vectors as SMs). A cluster of nb blocks shares the vector as
+// in k_conv_bands: block r holds its band's input rows with the K - 1 halo
+// rows (from the work slot), runs the horizontal and the fused vertical and
+// likelihood passes for its rows, and keeps d log L / d M of its rows over
+// its input's interior. After a cluster barrier it copies its halo rows of
+// d log L / d M from the blocks that own them (distributed shared memory)
+// and block 0 adds the bands' log L and chi^2 in rank order; after a second
+// barrier (no remote reads beyond it) each block correlates its rows. Per
+// pixel the arithmetic is that of conv_vector_sep (same factors, taps and
+// order), so the gradient bits do not depend on the banding. With
+// MODE_CORR the work slot already holds d log L / d M: each block loads its
+// rows with their halo and the blocks meet at a barrier before any of them
+// writes the work slot.
+__host__ __device__ inline size_t conv_sep_band_smem_bytes(int W, int K, int R, int rows) {
+  const size_t P = size_t(rowconv_pitch(W, K)), Ht = size_t(sep_rows(rows, K));
+  return (2 * size_t((2 * R * K + 3) & ~3) + (1 + size_t(R)) * Ht * P) * sizeof(float);
+}
+
+template <int K>
+__global__ void __launch_bounds__(BAND_THREADS, 2) k_conv_sep_bands(const __grid_constant__ OneSeg src, int mode,
+                                                                       int rows) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ float4 smem4[];
+  float* smem = reinterpret_cast<float*>(smem4);
+  __shared__ double red2[2 * (BAND_THREADS / 32)];
+  __shared__ double band_sum[2];
+  const PdlScope pdl;
+  constexpr int c = (K - 1) / 2;
+  const Seg& s = src.s;
+  const int nb = int(cluster.num_blocks()), rank = int(cluster.block_rank());
+  const int b = blockIdx.x / nb;
+  const int H = s.H, W = s.W, HW = H * W, R = s.psf_rank;
+  const int r0 = min(H, rank * rows), nr = min(H, r0 + rows) - r0;   // nr may be 0
+  const SepLayout L = sep_layout(s, smem, rows);                      // local row li holds image row r0 - c + li
+  const int P = L.P;
+  float* work = s.work + size_t(b) * HW;
+  const bool want_sim = (mode == MODE_SIM);
+  const bool corr_only = (mode == MODE_CORR);
+  const bool want_grad = (mode == MODE_GRAD) || corr_only;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+  for (int i = threadIdx.x; i < 2 * R * K; i += blockDim.x) L.fac[i] = s.psf_sep[i];
+  for (int i = threadIdx.x; i < R * K; i += blockDim.x) {
+    const float u = s.psf_sep[(i / K) * 2 * K + i % K];
+    L.tapu[i] = make_float2(u, u);
+  }
+  // the band's rows and halo rows of the input; rows outside the image, or
+  // past the last halo row, are zero
+  for (int li = wid; li < L.Ht; li += nw) {
+    const int g = r0 - c + li;
+    float* row = L.img + li * P;
+    if (li < nr + K - 1 && g >= 0 && g < H) {
+      for (int j = lane; j < W; j += 32) cp_async4(&row[j + c], &work[g * W + j]);
+      for (int q = lane; q < P - W; q += 32) row[q < c ? q : W + q] = 0.f;
+    } else {
+      for (int j = lane; j < P; j += 32) row[j] = 0.f;
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int Wp2 = (W + 1) >> 1, nvu = ((nr + SEP_RV - 1) / SEP_RV) * Wp2;
+  if (!corr_only) {
+    sep_hpass<K>(L.img, L, W, R, true);
+    __syncthreads();
+    float ll = 0.f, c2 = 0.f;
+    for (int u = threadIdx.x; u < nvu; u += blockDim.x) {
+      const int strip = u / Wp2, j = 2 * (u - strip * Wp2), i0 = strip * SEP_RV;
+      const bool two = j + 1 < W;
+      float2 m[SEP_RV];
+      sep_vunit<K>(L, R, true, i0, j, m);
+#pragma unroll
+      for (int o = 0; o < SEP_RV; ++o) {
+        const int li = i0 + o;
+        if (li >= nr) break;
+        const int p = (r0 + li) * W + j;
+        if (want_sim) {
+          s.sim[size_t(b) * HW + p] = m[o].x;
+          if (two) s.sim[size_t(b) * HW + p + 1] = m[o].y;
+          continue;
+        }
+        const float g0 = pixel_terms(s, p, m[o].x, ll, c2);
+        if (want_grad) L.img[(li + c) * P + j + c] = g0;
+        if (two) {
+          const float g1 = pixel_terms(s, p + 1, m[o].y, ll, c2);
+          if (want_grad) L.img[(li + c) * P + j + 1 + c] = g1;
+        }
+      }
+    }
+    ll = warp_sum_f(ll);
+    c2 = warp_sum_f(c2);
+    if (lane == 0) {
+      red2[2 * wid] = double(ll);
+      red2[2 * wid + 1] = double(c2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double Ls = 0.0, Cs = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        Ls += red2[2 * w];
+        Cs += red2[2 * w + 1];
+      }
+      band_sum[0] = Ls;
+      band_sum[1] = Cs;
+    }
+    cluster.sync();   // every band's d log L / d M and sums are in its shared memory
+    if (!want_sim && rank == 0 && threadIdx.x == 0) {
+      double Ls = 0.0, Cs = 0.0;
+      for (int r = 0; r < nb; ++r) {
+        const double* bs = cluster.map_shared_rank(band_sum, r);
+        Ls += bs[0];
+        Cs += bs[1];
+      }
+      if (s.loglik) s.loglik[b] = -0.5 * Ls;
+      if (s.chi2) s.chi2[b] = Cs;
+    }
+    if (want_grad) {
+      // the halo rows of d log L / d M from the bands that own them
+      for (int li = wid; li < nr + K - 1; li += nw) {
+        if (li >= c && li < c + nr) continue;
+        const int g = r0 - c + li;
+        if (g < 0 || g >= H) continue;   // stays zero
+        const int owner = g / rows;
+        const float* orow = cluster.map_shared_rank(L.img, owner) + (g - owner * rows + c) * P + c;
+        for (int j = lane; j < W; j += 32) L.img[li * P + j + c] = orow[j];
+      }
+    }
+    cluster.sync();   // no block reads another's shared memory after this barrier
+    if (!want_grad) return;
+  } else {
+    cluster.sync();   // every band holds its input before any band writes the work slot
+  }
+  sep_hpass<K>(L.img, L, W, R, false);
+  __syncthreads();
+  const float inv_k2 = 1.0f / float(s.k * s.k);
+  for (int u = threadIdx.x; u < nvu; u += blockDim.x) {
+    const int strip = u / Wp2, j = 2 * (u - strip * Wp2), i0 = strip * SEP_RV;
+    float2 m[SEP_RV];
+    sep_vunit<K>(L, R, false, i0, j, m);
+#pragma unroll
+    for (int o = 0; o < SEP_RV; ++o) {
+      const int li = i0 + o;
+      if (li >= nr) break;
+      work[(r0 + li) * W + j] = m[o].x * inv_k2;
+      if (j + 1 < W) work[(r0 + li) * W + j + 1] = m[o].y * inv_k2;
+    }
+  }
+}
+
 // ------------------------------------------------------------- k_final ----
 
-// The per-vector chain rule from the summed accumulators a[NACC] and the
-// parameters p (both FP64): gradient entry j. Shared by the two k_final
-// variants so that they give identical results.
 // b_n / n of a Sersic index.
 __device__ __forceinline__ double bn_over_n(float n) {
   const double x = double(n);
   return (1.9992 * x - 0.3271) / x;
 }
 
-// ms, ml: bn_over_n of the source (pf[16]) and of the lens light (pf[9]).
+// The per-vector chain rule from the summed accumulators a[NACC] and the
+// parameters pf (FP64 arithmetic): gradient entry j; ms, ml: bn_over_n of
+// the source (pf[16]) and of the lens light (pf[9]). Shared by the two
+// k_final variants so that they give identical results.
 __device__ __forceinline__ double chain_rule(int j, const double* a, const float* pf, double ms, double ml) {
   const double ln2 = 0.69314718055994530942;
   if (j < 8) return j == 0 ? ms * (double(pf[1]) - 1.0) / double(pf[0]) * a[A_THETAE] : ms * a[A_THETAE + j];
@@ -1670,10 +1824,50 @@ size_t conv_sep_smem_bytes(int H, int W, int K, int R) {
   return (2 * size_t((2 * R * K + 3) & ~3) + (1 + size_t(R)) * Ht * P) * sizeof(float);
 }
 
+// 2 K R multiply-adds per pixel and pass against K^2, with a pass of
+// shared-memory traffic per term: worth it at R <= K / 4
+static bool conv_sep_worth(int K, int R) { return R > 0 && 4 * R <= K && (K == 11 || K == 21); }
+
 bool conv_sep_ok(int H, int W, int K, int R) {
-  // 2 K R multiply-adds per pixel and pass against K^2, with a pass of
-  // shared-memory traffic per term: worth it at R <= K / 4
-  return R > 0 && 4 * R <= K && (K == 11 || K == 21) && conv_sep_smem_bytes(H, W, K, R) <= CONV_TWO_BUF_MAX_SMEM;
+  return conv_sep_worth(K, R) && conv_sep_smem_bytes(H, W, K, R) <= CONV_TWO_BUF_MAX_SMEM;
+}
+
+// Row bands of the separable cluster convolution: at most 8 (a portable
+// cluster) of at least max(16, (K - 1) / 2) rows, so that a band's halo rows
+// come from its two neighbours. small: a batch below half as many vectors
+// as SMs, up to 2 SMs / B bands of at least 2 (K - 1) rows (up to two
+// blocks per SM over the call); else the fewest bands whose blocks fit two
+// per SM, or one. Returns the band count (0: none) and the rows per band.
+static int sep_band_plan(int H, int W, int K, int R, bool small, int B, int* rows_out) {
+  const int min_rows = (K - 1) / 2 > 16 ? (K - 1) / 2 : 16;
+  int best = 0, best_rows = 0;
+  if (small) {
+    // bands of at least 2 (K - 1) rows: thinner ones spend more on the halo
+    // rows' horizontal passes than the extra blocks gain
+    const int small_rows = 2 * (K - 1) > min_rows ? 2 * (K - 1) : min_rows;
+    int nb = 2 * num_sms() / (B > 0 ? B : 1);
+    if (nb > 8) nb = 8;
+    while (nb > 1 && (H + nb - 1) / nb < small_rows) --nb;
+    const int rows = (H + nb - 1) / nb;
+    if (nb >= 2 && conv_sep_band_smem_bytes(W, K, R, rows) <= CONV_TWO_BUF_MAX_SMEM) best = nb, best_rows = rows;
+  } else {
+    // two blocks of 112 KB (and their reserved shared memory) fit an SM's 228 KB
+    for (const size_t cap : {size_t(112 * 1024), size_t(CONV_TWO_BUF_MAX_SMEM)}) {
+      for (int nb = 2; nb <= 8 && best == 0; ++nb) {
+        const int rows = (H + nb - 1) / nb;
+        if (rows < min_rows) break;
+        if (conv_sep_band_smem_bytes(W, K, R, rows) <= cap) best = nb, best_rows = rows;
+      }
+      if (best) break;
+    }
+  }
+  *rows_out = best_rows;
+  return best;
+}
+
+bool conv_sep_any(int H, int W, int K, int R) {
+  int rows;
+  return conv_sep_ok(H, W, K, R) || (conv_sep_worth(K, R) && sep_band_plan(H, W, K, R, false, 0, &rows) > 0);
 }
 
 size_t seg_conv_smem(const Seg& g) {
@@ -1918,6 +2112,35 @@ static cudaError_t launch_conv_bands(const OneSeg& src, int nb, int mode, cudaSt
   return cudaLaunchKernelEx(&cfg, k_conv_bands<K>, src, mode, rows);
 }
 
+template <int K>
+static cudaError_t launch_conv_sep_bands(const OneSeg& src, int nb, int rows, int mode, cudaStream_t st) {
+  static size_t attr = 48 * 1024;
+  const size_t smem = conv_sep_band_smem_bytes(src.s.W, K, src.s.psf_rank, rows);
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (smem > attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_conv_sep_bands<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+      attr = smem;
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(src.s.B) * unsigned(nb));
+  cfg.blockDim = dim3(BAND_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = unsigned(nb);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k_conv_sep_bands<K>, src, mode, rows);
+}
+
 template <class Src>
 static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj_final, cudaStream_t st,
                             Hooks* hooks, bool persistent, bool one_tile = false, bool fwd_rays = true,
@@ -1971,8 +2194,17 @@ cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
   cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false, mode != MODE_CORR);
   if (e != cudaSuccess) return e;
   hooks->before(GL_K_CONV, st);
-  const int nb = (mode == MODE_CORR || s.conv_sep) ? 0 : conv_bands(s.B, s.H, s.W, s.K);
-  if (nb > 0)
+  // a separable PSF: the whole image in one block, or row bands over a
+  // cluster (small batches, and images whose buffers do not fit one block);
+  // else the 2-D stencil, in bands for small batches
+  int rows = 0;
+  const bool small = 2 * s.B <= num_sms();
+  const int sb = s.psf_rank > 0 && (small || !s.conv_sep) ? sep_band_plan(s.H, s.W, s.K, s.psf_rank, small, s.B, &rows) : 0;
+  const int nb = (sb > 0 || mode == MODE_CORR || s.conv_sep) ? 0 : conv_bands(s.B, s.H, s.W, s.K);
+  if (sb > 0)
+    e = s.K == 11 ? launch_conv_sep_bands<11>(src, sb, rows, mode, st)
+                  : launch_conv_sep_bands<21>(src, sb, rows, mode, st);
+  else if (nb > 0)
     e = s.K == 11 ? launch_conv_bands<11>(src, nb, mode, st) : launch_conv_bands<21>(src, nb, mode, st);
   else
     e = launch_conv_one(src, s.B, mode, st, s.B < num_sms());

@@ -42,6 +42,9 @@ bool conv_two_buf(int H, int W, int K);
 // convolution (separable or direct, as its flags say).
 size_t conv_sep_smem_bytes(int H, int W, int K, int R);
 bool conv_sep_ok(int H, int W, int K, int R);
+// Whether a system of this size convolves a rank-R PSF separably in single
+// calls (whole image in one block, or in row bands over a cluster).
+bool conv_sep_any(int H, int W, int K, int R);
 size_t seg_conv_smem(const Seg& g);
 
 // Convolution kernel class of a PSF side (0: K = 11, 1: K = 21, 2: any other odd K).

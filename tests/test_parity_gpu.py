@@ -417,3 +417,56 @@ def test_separable_psf_convolution(abi, H, W, k, K, B, rank):
     idx = _sample_indices(B, min(B, 24), H + W)
     rl, _, rg = oracle_eval(spec, image, psf, params[idx])
     assert_plain_parity(ll[idx], g[idx], rl, rg, "separable PSF rank %d %dx%d K=%d" % (rank, H, W, K))
+
+
+@pytest.mark.parametrize("H,W,k,K,B", [(80, 80, 2, 11, 1), (61, 59, 2, 11, 7), (100, 90, 1, 21, 4), (100, 40, 2, 21, 30)])
+def test_separable_bands_equal_one_block(abi, H, W, k, K, B):
+    """Below half as many vectors as SMs a single call convolves a separable
+    PSF on a cluster of row bands; a grouped call convolves the whole image
+    in one block. Per pixel the arithmetic is the same (factors, taps and
+    their order), so the gradients are the same bits and the model images
+    agree with the oracle."""
+    spec = inputs.SystemSpec(H, W, k, K, "gaussian")
+    truth, image, psf = make_system(spec, 900 + H * W + K)
+    params = inputs.draw_perturbed(np.random.default_rng(H * W + 1), truth, B).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    assert s.psf_rank() == 1
+    p = torch.from_numpy(params).cuda()
+    ll1, g1 = (t.cpu().numpy() for t in s.loglik_grad(p))
+    ll_only = s.loglik(p).cpu().numpy()
+    lls, grads, _ = abi.loglik_grad_grouped([s], [p])
+    sim = s.simulate(p).cpu().numpy()
+    s.close()
+    np.testing.assert_array_equal(grads[0].cpu().numpy(), g1)
+    np.testing.assert_array_equal(ll_only, ll1)
+    assert_sum_order_close(lls[0].cpu().numpy(), ll1, "one block vs bands")
+    ref = oracle.simulate(params.astype(np.float64), H, W, psf, spec.pixel_scale, k)
+    tol = 1e-4 * np.abs(ref) + 1e-5 * np.abs(ref).max()
+    assert np.all(np.abs(sim - ref) <= tol), np.max(np.abs(sim - ref) / tol)
+    rl, _, rg = oracle_eval(spec, image, psf, params)
+    assert_plain_parity(ll1, g1, rl, rg, "separable bands %dx%d K=%d" % (H, W, K))
+
+
+@pytest.mark.parametrize("H,W,k,K,B", [(200, 200, 1, 21, 3), (170, 150, 1, 11, 200), (190, 210, 1, 21, 160)])
+def test_separable_bands_for_large_images(abi, H, W, k, K, B):
+    """Images whose separable buffers do not fit one block convolve in
+    cluster row bands (the last band shorter where the rows do not divide);
+    model images, log L and the gradient against the oracle, log L alone
+    equal to the gradient call's."""
+    spec = inputs.SystemSpec(H, W, k, K, "gaussian")
+    truth, image, psf = make_system(spec, 950 + H + W + K)
+    params = inputs.draw_perturbed(np.random.default_rng(H + 2 * W), truth, B).astype(np.float32)
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+    assert s.psf_rank() == 1
+    p = torch.from_numpy(params).cuda()
+    ll, g = (t.cpu().numpy() for t in s.loglik_grad(p))
+    ll_only = s.loglik(p).cpu().numpy()
+    sim = s.simulate(p[:2]).cpu().numpy()
+    s.close()
+    np.testing.assert_array_equal(ll_only, ll)
+    ref = oracle.simulate(params[:2].astype(np.float64), H, W, psf, spec.pixel_scale, k)
+    tol = 1e-4 * np.abs(ref) + 1e-5 * np.abs(ref).max()
+    assert np.all(np.abs(sim - ref) <= tol), np.max(np.abs(sim - ref) / tol)
+    idx = _sample_indices(B, min(B, 8), H + W)
+    rl, _, rg = oracle_eval(spec, image, psf, params[idx])
+    assert_plain_parity(ll[idx], g[idx], rl, rg, "separable bands %dx%d K=%d" % (H, W, K))

@@ -55,9 +55,18 @@ def test_observed_variance_system_matches_oracle(abi):
     assert_plain_parity(ll, g, rl, rg, "observed variance")
 
 
-@pytest.mark.parametrize("B", [1, 13, 64])
-def test_profiled_loglik_matches_oracle(abi, B):
-    spec, truth, psf, _, image = _system(3)
+# K = 9: the 2-D stencil; K = 11 (a Gaussian, rank 1): the separable form,
+# in cluster bands below half as many vectors as SMs and whole-image above.
+# Named exceptions, measured: vector 78 of the 200-vector draw has a
+# source-plane ray 0.28 mas from the source centre (n_s = 2.56), the
+# closest of the draw (median 4.5 mas): x_epl 3.35 and x_s 2.47 x the plain
+# tolerance, the same with the 2-D stencil (K = 9: 3.37, 2.48).
+PROFILED_EXCEPTIONS = {(200, 11): {"x_epl": 4.0, "x_s": 3.0}}
+
+
+@pytest.mark.parametrize("B,K", [(1, 9), (13, 9), (64, 9), (5, 11), (200, 11)])
+def test_profiled_loglik_matches_oracle(abi, B, K):
+    spec, truth, psf, _, image = _system(3, K=K)
     params = inputs.draw_perturbed(np.random.default_rng(B), truth, B, frac=0.02).astype(np.float32)
     s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg,
                      observed_variance=True)
@@ -74,7 +83,7 @@ def test_profiled_loglik_matches_oracle(abi, B):
     sig = np.sqrt(vo.observed_variance(image, np.float32(spec.sigma_bkg), spec.gain_exposure))
     at = params.copy()
     at[:, vo.I_L], at[:, vo.I_S] = ramps[:, 0], ramps[:, 1]
-    assert_plain_parity(ll, g, rl, rg, "profiled")
+    assert_plain_parity(ll, g, rl, rg, "profiled", grad_exceptions=PROFILED_EXCEPTIONS.get((B, K)))
     np.testing.assert_allclose(c2, rc2, rtol=1e-3)
 
 
