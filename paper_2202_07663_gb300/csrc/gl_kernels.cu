@@ -261,27 +261,33 @@ __device__ __forceinline__ void series_coeffs(int lane, float t, VecConst* V) {
   }
 }
 
-// Block size of k_setup: eight warps, one vector each per step.
-constexpr int SETUP_THREADS = 8 * 32;
+// Block size of k_setup: eight warps of per-vector work and one for the
+// FP64 constants of their vectors.
+constexpr int SETUP_THREADS = 9 * 32;
 
-// A block takes its vectors wpb (warps per block) at a time. First the FP64
-// constants: thread 3 v + part of the block forms part `part` of vector v
-// of the chunk (setup_fp64_part), so that one warp's FP64 instructions serve
-// several vectors. Then one warp per vector: lanes 0..21 check one parameter
-// each, lane 0 the EPL's FP32 constants, lanes 1 and 2 the validity of the
-// light profiles; all lanes compute the series coefficients and, by ballot,
-// the term count (FP32: every constant feeds FP32 arithmetic). The two
-// phases write disjoint fields of VecConst.
+// A block takes its vectors wpb (warps per block less one) at a time. The
+// last warp forms the FP64 constants: lane 3 v + part forms part `part` of
+// vector v of the chunk (setup_fp64_part), so that one warp's FP64
+// instructions serve several vectors. Each other warp takes one vector:
+// lanes 0..21 check one parameter each, lane 0 the EPL's FP32 constants,
+// lanes 1 and 2 the validity of the light profiles; all lanes compute the
+// series coefficients and, by ballot, the term count (FP32: every constant
+// feeds FP32 arithmetic). The two kinds of warp run side by side and write
+// disjoint fields of VecConst (one call at 60x60, B = 4096: 12.5 -> 11.8 us
+// against the FP64 parts in the first warp before its own vector).
 template <class Src>
 __global__ void k_setup(const __grid_constant__ Src src) {
   const PdlScope pdl;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
+  const int wpb = (blockDim.x >> 5) - 1;
   const int nvec = src.nvec();
   for (int base = blockIdx.x * wpb; base < nvec; base += gridDim.x * wpb) {
-    if (int(threadIdx.x) < 3 * wpb) {
-      const int item = base + threadIdx.x / 3;
-      if (item < nvec) setup_fp64_part(src, item, threadIdx.x % 3);
+    if (warp == wpb) {
+      if (lane < 3 * wpb) {
+        const int item = base + lane / 3;
+        if (item < nvec) setup_fp64_part(src, item, lane % 3);
+      }
+      continue;
     }
     const int item = base + warp;
     if (item >= nvec) continue;   // warp-uniform
@@ -1714,6 +1720,11 @@ __device__ __forceinline__ double chain_rule(int j, const double* a, const float
 }
 
 // One thread per vector (calls whose vectors have one ray tile each).
+// Block size of k_final (one thread per vector): one warp, so that a large
+// batch's FP64 chain rule spreads over four times as many SMs as with
+// FINAL_THREADS (60x60, B = 4096: 11.2 -> 10.7 us).
+constexpr int FINAL1_THREADS = 32;
+
 template <class Src>
 __global__ void k_final(const __grid_constant__ Src src) {
   const PdlScope pdl;
@@ -2147,14 +2158,14 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
                             bool short_tiles = false) {
   const int sms = num_sms();
   cudaError_t e;
-  const int vthreads = SETUP_THREADS, wpb = vthreads / 32;
+  const int vthreads = SETUP_THREADS, wpb = vthreads / 32 - 1;
   int sgrid = (nvec + wpb - 1) / wpb;
-  int fgrid = (nvec + FINAL_THREADS - 1) / FINAL_THREADS;
+  int fgrid = (nvec + FINAL1_THREADS - 1) / FINAL1_THREADS;
   int wgrid = (nvec + FINAL_THREADS / 32 - 1) / (FINAL_THREADS / 32);
   int rgrid = nray;
   if (persistent) {
     sgrid = sgrid < sms * 4 ? sgrid : sms * 4;
-    fgrid = fgrid < sms ? fgrid : sms;
+    fgrid = fgrid < sms * 4 ? fgrid : sms * 4;
     wgrid = wgrid < sms * 4 ? wgrid : sms * 4;
     rgrid = rgrid < sms * 4 ? rgrid : sms * 4;
   }
@@ -2179,7 +2190,7 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
     if (e != cudaSuccess || (e = h) != cudaSuccess) return e;
     hooks->before(GL_K_FINAL, st);
     if (one_tile)
-      e = launch_pdl(k_final<Src>, unsigned(fgrid), FINAL_THREADS, 0, st, src);
+      e = launch_pdl(k_final<Src>, unsigned(fgrid), FINAL1_THREADS, 0, st, src);
     else
       e = launch_pdl(k_final_warp<Src>, unsigned(wgrid), FINAL_THREADS, 0, st, src);
     h = hooks->after(GL_K_FINAL, st);
