@@ -106,7 +106,7 @@ struct DevTable {
   }
 };
 
-// Copy a struct of 4-byte words into shared memory with the whole block.// Copy a struct of 4-byte words into shared memory with the whole block.
+// Copy a struct of 4-byte words into shared memory with the whole block.
 template <class T>
 __device__ __forceinline__ void block_copy(T* dst, const T* src) {
   static_assert(sizeof(T) % 4 == 0, "word copy");
@@ -1212,14 +1212,22 @@ __device__ __forceinline__ void sep_load(const Seg& s, const SepLayout& L, const
 // Horizontal passes: row buffer r, row i, columns j0 .. j0 + 15, for the Ht
 // rows. A warp takes 32 consecutive rows of one strip (float4 loads of rows
 // an odd number of 16-byte words apart are conflict-free); each unit loads
-// its input span once for the R terms.
-template <int K>
-__device__ __forceinline__ void sep_hpass(const float* __restrict__ in, const SepLayout& L, int W, int R, bool flip) {
+// its input span once for the R terms. FLIP: the flipped factor (the model's
+// convolution); RC: the rank when known at compile time (1), else 0.
+template <int K, bool FLIP, int RC>
+__device__ __forceinline__ void sep_hpass(const float* __restrict__ in, const SepLayout& L, int W, int Rrt) {
   constexpr int S = 16, NIN = (S + K - 1 + 3) & ~3;
-  const int P = L.P, Ht = L.Ht, nstrip = (W + S - 1) / S, rg = (Ht + 31) >> 5;
+  const int R = RC > 0 ? RC : Rrt;
+  const int P = L.P, Ht = L.Ht, nstrip = (W + S - 1) / S, rg = (Ht + 31) >> 5, tasks = nstrip * rg;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int w = wid; w < nstrip * rg; w += nw) {
-    const int strip = w / rg, i = (w - strip * rg) * 32 + lane, j0 = strip * S;   // warp-uniform division
+  int strip = wid / rg, g = wid - strip * rg;   // task w = strip * rg + g, stepped without division
+  for (int w = wid; w < tasks; w += nw) {
+    const int i = g * 32 + lane, j0 = strip * S;
+    g += nw;
+    while (g >= rg) {
+      g -= rg;
+      ++strip;
+    }
     if (i >= Ht) continue;
     float x[NIN];
     const float4* r4 = reinterpret_cast<const float4*>(in + i * P + j0);
@@ -1233,15 +1241,12 @@ __device__ __forceinline__ void sep_hpass(const float* __restrict__ in, const Se
     }
     for (int r = 0; r < R; ++r) {
       const float* v = L.fac + (2 * r + 1) * K;
-      float tv[K];
-#pragma unroll
-      for (int q = 0; q < K; ++q) tv[q] = v[flip ? K - 1 - q : q];
       float acc[S];
 #pragma unroll
       for (int o = 0; o < S; ++o) {
         float a = 0.f;
 #pragma unroll
-        for (int q = 0; q < K; ++q) a = fmaf(tv[q], x[o + q], a);
+        for (int q = 0; q < K; ++q) a = fmaf(v[FLIP ? K - 1 - q : q], x[o + q], a);
         acc[o] = a;
       }
       float4* t4 = reinterpret_cast<float4*>(L.tmp + size_t(r) * Ht * P + i * P + j0);
@@ -1254,9 +1259,10 @@ __device__ __forceinline__ void sep_hpass(const float* __restrict__ in, const Se
 // Vertical passes of one unit: rows i0 .. i0 + 7 of columns j, j + 1 (j
 // even) in packed pairs, summed over the R terms (per lane the FMAs of the
 // scalar form, in the same order).
-template <int K>
-__device__ __forceinline__ void sep_vunit(const SepLayout& L, int R, bool flip, int i0, int j, float2 (&m)[SEP_RV]) {
+template <int K, bool FLIP, int RC>
+__device__ __forceinline__ void sep_vunit(const SepLayout& L, int Rrt, int i0, int j, float2 (&m)[SEP_RV]) {
   constexpr int NV = SEP_RV + K - 1;
+  const int R = RC > 0 ? RC : Rrt;
 #pragma unroll
   for (int o = 0; o < SEP_RV; ++o) m[o] = make_float2(0.f, 0.f);
   for (int r = 0; r < R; ++r) {
@@ -1269,8 +1275,27 @@ __device__ __forceinline__ void sep_vunit(const SepLayout& L, int R, bool flip, 
     for (int o = 0; o < SEP_RV; ++o) {
       float2 a = m[o];
 #pragma unroll
-      for (int q = 0; q < K; ++q) a = __ffma2_rn(tap[flip ? K - 1 - q : q], x[o + q], a);
+      for (int q = 0; q < K; ++q) a = __ffma2_rn(tap[FLIP ? K - 1 - q : q], x[o + q], a);
       m[o] = a;
+    }
+  }
+}
+
+// Calls f(i0, j) for every vertical unit of nvs strips of 8 rows and Wp2
+// column pairs. Where a block's threads cover at least one strip's pairs,
+// thread t keeps column pair t % Wp2 and steps through the strips
+// (one division per call); else the units are spread over all threads.
+template <class F>
+__device__ __forceinline__ void for_vunits(int nvs, int Wp2, F&& f) {
+  const int spr = blockDim.x / Wp2;   // strips per round
+  if (spr > 0) {
+    const int s0 = threadIdx.x / Wp2, jp = threadIdx.x - s0 * Wp2;
+    if (s0 < spr)
+      for (int strip = s0; strip < nvs; strip += spr) f(strip * SEP_RV, 2 * jp);
+  } else {
+    for (int u = threadIdx.x; u < nvs * Wp2; u += blockDim.x) {
+      const int strip = u / Wp2;
+      f(strip * SEP_RV, 2 * (u - strip * Wp2));
     }
   }
 }
@@ -1282,30 +1307,30 @@ __device__ __forceinline__ void sep_vunit(const SepLayout& L, int R, bool flip, 
 // (the horizontal step has read it); the correlation's vertical step writes
 // the subpixel adjoint to the vector's work slot. Every pixel's model value,
 // likelihood terms and adjoint are fixed by the layout, not the block size;
-// log L is summed in a block-size-dependent order. Vertical units (8 rows
-// of a column pair) go to consecutive threads along the row.
-template <int K>
-__device__ void conv_vector_sep(const Seg& s, int b, int mode, float* smem, double* red2, bool prepared) {
+// log L is summed in a block-size-dependent order. MODE_T: the mode when
+// known at compile time, else -1 (mode_rt); RC as for sep_hpass.
+template <int K, int MODE_T, int RC>
+__device__ void conv_vector_sep(const Seg& s, int b, int mode_rt, float* smem, double* red2, bool prepared) {
   constexpr int c = (K - 1) / 2;
-  const int H = s.H, W = s.W, HW = H * W, R = s.psf_rank;
+  const int mode = MODE_T >= 0 ? MODE_T : mode_rt;
+  const int H = s.H, W = s.W, HW = H * W, R = RC > 0 ? RC : s.psf_rank;
   const SepLayout L = sep_layout(s, smem, H);
   float* work = s.work + size_t(b) * HW;
   const bool want_sim = (mode == MODE_SIM);
   const bool corr_only = (mode == MODE_CORR);   // the work slot holds d log L / d M already
   const bool want_grad = (mode == MODE_GRAD) || corr_only;
-  const int Wp2 = (W + 1) >> 1, nvu = L.nvs * Wp2;   // vertical units: 8 rows x a column pair
+  const int Wp2 = (W + 1) >> 1;
   if (!prepared) sep_prepare<K>(s, L);
   sep_load<K>(s, L, work);
   __syncthreads();
   if (!corr_only) {
-    sep_hpass<K>(L.img, L, W, R, true);
+    sep_hpass<K, true, RC>(L.img, L, W, R);
     __syncthreads();
     float ll = 0.f, c2 = 0.f;
-    for (int u = threadIdx.x; u < nvu; u += blockDim.x) {
-      const int strip = u / Wp2, j = 2 * (u - strip * Wp2), i0 = strip * SEP_RV;
+    for_vunits(L.nvs, Wp2, [&](int i0, int j) {
       const bool two = j + 1 < W;
       float2 m[SEP_RV];
-      sep_vunit<K>(L, R, true, i0, j, m);
+      sep_vunit<K, true, RC>(L, R, i0, j, m);
 #pragma unroll
       for (int o = 0; o < SEP_RV; ++o) {
         const int i = i0 + o;
@@ -1323,18 +1348,17 @@ __device__ void conv_vector_sep(const Seg& s, int b, int mode, float* smem, doub
           if (want_grad) L.img[(i + c) * L.P + j + 1 + c] = g1;
         }
       }
-    }
+    });
     if (want_sim) return;
     block_loglik(s, b, ll, c2, red2);   // also the barrier before the correlation reads img
     if (!want_grad) return;
   }
-  sep_hpass<K>(L.img, L, W, R, false);
+  sep_hpass<K, false, RC>(L.img, L, W, R);
   __syncthreads();
   const float inv_k2 = 1.0f / float(s.k * s.k);
-  for (int u = threadIdx.x; u < nvu; u += blockDim.x) {
-    const int strip = u / Wp2, j = 2 * (u - strip * Wp2), i0 = strip * SEP_RV;
+  for_vunits(L.nvs, Wp2, [&](int i0, int j) {
     float2 m[SEP_RV];
-    sep_vunit<K>(L, R, false, i0, j, m);
+    sep_vunit<K, false, RC>(L, R, i0, j, m);
 #pragma unroll
     for (int o = 0; o < SEP_RV; ++o) {
       const int i = i0 + o;
@@ -1342,7 +1366,7 @@ __device__ void conv_vector_sep(const Seg& s, int b, int mode, float* smem, doub
       work[i * W + j] = m[o].x * inv_k2;
       if (j + 1 < W) work[i * W + j + 1] = m[o].y * inv_k2;
     }
-  }
+  });
 }
 
 template <int K, int R, int NT, int MINB, class Src>
@@ -1361,7 +1385,7 @@ __global__ void __launch_bounds__(NT, MINB) k_conv(const __grid_constant__ Src s
       // a single-system call takes k_conv_sep for a separable PSF; a table
       // may mix both kinds of segment
       if (!std::is_same<Src, OneSeg>::value && ss.conv_sep)
-        conv_vector_sep<K>(ss, b, mode, smem, red2, false);
+        conv_vector_sep<K, -1, 0>(ss, b, mode, smem, red2, false);
       else
         conv_vector_rows<K>(ss, b, mode, smem, red2);
     } else {
@@ -1384,7 +1408,15 @@ __global__ void __launch_bounds__(NT, MINB) k_conv_sep(const __grid_constant__ O
   // the row buffers, and the next vector's horizontal pass comes after the
   // barrier that follows its image load
   sep_prepare<K>(src.s, sep_layout(src.s, smem, src.s.H));
-  for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x) conv_vector_sep<K>(src.s, item, mode, smem, red2, true);
+  // the gradient call of a rank-1 PSF (a sampled Gaussian) with its mode and
+  // rank known at compile time; any other call with both read at run time
+  if (mode == MODE_GRAD && src.s.psf_rank == 1) {
+    for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x)
+      conv_vector_sep<K, MODE_GRAD, 1>(src.s, item, mode, smem, red2, true);
+  } else {
+    for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x)
+      conv_vector_sep<K, -1, 0>(src.s, item, mode, smem, red2, true);
+  }
 }
 
 // ---- small batches: one vector's convolution over a cluster of row bands ----
@@ -1603,14 +1635,14 @@ __global__ void __launch_bounds__(BAND_THREADS, 2) k_conv_sep_bands(const __grid
   __syncthreads();
   const int Wp2 = (W + 1) >> 1, nvu = ((nr + SEP_RV - 1) / SEP_RV) * Wp2;
   if (!corr_only) {
-    sep_hpass<K>(L.img, L, W, R, true);
+    sep_hpass<K, true, 0>(L.img, L, W, R);
     __syncthreads();
     float ll = 0.f, c2 = 0.f;
     for (int u = threadIdx.x; u < nvu; u += blockDim.x) {
       const int strip = u / Wp2, j = 2 * (u - strip * Wp2), i0 = strip * SEP_RV;
       const bool two = j + 1 < W;
       float2 m[SEP_RV];
-      sep_vunit<K>(L, R, true, i0, j, m);
+      sep_vunit<K, true, 0>(L, R, i0, j, m);
 #pragma unroll
       for (int o = 0; o < SEP_RV; ++o) {
         const int li = i0 + o;
@@ -1672,13 +1704,13 @@ __global__ void __launch_bounds__(BAND_THREADS, 2) k_conv_sep_bands(const __grid
   } else {
     cluster.sync();   // every band holds its input before any band writes the work slot
   }
-  sep_hpass<K>(L.img, L, W, R, false);
+  sep_hpass<K, false, 0>(L.img, L, W, R);
   __syncthreads();
   const float inv_k2 = 1.0f / float(s.k * s.k);
   for (int u = threadIdx.x; u < nvu; u += blockDim.x) {
     const int strip = u / Wp2, j = 2 * (u - strip * Wp2), i0 = strip * SEP_RV;
     float2 m[SEP_RV];
-    sep_vunit<K>(L, R, false, i0, j, m);
+    sep_vunit<K, false, 0>(L, R, i0, j, m);
 #pragma unroll
     for (int o = 0; o < SEP_RV; ++o) {
       const int li = i0 + o;

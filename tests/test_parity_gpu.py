@@ -447,7 +447,8 @@ def test_separable_bands_equal_one_block(abi, H, W, k, K, B):
     assert_plain_parity(ll1, g1, rl, rg, "separable bands %dx%d K=%d" % (H, W, K))
 
 
-@pytest.mark.parametrize("H,W,k,K,B", [(200, 200, 1, 21, 3), (170, 150, 1, 11, 200), (190, 210, 1, 21, 160)])
+@pytest.mark.parametrize("H,W,k,K,B", [(200, 200, 1, 21, 3), (170, 150, 1, 11, 200), (190, 210, 1, 21, 160),
+                                       (201, 187, 1, 21, 150)])
 def test_separable_bands_for_large_images(abi, H, W, k, K, B):
     """Images whose separable buffers do not fit one block convolve in
     cluster row bands (the last band shorter where the rows do not divide);

@@ -64,9 +64,12 @@ def test_observed_variance_system_matches_oracle(abi):
 PROFILED_EXCEPTIONS = {(200, 11): {"x_epl": 4.0, "x_s": 3.0}}
 
 
-@pytest.mark.parametrize("B,K", [(1, 9), (13, 9), (64, 9), (5, 11), (200, 11)])
-def test_profiled_loglik_matches_oracle(abi, B, K):
-    spec, truth, psf, _, image = _system(3, K=K)
+@pytest.mark.parametrize("B,K,H,W", [(1, 9, 48, 44), (13, 9, 48, 44), (64, 9, 48, 44), (5, 11, 48, 44),
+                                     (200, 11, 48, 44), (80, 11, 200, 190)])
+def test_profiled_loglik_matches_oracle(abi, B, K, H, W):
+    """The last case is too large for the whole-image separable buffers: its
+    correlation-only pass runs in cluster row bands (4 of 50 rows)."""
+    spec, truth, psf, _, image = _system(3, H=H, W=W, K=K)
     params = inputs.draw_perturbed(np.random.default_rng(B), truth, B, frac=0.02).astype(np.float32)
     s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg,
                      observed_variance=True)
