@@ -231,7 +231,14 @@ __device__ __forceinline__ float lg2c(float x) {
   return fmaf(d, 1.44269504088896341f, y0);
 }
 __device__ __forceinline__ float lg2cT(float a) { return lg2c(a); }
-__device__ __forceinline__ F2 lg2cT(F2 a) { return {make_float2(lg2c(a.v.x), lg2c(a.v.y))}; }
+// The same correction on a packed pair: per lane the arithmetic of lg2c (the
+// two FMAs as one packed FMA each).
+__device__ __forceinline__ F2 lg2cT(F2 a) {
+  const float y0x = lg2(a.v.x), y0y = lg2(a.v.y);
+  const F2 e = {make_float2(ex2(-y0x), ex2(-y0y))};
+  const F2 d = {__ffma2_rn(a.v, e.v, make_float2(-1.f, -1.f))};
+  return {__ffma2_rn(d.v, make_float2(1.44269504088896341f, 1.44269504088896341f), make_float2(y0x, y0y))};
+}
 
 // The same for a packed pair of grid indices n already in float (exact: |n|
 // is far below 2^24), so that the inner subpixel loops step n by exact float
