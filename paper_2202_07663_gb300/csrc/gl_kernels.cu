@@ -261,32 +261,33 @@ __device__ __forceinline__ void series_coeffs(int lane, float t, VecConst* V) {
   }
 }
 
-// Block size of k_setup: eight warps of per-vector work and one for the
+// Block size of k_setup: eight warps of per-vector work and two for the
 // FP64 constants of their vectors.
-constexpr int SETUP_THREADS = 9 * 32;
+constexpr int SETUP_THREADS = 10 * 32;
 
-// A block takes its vectors wpb (warps per block less one) at a time. The
-// last warp forms the FP64 constants: lane 3 v + part forms part `part` of
-// vector v of the chunk (setup_fp64_part), so that one warp's FP64
-// instructions serve several vectors. Each other warp takes one vector:
-// lanes 0..21 check one parameter each, lane 0 the EPL's FP32 constants,
-// lanes 1 and 2 the validity of the light profiles; all lanes compute the
-// series coefficients and, by ballot, the term count (FP32: every constant
-// feeds FP32 arithmetic). The two kinds of warp run side by side and write
-// disjoint fields of VecConst (one call at 60x60, B = 4096: 12.5 -> 11.8 us
-// against the FP64 parts in the first warp before its own vector).
+// A block takes its vectors wpb (warps per block less two) at a time. The
+// last two warps form the FP64 constants (setup_fp64_part): the first of
+// them the EPL part of each vector (lane v), the second the two light
+// profiles (lane 2 v + part - 1), so that neither warp's lanes diverge
+// between the two code paths and one warp's FP64 instructions serve several
+// vectors. Each other warp takes one vector: lanes 0..21 check one
+// parameter each, lane 0 the EPL's FP32 constants, lanes 1 and 2 the
+// validity of the light profiles; all lanes compute the series coefficients
+// and, by ballot, the term count (FP32: every constant feeds FP32
+// arithmetic). The kinds of warp run side by side and write disjoint fields
+// of VecConst (one call at 60x60, B = 4096: 12.5 -> 11.8 us against the
+// FP64 parts in the first warp before its own vector).
 template <class Src>
 __global__ void k_setup(const __grid_constant__ Src src) {
   const PdlScope pdl;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wpb = (blockDim.x >> 5) - 1;
+  const int wpb = (blockDim.x >> 5) - 2;
   const int nvec = src.nvec();
   for (int base = blockIdx.x * wpb; base < nvec; base += gridDim.x * wpb) {
-    if (warp == wpb) {
-      if (lane < 3 * wpb) {
-        const int item = base + lane / 3;
-        if (item < nvec) setup_fp64_part(src, item, lane % 3);
-      }
+    if (warp >= wpb) {
+      const bool epl = warp == wpb;
+      const int v = epl ? lane : lane >> 1;
+      if (v < wpb && base + v < nvec) setup_fp64_part(src, base + v, epl ? 0 : 1 + (lane & 1));
       continue;
     }
     const int item = base + warp;
@@ -1723,25 +1724,37 @@ __global__ void __launch_bounds__(BAND_THREADS, 2) k_conv_sep_bands(const __grid
 
 // ------------------------------------------------------------- k_final ----
 
-// b_n / n of a Sersic index.
-__device__ __forceinline__ double bn_over_n(float n) {
-  const double x = double(n);
-  return (1.9992 * x - 0.3271) / x;
+// The FP64 factors of a vector's chain rule, from five reciprocals:
+// b_n / n = 1.9992 - 0.3271 / n of the source and of the lens light, and
+// 1 / thetaE, 1 / R_l, 1 / R_s.
+struct ChainF {
+  double ms, ml, ite, iRl, iRs;
+};
+// Parameter whose reciprocal is factor i of chain_factors.
+__device__ __forceinline__ float recip_param(const float* pf, int i) {
+  return pf[i == 0 ? 16 : i == 1 ? 9 : i == 2 ? 0 : i == 3 ? 8 : 15];
+}
+__device__ __forceinline__ ChainF chain_factors(const double* r) {
+  ChainF f;
+  f.ms = fma(-0.3271, r[0], 1.9992);
+  f.ml = fma(-0.3271, r[1], 1.9992);
+  f.ite = r[2];
+  f.iRl = r[3];
+  f.iRs = r[4];
+  return f;
 }
 
-// The per-vector chain rule from the summed accumulators a[NACC] and the
-// parameters pf (FP64 arithmetic): gradient entry j; ms, ml: bn_over_n of
-// the source (pf[16]) and of the lens light (pf[9]). Shared by the two
-// k_final variants so that they give identical results.
-__device__ __forceinline__ double chain_rule(int j, const double* a, const float* pf, double ms, double ml) {
+// The per-vector chain rule from the summed accumulators a[NACC], the
+// parameters pf and the factors f (FP64 arithmetic): gradient entry j.
+// Shared by the two k_final variants so that they give identical results.
+__device__ __forceinline__ double chain_rule(int j, const double* a, const float* pf, const ChainF& f) {
   const double ln2 = 0.69314718055994530942;
-  if (j < 8) return j == 0 ? ms * (double(pf[1]) - 1.0) / double(pf[0]) * a[A_THETAE] : ms * a[A_THETAE + j];
+  if (j < 8) return j == 0 ? f.ms * (double(pf[1]) - 1.0) * f.ite * a[A_THETAE] : f.ms * a[A_THETAE + j];
   const int l = j < 15 ? 0 : 1, k = j - (l == 0 ? 8 : 15);
-  const float* q = pf + (l == 0 ? 8 : 15);
   const double* c = a + (l == 0 ? A_L_R : A_S_R);
-  const double m = l == 0 ? ml : ms;
+  const double m = l == 0 ? f.ml : f.ms;
   switch (k) {
-    case 0: return m / double(q[0]) * c[0];
+    case 0: return m * (l == 0 ? f.iRl : f.iRs) * c[0];
     case 1: return -1.9992 * c[1] + m * ln2 * c[2];
     case 2: return -0.5 * m * c[3];
     case 3: return -0.5 * m * c[4];
@@ -1774,8 +1787,11 @@ __global__ void k_final(const __grid_constant__ Src src) {
     for (int t = 0; t < s->ntiles; ++t)
       for (int i = 0; i < NACC; ++i) a[i] += part[t * NACC + i];
     const float* pf = s->params + size_t(b) * NPARAM;
-    const double ms = bn_over_n(pf[16]), ml = bn_over_n(pf[9]);
-    for (int j = 0; j < NPARAM; ++j) g[j] = chain_rule(j, a, pf, ms, ml);
+    double r[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) r[i] = 1.0 / double(recip_param(pf, i));
+    const ChainF f = chain_factors(r);
+    for (int j = 0; j < NPARAM; ++j) g[j] = chain_rule(j, a, pf, f);
   }
 }
 
@@ -1813,10 +1829,13 @@ __global__ void k_final_warp(const __grid_constant__ Src src) {
     }
     __syncwarp();
     const float* pf = s->params + size_t(b) * NPARAM;
-    double fac = 0.0;   // lanes 0, 1 compute the two factors once; the others receive them
-    if (lane < 2) fac = bn_over_n(pf[lane == 0 ? 16 : 9]);
-    const double ms = __shfl_sync(0xffffffffu, fac, 0), ml = __shfl_sync(0xffffffffu, fac, 1);
-    if (lane < NPARAM) g[lane] = chain_rule(lane, sa[w], pf, ms, ml);
+    // lanes 0..4 take the five divisions at once; every lane receives them
+    const double rl = lane < 5 ? 1.0 / double(recip_param(pf, lane)) : 0.0;
+    double r[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) r[i] = __shfl_sync(0xffffffffu, rl, i);
+    const ChainF f = chain_factors(r);
+    if (lane < NPARAM) g[lane] = chain_rule(lane, sa[w], pf, f);
     __syncwarp();
   }
 }
@@ -2190,7 +2209,7 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
                             bool short_tiles = false) {
   const int sms = num_sms();
   cudaError_t e;
-  const int vthreads = SETUP_THREADS, wpb = vthreads / 32 - 1;
+  const int vthreads = SETUP_THREADS, wpb = vthreads / 32 - 2;
   int sgrid = (nvec + wpb - 1) / wpb;
   int fgrid = (nvec + FINAL1_THREADS - 1) / FINAL1_THREADS;
   int wgrid = (nvec + FINAL_THREADS / 32 - 1) / (FINAL_THREADS / 32);
