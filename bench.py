@@ -723,14 +723,14 @@ def run_reference(args):
     return 0
 
 
-def run_small_batch(args, B: int = 50):
+def small_batch_workload(device, steps: int = 200, warmup: int = 5, B: int = 50, graph: bool = True) -> dict:
     """The call the samplers make (50 chains, Table 1): per-call time of
     log L + gradient for B vectors of one 80x80 system (k = 2, 11x11 PSF,
-    the paper's noise), inputs resident, CUDA events around K calls."""
+    the paper's noise), inputs resident, CUDA events around the calls on one
+    stream, issued one by one and (graph) replayed from a CUDA graph of 10
+    calls."""
     import torch
-    from paper_2202_07663_gb300 import abi, build
-    build.build()
-    device = torch.device("cuda", 0)
+    from paper_2202_07663_gb300 import abi
     spec = inputs.PAPER_SAMPLE_SPEC
     rng = np.random.default_rng(50)
     truth = inputs.draw_table(rng, inputs.PAPER_SIM, 1)[0]
@@ -746,20 +746,49 @@ def run_small_batch(args, B: int = 50):
                          .astype(np.float32)).to(device)
     ll = torch.empty(B, dtype=torch.float64, device=device)
     g = torch.empty(B, 22, dtype=torch.float64, device=device)
-    for _ in range(args.warmup):
-        s.loglik_grad(p, out=(ll, g, None))
-    torch.cuda.synchronize()
+    st = torch.cuda.Stream(device)
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(args.steps):
-        s.loglik_grad(p, out=(ll, g, None))
-    e.record()
-    torch.cuda.synchronize()
-    us = 1e3 * a.elapsed_time(e) / args.steps
+    with torch.cuda.stream(st):
+        for _ in range(warmup):
+            s.loglik_grad(p, out=(ll, g, None))
+        st.synchronize()
+        a.record(st)
+        for _ in range(steps):
+            s.loglik_grad(p, out=(ll, g, None))
+        e.record(st)
+        st.synchronize()
+        eager_us = 1e3 * a.elapsed_time(e) / steps
+        graph_us = None
+        if graph:
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, stream=st):
+                for _ in range(10):
+                    s.loglik_grad(p, out=(ll, g, None))
+            for _ in range(3):
+                gr.replay()
+            st.synchronize()
+            reps = max(1, steps // 10)
+            a.record(st)
+            for _ in range(reps):
+                gr.replay()
+            e.record(st)
+            st.synchronize()
+            graph_us = 1e3 * a.elapsed_time(e) / (10 * reps)
+    finite = bool(torch.isfinite(ll).all().item() and torch.isfinite(g).all().item())
     s.close()
-    print(json.dumps({"workload": "small-batch-80x80-k2-psf11-B50", "B": B, "steps": args.steps,
-                      "us_per_call": us, "evals_per_s": B / (us * 1e-6),
-                      "finite": bool(torch.isfinite(ll).all().item() and torch.isfinite(g).all().item())}))
+    out = {"workload": "small-batch-80x80-k2-psf11-B50", "B": B, "steps": steps,
+           "us_per_call": eager_us, "evals_per_s": B / (eager_us * 1e-6), "finite": finite}
+    if graph_us is not None:
+        out.update(graph_us_per_call=graph_us, graph_evals_per_s=B / (graph_us * 1e-6))
+    return out
+
+
+def run_small_batch(args, B: int = 50):
+    """--small-batch: the samplers' call alone (one JSON line)."""
+    import torch
+    from paper_2202_07663_gb300 import build
+    build.build()
+    print(json.dumps(small_batch_workload(torch.device("cuda", 0), args.steps, args.warmup, B, graph=False)))
     return 0
 
 
@@ -815,7 +844,8 @@ def main():
             "stress": measure(inputs.STRESS, device, 0, 1, 20, 3, cpu, peaks),
             "hmc": run_hmc_workload(device, cpu=cpu), "serving": run_serving_workload(device),
             "map": run_map_workload(device), "hmc_paper": run_hmc_paper_workload(device),
-            "variant": run_variant_workload(device), "pipeline": run_pipeline_workload(device)}
+            "variant": run_variant_workload(device), "pipeline": run_pipeline_workload(device),
+            "small_batch": small_batch_workload(device)}
     out["peaks"] = peaks
     print(json.dumps(out))
     if world > 1:
