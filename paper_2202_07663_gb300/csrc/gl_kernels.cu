@@ -1200,14 +1200,14 @@ __device__ __forceinline__ void sep_prepare(const Seg& s, const SepLayout& L) {
 }
 
 // The binned image (the vector's work slot) into the input's interior by
-// asynchronous copies; the caller synchronises the block after.
+// asynchronous copies, issued only: the caller waits for them
+// (cp_async_wait_all) and synchronises the block.
 template <int K>
-__device__ __forceinline__ void sep_load(const Seg& s, const SepLayout& L, const float* work) {
+__device__ __forceinline__ void sep_load_issue(const Seg& s, const SepLayout& L, const float* work) {
   constexpr int c = (K - 1) / 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = wid; i < s.H; i += nw)
     for (int j = lane; j < s.W; j += 32) cp_async4(&L.img[(i + c) * L.P + j + c], &work[i * s.W + j]);
-  cp_async_wait_all();
 }
 
 // Horizontal passes: row buffer r, row i, columns j0 .. j0 + 15, for the Ht
@@ -1309,9 +1309,15 @@ __device__ __forceinline__ void for_vunits(int nvs, int Wp2, F&& f) {
 // the subpixel adjoint to the vector's work slot. Every pixel's model value,
 // likelihood terms and adjoint are fixed by the layout, not the block size;
 // log L is summed in a block-size-dependent order. MODE_T: the mode when
-// known at compile time, else -1 (mode_rt); RC as for sep_hpass.
-template <int K, int MODE_T, int RC>
-__device__ void conv_vector_sep(const Seg& s, int b, int mode_rt, float* smem, double* red2, bool prepared) {
+// known at compile time, else -1 (mode_rt); RC as for sep_hpass. PF (with
+// MODE_T the gradient mode): this vector's image copies were issued by the
+// caller, and the copies of vector next_b (if >= 0) are issued once the
+// correlation's horizontal pass has read the input, so that they run during
+// the vertical pass.
+template <int K, int MODE_T, int RC, bool PF = false>
+__device__ void conv_vector_sep(const Seg& s, int b, int mode_rt, float* smem, double* red2, bool prepared,
+                                int next_b = -1) {
+  static_assert(!PF || MODE_T == MODE_GRAD, "prefetch only in the gradient pass");
   constexpr int c = (K - 1) / 2;
   const int mode = MODE_T >= 0 ? MODE_T : mode_rt;
   const int H = s.H, W = s.W, HW = H * W, R = RC > 0 ? RC : s.psf_rank;
@@ -1322,7 +1328,8 @@ __device__ void conv_vector_sep(const Seg& s, int b, int mode_rt, float* smem, d
   const bool want_grad = (mode == MODE_GRAD) || corr_only;
   const int Wp2 = (W + 1) >> 1;
   if (!prepared) sep_prepare<K>(s, L);
-  sep_load<K>(s, L, work);
+  if (!PF) sep_load_issue<K>(s, L, work);
+  cp_async_wait_all();
   __syncthreads();
   if (!corr_only) {
     sep_hpass<K, true, RC>(L.img, L, W, R);
@@ -1356,6 +1363,7 @@ __device__ void conv_vector_sep(const Seg& s, int b, int mode_rt, float* smem, d
   }
   sep_hpass<K, false, RC>(L.img, L, W, R);
   __syncthreads();
+  if (PF && next_b >= 0) sep_load_issue<K>(s, L, s.work + size_t(next_b) * HW);
   const float inv_k2 = 1.0f / float(s.k * s.k);
   for_vunits(L.nvs, Wp2, [&](int i0, int j) {
     float2 m[SEP_RV];
@@ -1412,8 +1420,14 @@ __global__ void __launch_bounds__(NT, MINB) k_conv_sep(const __grid_constant__ O
   // the gradient call of a rank-1 PSF (a sampled Gaussian) with its mode and
   // rank known at compile time; any other call with both read at run time
   if (mode == MODE_GRAD && src.s.psf_rank == 1) {
-    for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x)
-      conv_vector_sep<K, MODE_GRAD, 1>(src.s, item, mode, smem, red2, true);
+    // each vector's image copies run during the previous vector's last pass
+    const int n = src.nconv();
+    if (int(blockIdx.x) < n)
+      sep_load_issue<K>(src.s, sep_layout(src.s, smem, src.s.H), src.s.work + size_t(blockIdx.x) * src.s.H * src.s.W);
+    for (int item = blockIdx.x; item < n; item += gridDim.x) {
+      const int next = item + int(gridDim.x);
+      conv_vector_sep<K, MODE_GRAD, 1, true>(src.s, item, mode, smem, red2, true, next < n ? next : -1);
+    }
   } else {
     for (int item = blockIdx.x; item < src.nconv(); item += gridDim.x)
       conv_vector_sep<K, -1, 0>(src.s, item, mode, smem, red2, true);
