@@ -53,6 +53,18 @@ def test_gaussian_psf_is_rank_one(abi, K):
     _check_terms(psf, R, fac, s)
 
 
+def test_delta_and_zero_psfs(abi):
+    """A delta PSF (the identity convolution) is rank 1 with unit factors;
+    an all-zero PSF keeps the 2-D form (no norm to compare against)."""
+    K = 11
+    d = np.zeros((K, K), np.float32)
+    d[5, 5] = 1.0
+    R, fac = abi.psf_factor(d)
+    assert R == 1
+    np.testing.assert_allclose(np.outer(fac[0, 0], fac[0, 1]), d, atol=1e-7)
+    assert abi.psf_factor(np.zeros((K, K), np.float32))[0] == 0
+
+
 def test_sum_of_two_gaussians_is_rank_two(abi):
     x = np.arange(21) - 10.0
     g1, g2 = np.exp(-0.5 * (x / 1.3) ** 2), np.exp(-0.5 * ((x - 1.0) / 3.1) ** 2)
