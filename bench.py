@@ -318,9 +318,14 @@ def measure(workload: str, device, rank: int, world: int, steps: int, warmup: in
         step()
     torch.cuda.synchronize()
 
-    # ---- device-timed steps (inputs resident in HBM; L2 flushed between steps)
+    # ---- device-timed steps (inputs resident in HBM; L2 flushed between steps).
+    # Only the dominant kernel is bracketed by the library's events here: an
+    # event between two kernels of a call ends their programmatic overlap, and
+    # bracketing all five lengthened the 60x60 step by ~30 us (two boundaries:
+    # ~8 us). The other kernels' times come from a profiled pass below.
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     abi.gl_profile_reset()
+    abi.gl_profile_select([abi.GL_K_RAY_ADJ])
     abi.gl_profile_enable(True)
     n0 = abi.gl_launch_count()
     if world > 1:
@@ -339,12 +344,28 @@ def measure(workload: str, device, rank: int, world: int, steps: int, warmup: in
     if world > 1:
         dist.barrier()
     launches = abi.gl_launch_count() - n0
-    prof = abi.gl_profile_read()
+    prof_timed = abi.gl_profile_read()
     abi.gl_profile_enable(False)
-    del flush
     step_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, device, world)
     value = whole_job_rate(world, B, step_ms * 1e-3)
     ll_host, g_host = ll.cpu().numpy(), g.cpu().numpy()
+
+    # ---- profiled pass: every kernel bracketed (shares; slower steps, not the metric)
+    psteps = min(steps, 100)
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(psteps)]
+    abi.gl_profile_reset()
+    abi.gl_profile_select(range(abi.GL_KERNEL_KINDS))
+    abi.gl_profile_enable(True)
+    for a, b in pev:
+        flush.zero_()
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    prof = abi.gl_profile_read()
+    abi.gl_profile_enable(False)
+    profiled_ms = sum(a.elapsed_time(b) for a, b in pev) / psteps
+    del flush
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     hp = torch.from_numpy(params).pin_memory()
@@ -369,7 +390,7 @@ def measure(workload: str, device, rank: int, world: int, steps: int, warmup: in
     work = {"k_ray_adj": float(rays * flops_ray_adj(N_adj).sum()),
             "k_ray_fwd": float(rays * flops_ray_fwd(N_fwd).sum()),
             "k_conv": float(B * spec.H * spec.W * flops_conv_pixel(spec.K, True, psf_rank))}
-    n_adj, ms_adj = prof["k_ray_adj"]
+    n_adj, ms_adj = prof_timed["k_ray_adj"]   # the timed steps' own adjoint launches
     adj_s = (ms_adj / max(n_adj, 1)) * 1e-3
     fp32_peak = peaks["fp32_tflops"]
     sms = torch.cuda.get_device_properties(device).multi_processor_count
@@ -406,6 +427,8 @@ def measure(workload: str, device, rank: int, world: int, steps: int, warmup: in
         "roofline": {"bound": "alu", "kernel": "k_ray_adj", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "flops_per_launch": work["k_ray_adj"], "launch_ms": adj_s * 1e3,
+                     "launch_basis": "CUDA events around every k_ray_adj launch of the timed steps, on the "
+                                     "launching stream (the only kernel bracketed in them)",
                      "peak_basis": "measured: packed-FMA probe kernel of this library (gl_profile_peak) on this "
                                    "GPU before the timed steps, best of five launches",
                      "peak_nominal": fp32_nominal, "frac_of_nominal": achieved / fp32_nominal,
@@ -416,6 +439,9 @@ def measure(workload: str, device, rank: int, world: int, steps: int, warmup: in
                               "peak_basis": "measured: ex2 probe kernel (gl_profile_peak)"},
                      "mean_series_terms": float(N_adj.mean()), "kernel_source": th},
         "kernels": kern,
+        "kernels_basis": "a profiled pass of %d more steps with every kernel bracketed by CUDA events on the "
+                         "launching stream (the events end the programmatic overlap between kernels, so those "
+                         "steps took %.4f ms against the metric's %.4f)" % (psteps, profiled_ms, step_ms),
         "cpu_baseline": cpu_base,
         "error": err,
         "clocks": clocks,

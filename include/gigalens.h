@@ -558,12 +558,17 @@ const char* gl_error_string(int code);
 const char* gl_last_error_message(void);
 
 /*
- * Instrumentation. When enabled, every kernel the library launches is
- * bracketed by CUDA events recorded on the launching stream. gl_profile_read
- * synchronises on those events and fills, per kernel kind (indices below),
- * the number of launches and the summed device time in milliseconds;
- * arrays hold GL_KERNEL_KINDS entries. gl_launch_count counts every kernel
- * launch since load (profiling on or off).
+ * Instrumentation. When enabled, every kernel the library launches of the
+ * selected kinds (gl_profile_select: bit k for kind k; all kinds until
+ * called) is bracketed by CUDA events recorded on the launching stream.
+ * An event between two kernels of a call also ends their programmatic
+ * overlap (the next kernel is launched only when the previous one has
+ * finished), so bracketing every kernel lengthens a call; bracketing one
+ * kind costs only its two boundaries. gl_profile_read synchronises on the
+ * events and fills, per kernel kind (indices below), the number of launches
+ * and the summed device time in milliseconds; arrays hold GL_KERNEL_KINDS
+ * entries. gl_launch_count counts every kernel launch since load
+ * (profiling on or off).
  */
 #define GL_KERNEL_KINDS 6
 enum gl_kernel_kind {
@@ -575,6 +580,7 @@ enum gl_kernel_kind {
   GL_K_OTHER = 5
 };
 int gl_profile_enable(int on);
+int gl_profile_select(unsigned kinds);
 int gl_profile_reset(void);
 int gl_profile_read(long long* launches, double* total_ms);
 const char* gl_kernel_name(int kind);

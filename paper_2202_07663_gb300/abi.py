@@ -82,6 +82,7 @@ SIGNATURES = {
     "gl_launch_count": ([], ctypes.c_longlong),
     "gl_profile_peak": ([_i, _vp], _i),
     "gl_psf_factor": ([_vp, _i, _vp, _i, _vp], _i),
+    "gl_profile_select": ([ctypes.c_uint], _i),
     "gl_system_psf_rank": ([_vp], _i),
 }
 
@@ -220,6 +221,15 @@ def gl_hmc_affine_pullback(B, d, grad_z, L, grad_x, stream):
 
 def gl_profile_enable(on: bool) -> None:
     lib_handle().gl_profile_enable(1 if on else 0)
+
+
+def gl_profile_select(kinds) -> None:
+    """Bracket only the given kernel kinds (an iterable of GL_K_* values)
+    while profiling is on."""
+    mask = 0
+    for k in kinds:
+        mask |= 1 << int(k)
+    lib_handle().gl_profile_select(mask)
 
 
 def gl_profile_reset() -> None:

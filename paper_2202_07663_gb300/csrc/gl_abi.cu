@@ -83,13 +83,16 @@ struct Profiler final : gl::Hooks {
   };
   std::mutex mu;
   bool on = false;
+  unsigned kinds = ~0u;   // the kernel kinds bracketed while on (bit k: kind k)
+  bool rec_cur = false;
   std::vector<Rec> recs;
   Rec cur{};
   long long launches[GL_KERNEL_KINDS] = {};
   double ms[GL_KERNEL_KINDS] = {};
 
   void before(int kind, cudaStream_t st) override {
-    if (!on) return;
+    rec_cur = on && (kinds >> kind & 1u);
+    if (!rec_cur) return;
     cur.kind = kind;
     cudaEventCreate(&cur.a);
     cudaEventCreate(&cur.b);
@@ -99,10 +102,11 @@ struct Profiler final : gl::Hooks {
     (void)kind;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     cudaError_t e = cudaGetLastError();
-    if (on) {
+    if (rec_cur) {
       cudaEventRecord(cur.b, st);
       std::lock_guard<std::mutex> lk(mu);
       recs.push_back(cur);
+      rec_cur = false;
     }
     return e;
   }
@@ -733,6 +737,12 @@ const char* gl_last_error_message(void) { return g_msg; }
 int gl_profile_enable(int on) {
   g_prof.drain();
   g_prof.on = on != 0;
+  return GL_OK;
+}
+
+int gl_profile_select(unsigned kinds) {
+  g_prof.drain();
+  g_prof.kinds = kinds;
   return GL_OK;
 }
 

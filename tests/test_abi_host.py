@@ -61,7 +61,8 @@ def test_error_codes_mirror_header():
 NULL_TOLERANT = {"gl_system_destroy", "gl_batcher_destroy", "gl_profile_read", "gl_error_string",
                  "gl_last_error_message", "gl_kernel_name", "gl_launch_count", "gl_profile_enable",
                  "gl_profile_reset", "gl_vi_param_count", "gl_vi_workspace_bytes", "gl_system_scratch_bytes",
-                 "gl_system_resident_bytes", "gl_system_scratch_held", "gl_batcher_segment_bytes"}
+                 "gl_system_resident_bytes", "gl_system_scratch_held", "gl_batcher_segment_bytes",
+                 "gl_profile_select"}
 
 
 @pytest.mark.parametrize("name", [n for n in declared_functions() if n not in NULL_TOLERANT])
