@@ -200,6 +200,16 @@ def test_deterministic_and_host_path(abi):
     np.testing.assert_array_equal(hg, a[1])
     ll_only = s.loglik(p).cpu().numpy()
     np.testing.assert_array_equal(ll_only, a[0])
+    # page-locked host buffers, twice (the staging buffers are reused)
+    pp = torch.from_numpy(params).pin_memory()
+    pl = torch.empty(40, dtype=torch.float64).pin_memory()
+    pg = torch.empty(40, 22, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        pl.fill_(np.nan)
+        pg.fill_(np.nan)
+        s.loglik_grad_host(pp.numpy(), pl.numpy(), pg.numpy())
+        np.testing.assert_array_equal(pl.numpy(), a[0])
+        np.testing.assert_array_equal(pg.numpy(), a[1])
     s.close()
 
 
