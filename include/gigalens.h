@@ -570,14 +570,17 @@ const char* gl_last_error_message(void);
  * entries. gl_launch_count counts every kernel launch since load
  * (profiling on or off).
  */
-#define GL_KERNEL_KINDS 6
+#define GL_KERNEL_KINDS 7
 enum gl_kernel_kind {
   GL_K_SETUP = 0,    /* per-vector constants */
   GL_K_RAY_FWD = 1,  /* ray shooting + lights + k x k binning */
   GL_K_CONV = 2,     /* PSF convolution + likelihood (+ pixel adjoint) */
   GL_K_RAY_ADJ = 3,  /* recomputed rays + forward-mode derivatives */
   GL_K_FINAL = 4,    /* per-vector gradient reduction */
-  GL_K_OTHER = 5
+  GL_K_OTHER = 5,
+  GL_K_ORDER = 6     /* order of a call's vectors, longest EPL series first:
+                        two kernels (keys, counting sort) in single-system
+                        calls of at least one vector per SM */
 };
 int gl_profile_enable(int on);
 int gl_profile_select(unsigned kinds);

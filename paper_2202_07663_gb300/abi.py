@@ -21,8 +21,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "lib
 
 GL_OK = 0
 GL_ERR_INVALID_ARG, GL_ERR_OOM, GL_ERR_CUDA, GL_ERR_TIMEOUT, GL_ERR_BUDGET, GL_ERR_UNSUPPORTED = range(-1, -7, -1)
-GL_K_SETUP, GL_K_RAY_FWD, GL_K_CONV, GL_K_RAY_ADJ, GL_K_FINAL, GL_K_OTHER = range(6)
-GL_KERNEL_KINDS = 6
+GL_K_SETUP, GL_K_RAY_FWD, GL_K_CONV, GL_K_RAY_ADJ, GL_K_FINAL, GL_K_OTHER, GL_K_ORDER = range(7)
+GL_KERNEL_KINDS = 7
 GL_MAX_SEGMENTS = 256
 
 _lock = threading.Lock()

@@ -765,7 +765,8 @@ int gl_profile_read(long long* launches, double* total_ms) {
 }
 
 const char* gl_kernel_name(int kind) {
-  static const char* names[GL_KERNEL_KINDS] = {"k_setup", "k_ray_fwd", "k_conv", "k_ray_adj", "k_final", "other"};
+  static const char* names[GL_KERNEL_KINDS] = {"k_setup", "k_ray_fwd", "k_conv", "k_ray_adj", "k_final", "other",
+                                                   "k_order"};
   return (kind >= 0 && kind < GL_KERNEL_KINDS) ? names[kind] : "unknown";
 }
 

@@ -92,7 +92,8 @@ struct __align__(16) VecConst {
   float kap_c;             // (2 - t) / 2: kappa = kap_c (thetaE/rho)^t
   float omt;               // 1 - t
   float e1i, e2i;          // e1, e2 times 1 / (1 - |eps|^2)
-  float pad_[4];
+  int order;               // written by k_order into slot p: the vector the ray kernels take p-th
+  float pad_[3];
   LightC light[2];         // [0] lens light at theta, [1] source at beta
   float an[NMAX];          // a_n = c_1 ... c_n, n = 1..NMAX at index n-1
   float ant[NMAX];         // d a_n / d t
@@ -117,6 +118,7 @@ struct Seg {
   int B;
   int ntiles;              // ray tiles per vector
   int tile_pix;            // detector pixels per ray tile
+  int ray_order;           // 1: the ray kernels take the vectors in VecConst::order (k_order); 0: as given
   double* loglik;          // [B] or null
   double* chi2;            // [B] or null
   double* grad;            // [B, 22] or null

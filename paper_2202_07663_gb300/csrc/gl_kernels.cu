@@ -121,6 +121,32 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Per-vector constants live in slots. With ray_order, k_order has put the
+// vectors in the slots longest EPL series first, and k_setup writes into
+// each slot the vector it holds (VecConst::order); else slot p holds vector
+// p. The ray kernels take their items slot by slot, so the heaviest
+// vectors' blocks come first, and write every result at the vector's own
+// index.
+// A slot's vector outside 0 .. B - 1 can only come from parameters changed
+// by another stream while k_order ran; it is then read as p, so that no
+// access leaves the batch.
+__device__ __forceinline__ int slot_checked(int o, int p, int B) { return unsigned(o) < unsigned(B) ? o : p; }
+__device__ __forceinline__ int slot_vector(const Seg& s, int p) {
+  return s.ray_order ? slot_checked(s.vc[p].order, p, s.B) : p;
+}
+// The same in k_setup, from the slot array k_order left at the start of the
+// work buffer (work + B ints).
+__device__ __forceinline__ int setup_vector(const Seg& s, int p) {
+  return s.ray_order ? slot_checked(reinterpret_cast<const int*>(s.work)[s.B + p], p, s.B) : p;
+}
+
+// Slot q and tile of a segment's ray item (local index in the segment); the
+// items of one slot are consecutive.
+__device__ __forceinline__ void ray_item(const Seg& ss, int local, int& q, int& tile) {
+  q = local / ss.ntiles;
+  tile = local - q * ss.ntiles;
+}
+
 // ------------------------------------------------------------- k_setup ----
 
 // Derived constants of one Sersic profile (R_eff, n, e1, e2, xc, yc, I0),
@@ -161,10 +187,10 @@ __device__ void setup_light(const float* p, LightC& L) {
 // different lanes of one warp, several vectors per warp.
 template <class Src>
 __device__ void setup_fp64_part(const Src& src, int item, int part) {
-  int b;
-  const Seg* s = src.vec_seg(item, b);
-  VecConst* V = s->vc + b;
-  const float* pp = s->params + size_t(b) * NPARAM;
+  int p;
+  const Seg* s = src.vec_seg(item, p);
+  VecConst* V = s->vc + p;
+  const float* pp = s->params + size_t(setup_vector(*s, p)) * NPARAM;
   if (part == 0) {
     const double e1 = pp[2], e2 = pp[3], thetaE = pp[0];
     const double om = 1.0 - (e1 * e1 + e2 * e2);
@@ -292,14 +318,16 @@ __global__ void k_setup(const __grid_constant__ Src src) {
     }
     const int item = base + warp;
     if (item >= nvec) continue;   // warp-uniform
-    int b;
-    const Seg* s = src.vec_seg(item, b);
-    VecConst* V = s->vc + b;
+    int p;
+    const Seg* s = src.vec_seg(item, p);
+    VecConst* V = s->vc + p;
+    const int b = setup_vector(*s, p);
     const float* pp = s->params + size_t(b) * NPARAM;
     bool ok = lane >= NPARAM || isfinite(pp[lane]);
     const float e1 = pp[2], e2 = pp[3], t = pp[1] - 1.0f;
     const float e2s = fmaf(e1, e1, e2 * e2);
     if (lane == 0) {
+      V->order = b;
       const float thetaE = pp[0];
       ok = ok && thetaE > 0.f && e2s < 1.f && t > -1.f && t < 3.f;
       const float i1me2 = 1.0f / (1.0f - e2s);
@@ -340,6 +368,152 @@ __global__ void k_setup(const __grid_constant__ Src src) {
   }
 }
 
+// ------------------------------------------------------------- k_order ----
+
+// Slots of a call's vectors, longest EPL series first (the order the ray
+// kernels then take them in). A ray's cost grows with the vector's series
+// terms N (331 + 14 N flops in the adjoint, 90 + 7 N in the forward), and a
+// batch drawn from a prior mixes short and long series; with the heaviest
+// vectors' blocks in the first waves the last waves hold the lightest
+// (longest-processing-time first). The order is fixed before k_setup, so its
+// key comes from the parameters: the series' terms fall like |eps|^n, so N
+// grows like log(tol) / log|eps|, and the key is 204.8 / -log2(|eps|^2)
+// (about four keys per term at tol = 2e-8), capped at NMAX - 1.
+//
+// Two kernels, both before k_setup, using the start of the work buffer
+// (which k_ray_fwd fills only later) as int arrays: key[B], then slot[B],
+// the vector each slot holds. k_keys forms the keys over many blocks (one
+// block reading every vector's row of parameters waits on one SM's
+// scattered loads: 11.8 us at B = 4096). k_order, one block, is a counting
+// sort: each warp counts its vectors per key in a row of its own (shared-
+// memory atomics that never meet another warp's: a batch's keys crowd into
+// a few values, and one counter per key for the whole block would make the
+// warps wait on each other), a block-wide scan over (key from the largest down, warp)
+// turns the counts into first slots, and each warp hands out its slots.
+// Within one (key, warp) the slots follow the order the warp's atomics are
+// served in; results do not depend on the slots. k_setup reads its slot's
+// vector from slot[] and keeps it in VecConst::order for the later kernels.
+constexpr int KEYS_THREADS = 256;
+constexpr int ORDER_THREADS = 1024;
+constexpr int ORDER_WARPS = ORDER_THREADS / 32;
+constexpr int ORDER_UNROLL = 4;         // keys loaded per thread before they are counted
+constexpr int ORDER_PITCH = NMAX + 1;   // per-warp row of counts; the odd pitch spreads the banks
+constexpr int ORDER_STAGE = 4096;       // batches up to this size are scattered in shared memory
+static_assert(4 * ORDER_THREADS == ORDER_WARPS * NMAX, "the scan gives each thread four (key, warp) counts");
+
+__device__ __forceinline__ int order_key(const float* params, int b) {
+  const float e1 = params[size_t(b) * NPARAM + 2], e2 = params[size_t(b) * NPARAM + 3];
+  const float e2s = fmaf(e1, e1, e2 * e2);
+  if (!(e2s < 1.f)) return 0;   // NaN or |eps| >= 1 (invalid: no ray work)
+  const float r = 204.8f / -lg2(e2s);   // 0 at eps = 0 (lg2 gives -inf)
+  return r < float(NMAX - 1) ? int(r) : NMAX - 1;
+}
+
+__device__ __forceinline__ int* order_keys(const Seg& s) { return reinterpret_cast<int*>(s.work); }
+__device__ __forceinline__ int* order_slots(const Seg& s) { return reinterpret_cast<int*>(s.work) + s.B; }
+
+__global__ void __launch_bounds__(KEYS_THREADS) k_keys(const __grid_constant__ OneSeg src) {
+  const PdlScope pdl;
+  const Seg& s = src.s;
+  int* key = order_keys(s);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < s.B; b += gridDim.x * blockDim.x) key[b] = order_key(s.params, b);
+}
+
+// This lane's entry of row[key], the warp's own row (key < 0: no vector):
+// a shared-memory atomic that meets only the warp's other lanes.
+__device__ __forceinline__ int order_take(int* row, int key) { return key >= 0 ? atomicAdd(&row[key], 1) : 0; }
+
+__device__ __forceinline__ int order_key_at(const int* key, int b, int B) {
+  if (b >= B) return -1;
+  const int k = key[b];
+  return k < 0 ? 0 : (k > NMAX - 1 ? NMAX - 1 : k);
+}
+
+__global__ void __launch_bounds__(ORDER_THREADS) k_order(const __grid_constant__ OneSeg src) {
+  __shared__ int cnt[ORDER_WARPS * ORDER_PITCH];   // [warp][key]: vectors, then the warp's next slot
+  __shared__ int wsum[ORDER_WARPS];
+  __shared__ int stage[ORDER_STAGE];               // slot -> vector, for B <= ORDER_STAGE
+  const PdlScope pdl;
+  const Seg& s = src.s;
+  const int B = s.B, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int chunk = ORDER_UNROLL * ORDER_THREADS;
+  const int* keys = order_keys(s);
+  int* slots = order_slots(s);
+  const bool staged = B <= ORDER_STAGE;
+  int* row = cnt + w * ORDER_PITCH;
+  for (int i = tid; i < ORDER_WARPS * ORDER_PITCH; i += ORDER_THREADS) cnt[i] = 0;
+  __syncthreads();
+  int first[ORDER_UNROLL];   // the first chunk's keys, kept for the scatter
+  for (int b0 = tid; b0 - tid < B; b0 += chunk) {   // the same trip count for every thread
+    int key[ORDER_UNROLL];
+#pragma unroll
+    for (int u = 0; u < ORDER_UNROLL; ++u) key[u] = order_key_at(keys, b0 + u * ORDER_THREADS, B);
+#pragma unroll
+    for (int u = 0; u < ORDER_UNROLL; ++u) {
+      order_take(row, key[u]);
+      if (b0 == tid) first[u] = key[u];
+    }
+  }
+  __syncthreads();
+  // exclusive scan in the order (key from NMAX - 1 down, warp 0 .. 31):
+  // thread t takes positions 4 t .. 4 t + 3, one key and four warps
+  {
+    const int key = NMAX - 1 - (4 * tid) / ORDER_WARPS, w0 = (4 * tid) % ORDER_WARPS;
+    int v[4], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = cnt[(w0 + j) * ORDER_PITCH + key];
+      sum += v[j];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const int t = wsum[lane];
+      int c = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, c, o);
+        if (lane >= o) c += y;
+      }
+      wsum[lane] = c - t;
+    }
+    __syncthreads();
+    int slot = wsum[w] + incl - sum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      cnt[(w0 + j) * ORDER_PITCH + key] = slot;
+      slot += v[j];
+    }
+  }
+  __syncthreads();
+  // the same keys as the count, so the slots handed out are exactly 0 .. B - 1
+  for (int b0 = tid; b0 - tid < B; b0 += chunk) {
+    int key[ORDER_UNROLL];
+#pragma unroll
+    for (int u = 0; u < ORDER_UNROLL; ++u) key[u] = b0 == tid ? first[u] : order_key_at(keys, b0 + u * ORDER_THREADS, B);
+#pragma unroll
+    for (int u = 0; u < ORDER_UNROLL; ++u) {
+      const int slot = order_take(row, key[u]);
+      if (key[u] >= 0 && slot < B) {
+        if (staged)
+          stage[slot] = b0 + u * ORDER_THREADS;
+        else
+          slots[slot] = b0 + u * ORDER_THREADS;
+      }
+    }
+  }
+  if (staged) {
+    __syncthreads();
+    for (int i = tid; i < B; i += ORDER_THREADS) slots[i] = stage[i];
+  }
+}
+
 // ----------------------------------------------------------- k_ray_fwd ----
 
 #ifndef GL_FWD_THREADS
@@ -360,9 +534,11 @@ __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd(const __gr
     const Seg* segp = src.ray_seg(item, local);
     block_copy(&ss, segp);
     __syncthreads();
-    const int b = local / ss.ntiles, tile = local - b * ss.ntiles;
-    block_copy(&sv, ss.vc + b);
+    int q, tile;
+    ray_item(ss, local, q, tile);
+    block_copy(&sv, ss.vc + q);
     __syncthreads();
+    const int b = ss.ray_order ? slot_checked(sv.order, q, ss.B) : q;   // the vector in slot q
     const int HW = ss.H * ss.W, W = ss.W, k = ss.k;
     const int p0 = tile * ss.tile_pix;
     const int p1 = min(HW, p0 + ss.tile_pix);
@@ -417,9 +593,11 @@ __global__ void __launch_bounds__(FWD_THREADS, GL_FWD_MINB) k_ray_fwd_basis(cons
     const Seg* segp = src.ray_seg(item, local);
     block_copy(&ss, segp);
     __syncthreads();
-    const int b = local / ss.ntiles, tile = local - b * ss.ntiles;
-    block_copy(&sv, ss.vc + b);
+    int q, tile;
+    ray_item(ss, local, q, tile);
+    block_copy(&sv, ss.vc + q);
     __syncthreads();
+    const int b = ss.ray_order ? slot_checked(sv.order, q, ss.B) : q;   // the vector in slot q
     if (threadIdx.x == 0) {
       sv.light[0].I0 = 1.f;
       sv.light[1].I0 = 1.f;
@@ -631,9 +809,11 @@ __global__ void __launch_bounds__(ADJ_THREADS, MINB) k_ray_adj(const __grid_cons
     const Seg* segp = src.ray_seg(item, local);
     block_copy(&ss, segp);
     __syncthreads();
-    const int b = local / ss.ntiles, tile = local - b * ss.ntiles;
-    block_copy(&sv, ss.vc + b);
+    int q, tile;
+    ray_item(ss, local, q, tile);
+    block_copy(&sv, ss.vc + q);
     __syncthreads();
+    const int b = ss.ray_order ? slot_checked(sv.order, q, ss.B) : q;   // the vector in slot q
     RT acc[NACC];
 #pragma unroll
     for (int a = 0; a < NACC; ++a) acc[a] = sp<RT>(0.f);
@@ -1788,10 +1968,11 @@ template <class Src>
 __global__ void k_final(const __grid_constant__ Src src) {
   const PdlScope pdl;
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < src.nvec(); item += gridDim.x * blockDim.x) {
-    int b;
-    const Seg* s = src.vec_seg(item, b);
+    int p;
+    const Seg* s = src.vec_seg(item, p);
+    const int b = slot_vector(*s, p);
     double* g = s->grad + size_t(b) * NPARAM;
-    if (s->vc[b].nterms < 0) {
+    if (s->vc[p].nterms < 0) {
       for (int i = 0; i < NPARAM; ++i) g[i] = nan("");
       continue;
     }
@@ -1818,10 +1999,11 @@ __global__ void k_final_warp(const __grid_constant__ Src src) {
   const PdlScope pdl;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   for (int item = blockIdx.x * wpb + w; item < src.nvec(); item += gridDim.x * wpb) {
-    int b;
-    const Seg* s = src.vec_seg(item, b);
+    int p;
+    const Seg* s = src.vec_seg(item, p);
+    const int b = slot_vector(*s, p);
     double* g = s->grad + size_t(b) * NPARAM;
-    if (s->vc[b].nterms < 0) {   // warp-uniform
+    if (s->vc[p].nterms < 0) {   // warp-uniform
       if (lane < NPARAM) g[lane] = nan("");
       continue;
     }
@@ -1976,9 +2158,12 @@ static int fwd_blocks_per_sm() {
 // a two-block wave: a block's time grows with the blocks sharing its SM, and
 // three share 1.027x the work of two; three only for tiles of at most
 // ADJ_SHORT_TILE_RAYS rays, whose spills cost little). Tiles keep at least
-// 8 rays per thread of a 256-thread block; ties go to fewer tiles. Small
-// batches are where the waves matter: 50 vectors of 80 x 80, k = 2, take 9
-// tiles (one adjoint wave) instead of 13 (1.4 waves).
+// 8 rays per thread of a 256-thread block; ties go to fewer tiles. 50
+// vectors of 80 x 80, k = 2, take 12 tiles (two adjoint waves). The model
+// sees neither a batch's spread of per-vector cost nor the forward's
+// faster blocks in a partly filled wave: halving the forward's weight chose
+// 9 tiles there (46.9 -> 44.1 us a call near one mode) but 2 instead of 5
+// for 300 vectors drawn from the prior (178 -> 204 us), so it was not kept.
 struct TilePlan {
   int ntiles, tile_pix;
   bool adj3;
@@ -2217,6 +2402,26 @@ static cudaError_t launch_conv_sep_bands(const OneSeg& src, int nb, int rows, in
   return cudaLaunchKernelEx(&cfg, k_conv_sep_bands<K>, src, mode, rows);
 }
 
+// Vectors at or above this count are taken longest series first (k_order).
+// Graph-replayed calls at 80 x 80, k = 2, vectors drawn from the prior, in
+// random order against heaviest first: 300 vectors 179.6 -> 163.9 us, 1000
+// vectors 478.3 -> 465.2 us; 60 x 60, B = 4096: 958.9 -> 939.6 us. Below
+// it the sort's launch is not repaid (a 50-vector call near one mode).
+static bool ray_order_pays(const Seg& s) { return s.B >= num_sms() && s.H * s.W >= 2; }
+
+// k_order before k_setup, for single-segment calls that take their vectors
+// in order.
+static bool takes_order(const OneSeg& src) { return src.s.ray_order != 0; }
+template <class Src>
+static bool takes_order(const Src&) { return false; }
+static cudaError_t launch_order(const OneSeg& src, int stage, cudaStream_t st) {
+  if (stage == 0)
+    return launch_pdl(k_keys, unsigned((src.s.B + KEYS_THREADS - 1) / KEYS_THREADS), KEYS_THREADS, 0, st, src);
+  return launch_pdl(k_order, 1u, ORDER_THREADS, 0, st, src);
+}
+template <class Src>
+static cudaError_t launch_order(const Src&, int, cudaStream_t) { return cudaErrorInvalidValue; }
+
 template <class Src>
 static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool adj_final, cudaStream_t st,
                             Hooks* hooks, bool persistent, bool one_tile = false, bool fwd_rays = true,
@@ -2235,6 +2440,14 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
     rgrid = rgrid < sms * 4 ? rgrid : sms * 4;
   }
   if (fwd) {
+    if (takes_order(src)) {
+      for (int stage = 0; stage < 2; ++stage) {   // k_keys, k_order
+        hooks->before(GL_K_ORDER, st);
+        e = launch_order(src, stage, st);
+        const cudaError_t h = hooks->after(GL_K_ORDER, st);
+        if (e != cudaSuccess || (e = h) != cudaSuccess) return e;
+      }
+    }
     hooks->before(GL_K_SETUP, st);
     e = launch_pdl(k_setup<Src>, unsigned(sgrid), vthreads, 0, st, src);
     cudaError_t h = hooks->after(GL_K_SETUP, st);
@@ -2264,8 +2477,12 @@ static cudaError_t run_rays(const Src& src, int nvec, int nray, bool fwd, bool a
   return cudaSuccess;
 }
 
-cudaError_t launch_one(const Seg& s, int mode, cudaStream_t st, Hooks* hooks) {
-  if (s.B <= 0) return cudaSuccess;
+cudaError_t launch_one(const Seg& s0, int mode, cudaStream_t st, Hooks* hooks) {
+  if (s0.B <= 0) return cudaSuccess;
+  Seg s = s0;
+  // the key and slot arrays take 2 B ints of the work buffer, which in
+  // MODE_CORR already holds the vectors' d log L / d M
+  s.ray_order = mode != MODE_CORR && ray_order_pays(s) ? 1 : 0;
   OneSeg src{s};
   cudaError_t e = run_rays(src, s.B, s.B * s.ntiles, true, false, st, hooks, false, false, mode != MODE_CORR);
   if (e != cudaSuccess) return e;

@@ -213,6 +213,41 @@ def test_deterministic_and_host_path(abi):
     s.close()
 
 
+@pytest.mark.parametrize("B", [151, 152, 400])
+def test_vector_order_leaves_results_unchanged(abi, B):
+    """A batch of at least one vector per SM is taken longest EPL series
+    first (a device-side counting sort of the vectors by |eps|^2 of the EPL);
+    a smaller one as given. Either way each vector's results are the same
+    bits whatever the batch's order: the batch as given, reversed and shuffled.
+    Vectors drawn from the prior (series from a few to tens of terms), two
+    invalid ones (no ray work: the sort's lowest key), and the vectors of
+    the six largest and six smallest EPL ellipticities (longest and shortest
+    series) against the oracle."""
+    spec = inputs.PAPER_SAMPLE_SPEC
+    truth, image, psf = make_system(spec, 21)
+    P = inputs.draw_table(np.random.default_rng(22), inputs.PAPER_PRIOR_DRAW, B).astype(np.float32)
+    bad = [3, 77]
+    P[bad, 2] = 1.3   # |e_epl| >= 1
+    s = abi.GLSystem(image, psf, spec.pixel_scale, spec.k, spec.gain_exposure, sigma_bkg=spec.sigma_bkg)
+
+    def run(Q):
+        ll, g = s.loglik_grad(torch.from_numpy(np.ascontiguousarray(Q)).cuda())
+        return ll.cpu().numpy(), g.cpu().numpy()
+
+    ll, g = run(P)
+    for perm in (np.arange(B)[::-1], np.random.default_rng(23).permutation(B)):
+        lp, gp = run(P[perm])
+        np.testing.assert_array_equal(lp, ll[perm])
+        np.testing.assert_array_equal(gp, g[perm])
+    s.close()
+    assert np.all(np.isnan(ll[bad])) and np.all(np.isnan(g[bad]))
+    good = np.setdiff1d(np.arange(B), bad)
+    f = np.hypot(P[good, 2], P[good, 3])
+    pick = good[np.concatenate([np.argsort(f)[:6], np.argsort(f)[-6:]])]
+    rl, _, rg = oracle_eval(spec, image, psf, P[pick])
+    assert_plain_parity(ll[pick], g[pick], rl, rg, "prior batch B=%d, longest and shortest series" % B)
+
+
 def test_grouped_launch_equals_single_calls(abi):
     specs = [inputs.SystemSpec(40, 40, 2, 11), inputs.SystemSpec(25, 31, 4, 21), inputs.SystemSpec(18, 18, 1, 5)]
     systems, params, singles = [], [], []
