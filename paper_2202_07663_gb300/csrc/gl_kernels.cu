@@ -2158,12 +2158,15 @@ static int fwd_blocks_per_sm() {
 // a two-block wave: a block's time grows with the blocks sharing its SM, and
 // three share 1.027x the work of two; three only for tiles of at most
 // ADJ_SHORT_TILE_RAYS rays, whose spills cost little). Tiles keep at least
-// 8 rays per thread of a 256-thread block; ties go to fewer tiles. 50
-// vectors of 80 x 80, k = 2, take 12 tiles (two adjoint waves). The model
-// sees neither a batch's spread of per-vector cost nor the forward's
-// faster blocks in a partly filled wave: halving the forward's weight chose
-// 9 tiles there (46.9 -> 44.1 us a call near one mode) but 2 instead of 5
-// for 300 vectors drawn from the prior (178 -> 204 us), so it was not kept.
+// 8 rays per thread of a 256-thread block; ties go to fewer tiles. Below
+// one vector per SM the forward's waves weigh half: there they are partly
+// filled, and its blocks, sharing an SM with fewer others, finish sooner
+// than the model's full wave. 50 vectors of 80 x 80, k = 2, then take 9
+// tiles (one three-block adjoint wave) instead of 12 (46.9 -> 44.1 us a
+// call near one mode, 56.7 -> 54.0 us for vectors drawn from the prior);
+// 100 x 100, k = 4: 145.5 -> 145.0 us. Larger batches keep weight 1: with
+// half, 300 vectors from the prior took 2 tiles instead of 5 (178 -> 204 us;
+// the model does not see a batch's spread of per-vector cost).
 struct TilePlan {
   int ntiles, tile_pix;
   bool adj3;
@@ -2178,6 +2181,7 @@ static TilePlan plan_rays(int B, int H, int W, int k) {
   if (max_nt > HW) max_nt = HW;
   if (max_nt < 1) max_nt = 1;
   const double sms = num_sms(), fwd_slots = sms * fwd_blocks_per_sm();
+  const double wf = B < sms ? 0.5 : 1.0;   // weight of the forward's waves
   double best_cost = 0.0;
   for (long long nt = 1; nt <= max_nt; ++nt) {
     const int tp = int((HW + nt - 1) / nt);
@@ -2188,7 +2192,7 @@ static TilePlan plan_rays(int B, int H, int W, int k) {
     const double adj2 = std::ceil(items / (2 * sms)) * px;
     const bool short_tile = (long long)tp * k * k <= ADJ_SHORT_TILE_RAYS;
     const double adj3 = short_tile ? std::ceil(items / (3 * sms)) * px * (3.0 / 2.054) : 1e300;
-    const double cost = fwd + 2.4 * (adj3 < adj2 ? adj3 : adj2);
+    const double cost = wf * fwd + 2.4 * (adj3 < adj2 ? adj3 : adj2);
     if (nt == 1 || cost < best_cost * (1.0 - 1e-9)) {
       best_cost = cost;
       best = TilePlan{ntt, tp, adj3 < adj2};
