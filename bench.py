@@ -91,7 +91,7 @@ MUFU_RAY_ADJ = 13   # ex2/lg2/rcp per ray in the adjoint: EPL 5 (lg2, ex2, three
 # DRAM bytes per launch of k_ray_adj from one ncu capture, keyed by workload
 # and the kernel source it was taken on (sha256 prefix of gl_kernels.cu +
 # gl_device.cuh); any other source reports null traffic until it is captured again.
-TRAFFIC = {("multistart-60x60-k2-psf11-B4096", "1b162d5820662b43"): 64.466e6}
+TRAFFIC = {("multistart-60x60-k2-psf11-B4096", "7e5e9fc077046014"): 64.524e6}
 
 
 def kernel_source_hash() -> str:
