@@ -49,6 +49,22 @@ def test_error_strings_without_gpu(lib):
     assert lib.gl_loglik(None, None, 1, None, None, None) == -1
 
 
+def test_kernel_kinds_mirror_header(lib):
+    """The instrumentation kinds: the header's enum, the binding's constants
+    and the library's names agree, one name per kind."""
+    from paper_2202_07663_gb300 import abi
+    text = _read(HEADER)
+    kinds = dict(re.findall(r"(GL_K_\w+)\s*=\s*(\d+)", text))
+    n = int(re.search(r"#define GL_KERNEL_KINDS (\d+)", text).group(1))
+    assert n == abi.GL_KERNEL_KINDS and sorted(int(v) for v in kinds.values()) == list(range(n))
+    for name, value in kinds.items():
+        assert getattr(abi, name) == int(value), name
+    names = [lib.gl_kernel_name(i) for i in range(n)]
+    assert len(set(names)) == n and b"unknown" not in names
+    assert lib.gl_kernel_name(abi.GL_K_ORDER) == b"k_order"
+    assert lib.gl_kernel_name(n) == b"unknown"
+
+
 def test_error_codes_mirror_header():
     from paper_2202_07663_gb300 import abi
     codes = dict(re.findall(r"(GL_(?:OK|ERR_\w+))\s*=\s*(-?\d+)", _read(HEADER)))
